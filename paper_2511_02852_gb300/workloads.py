@@ -1,0 +1,160 @@
+"""Seeded synthetic workloads shared by the tests, the bench and the oracle.
+
+This module only *describes* scenes (spectrum parameters, patch geometry,
+seeds, frame counts).  It holds none of the method's arithmetic: every
+number the method derives from these parameters (spectra, buckets,
+injection counts, particle positions, heights) is computed separately by the
+CUDA library and by the FP64 oracle.
+
+The scenes follow the shapes the paper states for its own experiments
+(Sec. 5.2 defaults: N_omega = N_theta = 16, U10 in {3,5,10,15}, patch
+resolutions 256^2..1024^2) and the five evaluation configurations of the
+hybrid-ocean synthesis path (tiny, realistic, batched, mixed-large,
+serving).  No public dataset is involved; every input is synthetic.
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+
+JONSWAP = 0
+PHILLIPS = 1
+COS2S_MITSUYASU = 0
+COS2 = 1
+AMP_NORMALIZED = 0
+AMP_LITERAL = 1
+
+
+def spectrum(**kw):
+    """A spectrum/background description with the library defaults."""
+    d = dict(
+        spectrum=JONSWAP, spreading=COS2S_MITSUYASU,
+        wind_speed=10.0, fetch=100e3, depth=0.0, wind_dir=0.0, gamma=0.0,
+        n_buckets=16, n_theta=16, bucket_edges=None,
+        omega_lo_mul=0.5, omega_hi_mul=2.5, amp_mode=AMP_NORMALIZED,
+        fft_n=64, fft_L=256.0, choppiness=1.0, seed=0,
+    )
+    d.update(kw)
+    return d
+
+
+def patch(**kw):
+    """A wave-particle patch description with the library defaults."""
+    d = dict(
+        origin_x=0.0, origin_y=0.0, cell=0.25, width=128, height=128,
+        band=0.0, max_particles=0, prefill=0, inject_scale=1.0, bin_cells=0,
+        emitter=0, obj_radius=4.0, obj_speed=8.0, obj_path_radius=20.0,
+        wake_amp=0.05, wake_rate=2, n_buckets=0,
+    )
+    d.update(kw)
+    return d
+
+
+def scene(name, spec, patches, frames, dt=1.0 / 60.0, **extra):
+    s = dict(name=name, spectrum=spec, patches=patches, frames=frames, dt=dt)
+    s.update(extra)
+    return s
+
+
+# -- tiny: Phillips U=10, cos^2 spreading, deep water, 64^2 FFT over 256 m,
+#    one 128^2 patch at 0.5 m, four log-spaced buckets 0.5..4 rad/s,
+#    2,000 prefilled particles, 60 frames at 1/60 s, seed 0.
+def tiny():
+    edges = [0.5 * 8.0 ** (e / 4.0) for e in range(5)]
+    spec = spectrum(spectrum=PHILLIPS, spreading=COS2, wind_speed=10.0,
+                    depth=0.0, n_buckets=4, bucket_edges=edges, n_theta=16,
+                    fft_n=64, fft_L=256.0, seed=0)
+    p = patch(origin_x=-32.0, origin_y=-32.0, cell=0.5, width=128, height=128,
+              max_particles=65536, prefill=2000, inject_scale=1.0)
+    return scene("tiny", spec, [p], frames=60)
+
+
+# -- realistic: JONSWAP U10=15 m/s, fetch 100 km, gamma 3.3, depth 50 m,
+#    512^2 FFT over 1 km; one 1024^2 patch at 0.25 m around an object on a
+#    20 m circle at 8 m/s that emits wake particles; 16 equal-energy
+#    buckets, about 200k live particles; 600 frames.
+REALISTIC_INJECT_SCALE = 1.9
+
+
+def realistic():
+    spec = spectrum(spectrum=JONSWAP, spreading=COS2S_MITSUYASU,
+                    wind_speed=15.0, fetch=100e3, gamma=3.3, depth=50.0,
+                    n_buckets=16, n_theta=16, fft_n=512, fft_L=1000.0, seed=0)
+    p = patch(origin_x=-128.0, origin_y=-128.0, cell=0.25, width=1024,
+              height=1024, max_particles=400000, prefill=200000,
+              inject_scale=REALISTIC_INJECT_SCALE, emitter=1,
+              obj_radius=10.0, obj_speed=8.0, obj_path_radius=20.0,
+              wake_amp=0.05, wake_rate=2)
+    return scene("realistic", spec, [p], frames=600)
+
+
+# -- small parity scenes: same method, sizes the oracle finishes in seconds,
+#    spanning several synthesis tiles with ragged tails.
+def small_jonswap(seed=3):
+    spec = spectrum(spectrum=JONSWAP, wind_speed=12.0, fetch=50e3, gamma=0.0,
+                    depth=30.0, n_buckets=6, n_theta=12, fft_n=128,
+                    fft_L=300.0, choppiness=0.8, seed=seed)
+    p = patch(origin_x=17.3, origin_y=-40.1, cell=0.5, width=200, height=136,
+              max_particles=60000, prefill=3000, inject_scale=2.0, emitter=1,
+              obj_radius=6.0, obj_speed=6.0, obj_path_radius=15.0,
+              wake_amp=0.04, wake_rate=3)
+    return scene("small_jonswap", spec, [p], frames=12)
+
+
+def small_two_patches(seed=5):
+    spec = spectrum(spectrum=JONSWAP, wind_speed=9.0, fetch=30e3, gamma=2.0,
+                    depth=0.0, n_buckets=5, n_theta=8, wind_dir=0.7,
+                    fft_n=64, fft_L=200.0, seed=seed)
+    pa = patch(origin_x=-30.0, origin_y=12.0, cell=0.5, width=96, height=160,
+               max_particles=40000, prefill=1500, inject_scale=1.5)
+    pb = patch(origin_x=55.0, origin_y=-70.0, cell=0.25, width=72, height=72,
+               max_particles=40000, prefill=800, inject_scale=0.5, emitter=1,
+               obj_radius=3.0, obj_speed=4.0, obj_path_radius=5.0,
+               wake_amp=0.03, wake_rate=1)
+    return scene("small_two_patches", spec, [pa, pb], frames=8)
+
+
+# -- batched: 1024^2 FFT over 1 km; 32 patches, sides log-uniform in
+#    [64, 1024] cells at 0.25 m, 8-32 equal-energy buckets each (drawn per
+#    patch; all patches share one spectrum), 10k-500k particles
+#    each (log-uniform, rescaled to a 4M total), object speeds U(0, 12) m/s;
+#    300 frames; patch draws from seed 1.
+def batched(n_patches=32, total_particles=4_000_000, seed=1):
+    rng = np.random.default_rng(seed)
+    sides = np.exp(rng.uniform(math.log(64), math.log(1024), n_patches))
+    sides = np.clip(np.round(sides).astype(int), 64, 1024)
+    counts = np.exp(rng.uniform(math.log(1e4), math.log(5e5), n_patches))
+    counts = np.maximum(1, np.round(counts * total_particles / counts.sum()))
+    speeds = rng.uniform(0.0, 12.0, n_patches)
+    nbs = rng.integers(8, 33, n_patches)
+    ox = rng.uniform(-400.0, 400.0, n_patches)
+    oy = rng.uniform(-400.0, 400.0, n_patches)
+    spec = spectrum(spectrum=JONSWAP, wind_speed=12.0, fetch=100e3,
+                    gamma=3.3, depth=0.0, n_buckets=16, n_theta=16,
+                    fft_n=1024, fft_L=1000.0, seed=seed)
+    ps = []
+    for i in range(n_patches):
+        side = int(sides[i])
+        ps.append(patch(origin_x=float(ox[i]), origin_y=float(oy[i]),
+                        cell=0.25, width=side, height=side,
+                        max_particles=int(counts[i] * 2 + 4096),
+                        prefill=int(counts[i]), inject_scale=1.0,
+                        emitter=1 if speeds[i] > 0.5 else 0,
+                        obj_radius=4.0, obj_speed=float(max(speeds[i], 0.5)),
+                        obj_path_radius=min(20.0, side * 0.25 * 0.3),
+                        wake_amp=0.05, wake_rate=2, n_buckets=int(nbs[i])))
+    return scene("batched", spec, ps, frames=300)
+
+
+def scaled(sc, **patch_overrides):
+    """A copy of a scene with every patch's fields overridden."""
+    out = copy.deepcopy(sc)
+    for p in out["patches"]:
+        p.update(patch_overrides)
+    return out
+
+
+ALL = {"tiny": tiny, "realistic": realistic, "small_jonswap": small_jonswap,
+       "small_two_patches": small_two_patches, "batched": batched}
