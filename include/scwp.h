@@ -1,0 +1,263 @@
+/*
+ * scwp.h — C ABI of the GB300 (sm_103a) hybrid wave-particle / FFT ocean
+ * height-field synthesis of "Real-Time Interactive Hybrid Ocean:
+ * Spectrum-Consistent Wave Particle-FFT Coupling" (arXiv 2511.02852).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - a spectrum drives both a global FFT background and local wave-particle
+ *     (WP) patches (Sec. 3.1 and Fig. "Pipeline overview", Sec. 4.1);
+ *   - patches are rectangles placed around interactive objects inside which
+ *     the WP field replaces the background (Sec. 3.1, local replacement);
+ *   - every frame the background is evolved and inverse-transformed, the
+ *     particles are injected at the patch boundaries with counts from
+ *     Eqs. 15-17, advected, accumulated per frequency bucket and blended
+ *     into the background (Sec. 4.1-4.2).
+ *
+ * Conventions shared by every call:
+ *   - All pointers are plain host or device addresses; no C++ or framework
+ *     types cross this boundary.  The caller owns every pointer it passes;
+ *     the library copies what it keeps.
+ *   - Every call returns an scwp_status.  No exception crosses the ABI.  A
+ *     CUDA error is sticky: the context then answers SCWP_E_CUDA to every
+ *     call and must be destroyed.  scwp_last_error() gives the message.
+ *   - Calls on one context are not thread-safe; separate contexts are
+ *     independent.  Device work is ordered on the stream given at create.
+ *   - Device memory comes from the caller's allocator callback (if given),
+ *     else cudaMalloc; it is freed by scwp_destroy.
+ *   - Positions are Q16.16 fixed point in patch cell units relative to the
+ *     patch origin; texel (ix, iy) has its centre at ((ix+1/2)Q, (iy+1/2)Q).
+ *   - Maps are row-major float32 [height][width] (patch) or [N][N]
+ *     (background), row index = y.
+ */
+#ifndef SCWP_H
+#define SCWP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scwp_ctx scwp_ctx;
+
+typedef enum {
+    SCWP_OK = 0,
+    SCWP_E_INVALID = 1,   /* bad argument; nothing was changed            */
+    SCWP_E_NOMEM = 2,     /* the allocator failed                          */
+    SCWP_E_CAPACITY = 3,  /* particle pool full: injection was truncated   */
+    SCWP_E_CUDA = 4,      /* CUDA error (sticky)                           */
+    SCWP_E_TIMEOUT = 5,   /* a bounded device wait gave up (sticky)        */
+    SCWP_E_STATE = 6      /* call not valid in the current state           */
+} scwp_status;
+
+enum { SCWP_SPECTRUM_JONSWAP = 0, SCWP_SPECTRUM_PHILLIPS = 1 };
+enum { SCWP_SPREAD_COS2S_MITSUYASU = 0, SCWP_SPREAD_COS2 = 1 };
+enum { SCWP_AMP_NORMALIZED = 0, SCWP_AMP_LITERAL = 1 };
+enum { SCWP_FIELD_H = 0, SCWP_FIELD_DX = 1, SCWP_FIELD_DY = 2 };
+enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1 };
+
+#define SCWP_MAX_BUCKETS 64
+#define SCWP_MAX_THETA 256
+#define SCWP_WAKE_DIRS 4096
+
+/* Spectrum and background (Sec. 3.1 Eqs. 1-6; Sec. 3.3 Eq. 7 bucket range;
+ * Sec. 5.2 scene parameters).  JONSWAP: alpha, omega_p from Eq. 4; gamma
+ * from Eq. 4 unless gamma > 0.  Phillips (named in Sec. 2.1 / 3.1):
+ * S = 0.0081 g^2 w^-5 exp(-(g/(U w))^4).  Spreading: cos-2s with Mitsuyasu's
+ * s(w) (Eqs. 5-6), or one-sided (2/pi) cos^2.  Buckets: n_buckets
+ * equal-energy buckets on [omega_lo_mul, omega_hi_mul] * omega_p (default
+ * 0.5, 2.5; Sec. 3.3), or explicit ascending edges (n_buckets + 1 values,
+ * copied).  Directions: N_theta on the grid theta_w - pi + (j+1/2) 2pi/N.
+ * Background: fft_n x fft_n grid (power of two, 8..4096) over fft_L metres,
+ * choppiness lambda_c for the horizontal displacement. */
+typedef struct scwp_spectrum_desc {
+    int32_t spectrum;          /* SCWP_SPECTRUM_*                          */
+    int32_t spreading;         /* SCWP_SPREAD_*                            */
+    double wind_speed;         /* U10, m/s (> 0)                           */
+    double fetch;              /* m (> 0; JONSWAP)                         */
+    double depth;              /* m; <= 0: deep water                      */
+    double wind_dir;           /* rad                                      */
+    double gamma;              /* <= 0: Eq. 4                              */
+    int32_t n_buckets;         /* 1..SCWP_MAX_BUCKETS                      */
+    int32_t n_theta;           /* 1..SCWP_MAX_THETA                        */
+    const double* bucket_edges;/* n_buckets + 1 ascending, or NULL         */
+    double omega_lo_mul;       /* <= 0: 0.5                                */
+    double omega_hi_mul;       /* <= 0: 2.5                                */
+    int32_t amp_mode;          /* SCWP_AMP_*                               */
+    int32_t fft_n;             /* background grid size                     */
+    double fft_L;              /* background side, m                       */
+    double choppiness;         /* lambda_c                                 */
+    uint64_t seed;             /* Philox4x32-10 key                        */
+    /* device memory: alloc(bytes, user) -> device pointer or NULL;
+     * free(ptr, user).  Both NULL: cudaMalloc / cudaFree. */
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* alloc_user;
+    void* stream;              /* cudaStream_t; NULL: the legacy stream    */
+} scwp_spectrum_desc;
+
+/* A wave-particle patch (Sec. 3.1 local replacement; Sec. 3.3 injection;
+ * Sec. 4.3 object emission).  Injection per frame and edge pair s follows
+ * n = 4 L_s dt c_i / (pi r_i^2) * inject_scale (Eqs. 15-17) with a float64
+ * carry; amplitudes scale by 1/sqrt(inject_scale).  `prefill` particles are
+ * placed at creation, split over buckets in proportion to the injection's
+ * steady state.  With `emitter`, an object of radius obj_radius moves on a
+ * circle of radius obj_path_radius about the patch centre at obj_speed and
+ * emits wake_rate particles per Kelvin arm per frame into the bucket whose
+ * radius is closest to obj_radius, amplitude wake_amp. */
+typedef struct scwp_patch_desc {
+    double origin_x, origin_y; /* world position of the patch corner, m    */
+    double cell;               /* texel size, m                            */
+    int32_t width, height;     /* texels (1..16384)                        */
+    double band;               /* blend band, cells; <= 0: min(W,H)/8      */
+    int32_t max_particles;     /* particle pool capacity (> 0)             */
+    int32_t prefill;           /* particles placed at creation (>= 0)      */
+    double inject_scale;       /* <= 0: 1                                  */
+    int32_t bin_cells;         /* bin side in texels; <= 0: automatic      */
+    int32_t emitter;           /* 0/1                                      */
+    double obj_radius, obj_speed, obj_path_radius, wake_amp;
+    int32_t wake_rate;         /* particles per arm per frame              */
+    int32_t n_buckets;         /* <= 0: the spectrum's                     */
+} scwp_patch_desc;
+
+/* Per-patch statistics of the last completed frame (counts are exact). */
+typedef struct scwp_stats {
+    int64_t frame;             /* frames stepped                           */
+    double time;               /* running sum of dt, s                     */
+    int64_t live_particles;    /* after this frame's injection             */
+    int64_t bumps_binned;      /* bumps with >= 1 texel centre in support  */
+    int64_t eval_count;        /* sum over binned bumps of texels in support */
+    int64_t injected_total;    /* particles injected since creation        */
+    int32_t n_buckets;
+    int32_t error_flags;       /* bit 0: capacity, bit 1: timeout          */
+    int64_t live_per_bucket[SCWP_MAX_BUCKETS];
+    double injected_energy[SCWP_MAX_BUCKETS]; /* sum 1/8 A^2 pi r^2 (Eq. 12 / rho g) */
+} scwp_stats;
+
+/* Scalar description of a patch's tables and bins. */
+typedef struct scwp_patch_info {
+    int32_t n_buckets, n_theta, n_dirs;   /* n_dirs = n_theta (+ 4096 with an emitter) */
+    int32_t wake_bucket;
+    int32_t width, height;
+    int32_t total_bins;
+    int32_t capacity;
+    int32_t bin_cells[SCWP_MAX_BUCKETS];
+    int32_t nbx[SCWP_MAX_BUCKETS], nby[SCWP_MAX_BUCKETS], bin_base[SCWP_MAX_BUCKETS];
+} scwp_patch_info;
+
+/* Table identifiers for scwp_get_table (element type, count). */
+enum {
+    SCWP_TAB_OMEGA = 0,   /* double[nb]  bucket representative frequency   */
+    SCWP_TAB_K = 1,       /* double[nb]  wavenumber                        */
+    SCWP_TAB_C = 2,       /* double[nb]  phase speed                       */
+    SCWP_TAB_R = 3,       /* double[nb]  r = pi / k                        */
+    SCWP_TAB_E = 4,       /* double[nb]  bucket energy int S dw            */
+    SCWP_TAB_EDGES = 5,   /* double[nb+1]                                  */
+    SCWP_TAB_AMP = 6,     /* double[nb*nth]                                */
+    SCWP_TAB_RQ = 7,      /* int32[nb]   R_i = rint(r/dx Q)                */
+    SCWP_TAB_VX = 8,      /* int32[nb*nth] rint(c dt cos/dx Q)             */
+    SCWP_TAB_VY = 9,
+    SCWP_TAB_QX = 10,     /* int32[nb*nth] rint(r cos/dx Q)                */
+    SCWP_TAB_QY = 11,
+    SCWP_TAB_WAKE_VX = 12,/* int32[4096] (emitter only)                    */
+    SCWP_TAB_WAKE_VY = 13,
+    SCWP_TAB_WAKE_QX = 14,
+    SCWP_TAB_WAKE_QY = 15,
+    SCWP_TAB_CARRY = 16   /* double[nb*2] injection carries                */
+};
+
+/* Create a context: validates the description, computes the spectrum
+ * tables in float64 on the host, draws h0(k) (Philox4x32-10 + Box-Muller),
+ * allocates the background's device state.  *out = NULL on failure. */
+scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out);
+
+/* Add a patch: buckets, amplitudes and fixed-point tables (float64 host),
+ * particle pool, bins and output maps; places `prefill` particles.
+ * *patch_id = index in add order (0, 1, ...). */
+scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* patch_id);
+
+/* One frame of the hybrid ocean (Sec. 4.1): frame += 1, t += dt; the
+ * background spectrum update and inverse FFT; per patch advection,
+ * expiry, injection, wake emission, binning, synthesis and blend.
+ * Asynchronous on the context's stream.  dt > 0; the fixed-point
+ * velocity tables are rebuilt (float64, host) whenever dt changes. */
+scwp_status scwp_step(scwp_ctx* ctx, double dt);
+
+/* Copy a finished map: patch_id >= 0 a patch's blended map (height x
+ * width), patch_id = -1 the background (N x N).  dst_elems must be at
+ * least the map size.  dst_on_device = 1: device-to-device copy ordered on
+ * the stream (asynchronous); 0: device-to-host copy, synchronises the
+ * stream. */
+scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field,
+                            float* dst, size_t dst_elems, int32_t dst_on_device);
+
+/* Statistics of a patch after the last frame (synchronises the stream). */
+scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out);
+
+/* Table and bin geometry of a patch. */
+scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info* out);
+
+/* Copy one table (SCWP_TAB_*) of a patch into host memory; bytes must be at
+ * least the table's size. */
+scwp_status scwp_get_table(scwp_ctx* ctx, int32_t patch_id, int32_t table, void* dst, size_t bytes);
+
+/* Copy the live particles (SoA, host memory): x, y Q16.16; bd = bucket << 16
+ * | direction (direction >= n_theta: wake direction n_theta + a).  *n = live
+ * count; at most cap are copied (synchronises). */
+scwp_status scwp_get_particles(scwp_ctx* ctx, int32_t patch_id, int32_t* x, int32_t* y,
+                               uint32_t* bd, int64_t cap, int64_t* n);
+
+/* Replace the live particles of a patch (host SoA as above; n <= capacity).
+ * Directions and buckets are checked. */
+scwp_status scwp_set_particles(scwp_ctx* ctx, int32_t patch_id, const int32_t* x,
+                               const int32_t* y, const uint32_t* bd, int64_t n);
+
+/* Copy the last frame's bins of a patch (host memory): counts[total_bins],
+ * offsets[total_bins + 1], entries[n_entries] (bump ids 2p + k, k = 0 crest,
+ * 1 trough, stable in id order within a bin).  *n_entries = binned bumps. */
+scwp_status scwp_get_bins(scwp_ctx* ctx, int32_t patch_id, uint32_t* counts, uint32_t* offsets,
+                          uint32_t* entries, int64_t entries_cap, int64_t* n_entries);
+
+/* Recompute the synthesis and blend of every patch from the current
+ * particles and background without advancing the frame (the bins are
+ * rebuilt).  mode: SCWP_SYNTH_GATHER (tile gather, the default path of
+ * scwp_step) or SCWP_SYNTH_LAYERED (per-bucket layer splat + separable
+ * x / y passes + layer sum, Sec. 4.2). */
+scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode);
+
+/* Select the synthesis used by scwp_step (SCWP_SYNTH_*). */
+scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode);
+
+/* Stage timing with CUDA events on the context's stream: enable (1) or
+ * disable (0).  scwp_timing_read sums, over the frames stepped since the
+ * last read, the device time of [0] background FFT, [1] particle stages
+ * (advect .. bin), [2] synthesis + blend, [3] whole frame, in ms, and the
+ * number of frames; it synchronises and resets the sums. */
+scwp_status scwp_set_timing(scwp_ctx* ctx, int32_t enable);
+scwp_status scwp_timing_read(scwp_ctx* ctx, double ms_sum[4], int64_t* frames);
+
+/* Host-only: compute one table (SCWP_TAB_*, except SCWP_TAB_CARRY) of the
+ * patch `pdesc` would get under `sdesc` at time step dt, without a context
+ * or a GPU (the same float64 code scwp_add_patch runs).  bytes must be at
+ * least the table's size; *count receives its element count. */
+scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_desc* pdesc,
+                            double dt, int32_t table, void* dst, size_t bytes, int64_t* count);
+
+/* Number of kernels this context has enqueued since creation (every
+ * kernel of scwp_step / scwp_resynthesize counts once). */
+scwp_status scwp_launch_count(scwp_ctx* ctx, int64_t* n);
+
+/* Message of the last error on this context ("" if none). */
+const char* scwp_last_error(const scwp_ctx* ctx);
+
+/* Library version string. */
+const char* scwp_version(void);
+
+/* Free every device and host resource of the context (NULL is a no-op). */
+void scwp_destroy(scwp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCWP_H */

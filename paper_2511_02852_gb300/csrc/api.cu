@@ -1,0 +1,905 @@
+// C ABI of the hybrid ocean (include/scwp.h): context and patch management,
+// the per-frame orchestration of the sm_103a kernels (Sec. 4.1 pipeline), and
+// the copy / inspection calls.  Host bookkeeping that decides integers (the
+// injection carries, the wake's quantised angle) is float64 and lives in
+// host_spectrum.cpp / here, compiled without floating-point contraction.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/scwp.h"
+#include "host_spectrum.h"
+#include "internal.h"
+#include "philox.h"
+
+using namespace scwp;
+
+namespace scwp {
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace scwp
+
+namespace {
+
+constexpr int kTimingRing = 4096;
+
+struct PatchHost {
+    scwp_patch_desc d{};
+    int index = 0;
+    PatchTablesHost T;
+    PatchDev dev;
+    std::vector<double> carry;        // [nb][2]
+    std::vector<int32_t> nvalid;      // [nb][2]
+    std::vector<int16_t> dirlist;     // [nb][2][nth]
+    std::vector<BucketDev> bk;
+    std::vector<int32_t> bin_cells;
+    int64_t injected = 0;
+    std::vector<double> energy;       // [nb]
+    double band = 0;
+};
+
+struct FrameEvents {
+    cudaEvent_t e[6];                 // e0 start, e1 particles done, e2 synth start, e3 end, s0/s1 fft
+};
+
+}  // namespace
+
+struct scwp_ctx {
+    scwp_spectrum_desc d{};
+    std::vector<double> edges;
+    cudaStream_t st = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::string err;
+    scwp_status sticky = SCWP_OK;
+    SpectrumModel sm;
+    BgDev bg;
+    float2* h0 = nullptr;
+    double* omega = nullptr;
+    float2* tw = nullptr;
+    float2* G = nullptr;
+    float* bgout = nullptr;
+    int64_t frame = 0;
+    double t = 0.0;
+    double dt = -1.0;
+    bool bg_valid = false;
+    std::vector<PatchHost*> patches;
+    std::vector<void*> allocs;
+    int synth_mode = SCWP_SYNTH_GATHER;
+    bool timing = false;
+    std::vector<FrameEvents> ring;
+    int ring_n = 0;
+    double ms_sum[4] = {0, 0, 0, 0};
+    int64_t timed_frames = 0;
+    int64_t launches = 0;             // kernels enqueued by this context
+};
+
+namespace {
+
+scwp_status fail(scwp_ctx* c, scwp_status s, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (s == SCWP_E_CUDA || s == SCWP_E_TIMEOUT) c->sticky = s;
+    }
+    return s;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, SCWP_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void* dalloc(scwp_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (c->d.alloc) {
+        p = c->d.alloc(bytes, c->d.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back(p);
+    return p;
+}
+
+void dfree_all(scwp_ctx* c) {
+    for (void* p : c->allocs) {
+        if (c->d.free) c->d.free(p, c->d.alloc_user);
+        else cudaFree(p);
+    }
+    c->allocs.clear();
+}
+
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+scwp_status check_spectrum_desc(const scwp_spectrum_desc* d, std::string& why) {
+    if (!d) { why = "null descriptor"; return SCWP_E_INVALID; }
+    if (d->spectrum != SCWP_SPECTRUM_JONSWAP && d->spectrum != SCWP_SPECTRUM_PHILLIPS) { why = "spectrum"; return SCWP_E_INVALID; }
+    if (d->spreading != SCWP_SPREAD_COS2S_MITSUYASU && d->spreading != SCWP_SPREAD_COS2) { why = "spreading"; return SCWP_E_INVALID; }
+    if (!(d->wind_speed > 0)) { why = "wind_speed must be > 0"; return SCWP_E_INVALID; }
+    if (d->spectrum == SCWP_SPECTRUM_JONSWAP && !(d->fetch > 0)) { why = "fetch must be > 0"; return SCWP_E_INVALID; }
+    if (d->n_buckets < 1 || d->n_buckets > SCWP_MAX_BUCKETS) { why = "n_buckets out of range"; return SCWP_E_INVALID; }
+    if (d->n_theta < 1 || d->n_theta > SCWP_MAX_THETA) { why = "n_theta out of range"; return SCWP_E_INVALID; }
+    if (d->amp_mode != SCWP_AMP_NORMALIZED && d->amp_mode != SCWP_AMP_LITERAL) { why = "amp_mode"; return SCWP_E_INVALID; }
+    if (!pow2(d->fft_n) || d->fft_n < 8 || d->fft_n > 4096) { why = "fft_n must be a power of two in [8, 4096]"; return SCWP_E_INVALID; }
+    if (!(d->fft_L > 0)) { why = "fft_L must be > 0"; return SCWP_E_INVALID; }
+    if (d->bucket_edges) {
+        for (int i = 0; i < d->n_buckets; ++i)
+            if (!(d->bucket_edges[i + 1] > d->bucket_edges[i]) || !(d->bucket_edges[i] > 0)) {
+                why = "bucket_edges must be positive and ascending";
+                return SCWP_E_INVALID;
+            }
+    }
+    return SCWP_OK;
+}
+
+scwp_status check_patch_desc(const scwp_patch_desc* d, std::string& why) {
+    if (!d) { why = "null descriptor"; return SCWP_E_INVALID; }
+    if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384) { why = "patch size out of range"; return SCWP_E_INVALID; }
+    if (!(d->cell > 0)) { why = "cell must be > 0"; return SCWP_E_INVALID; }
+    if (d->max_particles < 1 || d->max_particles > (1 << 28)) { why = "max_particles out of range"; return SCWP_E_INVALID; }
+    if (d->prefill < 0) { why = "prefill < 0"; return SCWP_E_INVALID; }
+    if (d->n_buckets > SCWP_MAX_BUCKETS) { why = "n_buckets out of range"; return SCWP_E_INVALID; }
+    if (d->emitter) {
+        if (!(d->obj_path_radius > 0) || !(d->obj_radius > 0) || d->wake_rate < 0 || d->wake_rate > 1 << 20) {
+            why = "emitter parameters";
+            return SCWP_E_INVALID;
+        }
+    }
+    return SCWP_OK;
+}
+
+void model_from_desc(const scwp_spectrum_desc& d, SpectrumModel& sm) {
+    sm.init(d.spectrum, d.spreading, d.wind_speed, d.fetch, d.depth, d.wind_dir, d.gamma);
+}
+
+int patch_nb(const scwp_spectrum_desc& sd, const scwp_patch_desc& pd) {
+    return pd.n_buckets > 0 ? pd.n_buckets : sd.n_buckets;
+}
+
+void build_tables(const scwp_spectrum_desc& sd, const std::vector<double>& edges,
+                  const scwp_patch_desc& pd, const SpectrumModel& sm, PatchTablesHost& T) {
+    const int nb = patch_nb(sd, pd);
+    const double* e = (!edges.empty() && nb == sd.n_buckets) ? edges.data() : nullptr;
+    const double lo = sd.omega_lo_mul > 0 ? sd.omega_lo_mul : 0.5;
+    const double hi = sd.omega_hi_mul > 0 ? sd.omega_hi_mul : 2.5;
+    T.build(sm, nb, e, lo, hi, sd.n_theta, sd.amp_mode, pd.width, pd.height, pd.cell,
+            pd.inject_scale > 0 ? pd.inject_scale : 1.0, pd.obj_radius);
+}
+
+// bin side per bucket: 32 texels, doubled until the key space fits 16 bits
+void bin_geometry(PatchHost& P) {
+    const PatchTablesHost& T = P.T;
+    int C = P.d.bin_cells > 0 ? P.d.bin_cells : 32;
+    for (;;) {
+        int64_t total = 0;
+        for (int i = 0; i < T.nb; ++i) {
+            const int64_t Cq = (int64_t)C * kQ;
+            const int64_t nbx = ((int64_t)T.W * kQ + 2 * (int64_t)T.R[i]) / Cq + 1;
+            const int64_t nby = ((int64_t)T.H * kQ + 2 * (int64_t)T.R[i]) / Cq + 1;
+            total += nbx * nby;
+        }
+        if (total <= 65535 || P.d.bin_cells > 0 || C >= (1 << 14)) break;
+        C *= 2;
+    }
+    P.bin_cells.assign(T.nb, C);
+    P.bk.assign(T.nb, BucketDev{});
+    int base = 0;
+    for (int i = 0; i < T.nb; ++i) {
+        BucketDev& b = P.bk[i];
+        b.R = T.R[i];
+        b.invR = (float)(1.0 / (double)T.R[i]);
+        b.C = C * (int32_t)kQ;
+        b.nbx = (int32_t)(((int64_t)T.W * kQ + 2 * (int64_t)T.R[i]) / b.C + 1);
+        b.nby = (int32_t)(((int64_t)T.H * kQ + 2 * (int64_t)T.R[i]) / b.C + 1);
+        b.base = base;
+        base += b.nbx * b.nby;
+    }
+    P.dev.total_bins = base;
+    int bits = 1;
+    while ((1 << bits) < base + 1) ++bits;
+    P.dev.key_bits = bits;
+}
+
+void valid_dirs(PatchHost& P) {
+    const PatchTablesHost& T = P.T;
+    P.nvalid.assign(T.nb * 2, 0);
+    P.dirlist.assign((size_t)T.nb * 2 * T.nth, 0);
+    for (int i = 0; i < T.nb; ++i)
+        for (int s = 0; s < 2; ++s) {
+            int n = 0;
+            for (int j = 0; j < T.nth; ++j) {
+                const int32_t vn = s == 0 ? T.vx[(size_t)i * T.nth + j] : T.vy[(size_t)i * T.nth + j];
+                if (T.amp[(size_t)i * T.nth + j] > 0 && vn != 0)
+                    P.dirlist[((size_t)i * 2 + s) * T.nth + n++] = (int16_t)j;
+            }
+            P.nvalid[i * 2 + s] = n;
+        }
+}
+
+scwp_status upload_dt_tables(scwp_ctx* ctx, PatchHost& P) {
+    const PatchTablesHost& T = P.T;
+    const size_t ng = (size_t)T.nb * T.nth;
+    std::vector<int4> vq(ng + (P.dev.emitter ? kWakeDirs : 0));
+    for (size_t k = 0; k < ng; ++k) vq[k] = make_int4(T.vx[k], T.vy[k], T.qx[k], T.qy[k]);
+    if (P.dev.emitter)
+        for (int a = 0; a < kWakeDirs; ++a) vq[ng + a] = make_int4(T.wvx[a], T.wvy[a], T.wqx[a], T.wqy[a]);
+    valid_dirs(P);
+    CU(cudaMemcpyAsync(P.dev.vq, vq.data(), vq.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemcpyAsync(P.dev.dirlist, P.dirlist.data(), P.dirlist.size() * sizeof(int16_t),
+                       cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return SCWP_OK;
+}
+
+scwp_status ready(scwp_ctx* ctx) {
+    if (!ctx) return SCWP_E_INVALID;
+    if (ctx->sticky != SCWP_OK) return ctx->sticky;
+    return SCWP_OK;
+}
+
+SynthParams synth_params(scwp_ctx* ctx, const PatchHost& P) {
+    SynthParams sp{};
+    sp.W = P.T.W;
+    sp.H = P.T.H;
+    sp.nb = P.T.nb;
+    sp.lam_half = (float)(0.5 * ctx->d.choppiness);
+    sp.band = (float)P.band;
+    const double N = ctx->d.fft_n, L = ctx->d.fft_L;
+    double fx0 = (P.d.origin_x + 0.5 * P.d.cell) * N / L;
+    double fy0 = (P.d.origin_y + 0.5 * P.d.cell) * N / L;
+    fx0 -= N * std::floor(fx0 / N);
+    fy0 -= N * std::floor(fy0 / N);
+    sp.fx0 = (float)fx0;
+    sp.fy0 = (float)fy0;
+    sp.fsx = (float)(P.d.cell * N / L);
+    sp.N = ctx->d.fft_n;
+    sp.bg = ctx->bgout;
+    return sp;
+}
+
+scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P) {
+    CU(cudaMemsetAsync(P.dev.stats, 0, 2 * sizeof(unsigned long long), ctx->st));
+    CU(cudaMemsetAsync(P.dev.stats + 3, 0, (size_t)P.T.nb * sizeof(unsigned long long), ctx->st));
+    return SCWP_OK;
+}
+
+scwp_status synthesize(scwp_ctx* ctx, int mode) {
+    for (PatchHost* P : ctx->patches) {
+        const SynthParams sp = synth_params(ctx, *P);
+        if (mode == SCWP_SYNTH_LAYERED) CU(launch_layered(P->dev, sp, ctx->st));
+        else CU(launch_synth_gather(P->dev, sp, ctx->st));
+    }
+    return SCWP_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+const char* scwp_version(void) { return "scwp 0.1 (sm_103a)"; }
+
+const char* scwp_last_error(const scwp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
+    if (!out) return SCWP_E_INVALID;
+    *out = nullptr;
+    std::string why;
+    scwp_status s = check_spectrum_desc(desc, why);
+    if (s != SCWP_OK) return s;
+    scwp_ctx* ctx = new (std::nothrow) scwp_ctx();
+    if (!ctx) return SCWP_E_NOMEM;
+    ctx->d = *desc;
+    if (desc->bucket_edges) ctx->edges.assign(desc->bucket_edges, desc->bucket_edges + desc->n_buckets + 1);
+    ctx->d.bucket_edges = nullptr;
+    ctx->st = (cudaStream_t)desc->stream;
+    model_from_desc(ctx->d, ctx->sm);
+    auto bail = [&](scwp_status st) {
+        scwp_destroy(ctx);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(SCWP_E_CUDA);
+    }
+    const int N = desc->fft_n;
+    std::vector<float> h0;
+    std::vector<double> om;
+    build_background(ctx->sm, N, desc->fft_L, desc->seed, h0, om);
+    std::vector<float2> tw(N);
+    for (int m = 0; m < N; ++m) {
+        const double a = 2.0 * M_PI * m / N;
+        tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    const size_t NN = (size_t)N * N;
+    ctx->h0 = (float2*)dalloc(ctx, NN * sizeof(float2));
+    ctx->omega = (double*)dalloc(ctx, NN * sizeof(double));
+    ctx->tw = (float2*)dalloc(ctx, N * sizeof(float2));
+    ctx->G = (float2*)dalloc(ctx, 2 * NN * sizeof(float2));
+    ctx->bgout = (float*)dalloc(ctx, 3 * NN * sizeof(float));
+    if (!ctx->h0 || !ctx->omega || !ctx->tw || !ctx->G || !ctx->bgout) return bail(SCWP_E_NOMEM);
+    if (cudaMemcpy(ctx->h0, h0.data(), NN * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->omega, om.data(), NN * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(ctx->bgout, 0, 3 * NN * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(SCWP_E_CUDA);
+    }
+    ctx->bg.N = N;
+    ctx->bg.h0 = ctx->h0;
+    ctx->bg.omega = ctx->omega;
+    ctx->bg.tw = ctx->tw;
+    ctx->bg.G = ctx->G;
+    ctx->bg.out = ctx->bgout;
+    ctx->bg.lam = (float)desc->choppiness;
+    ctx->bg.dk = (float)(2.0 * M_PI / desc->fft_L);
+    *out = ctx;
+    return SCWP_OK;
+}
+
+scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* patch_id) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    std::string why;
+    if ((s = check_patch_desc(desc, why)) != SCWP_OK) return fail(ctx, s, why);
+    if (!ctx->edges.empty() && desc->n_buckets > 0 && desc->n_buckets != ctx->d.n_buckets) {
+        // explicit edges belong to the spectrum's bucket count; another count
+        // falls back to the equal-energy partition
+    }
+    PatchHost* P = new (std::nothrow) PatchHost();
+    if (!P) return fail(ctx, SCWP_E_NOMEM, "host allocation");
+    P->d = *desc;
+    P->index = (int)ctx->patches.size();
+    build_tables(ctx->d, ctx->edges, P->d, ctx->sm, P->T);
+    P->band = desc->band > 0 ? desc->band : std::min(desc->width, desc->height) / 8.0;
+    const PatchTablesHost& T = P->T;
+    PatchDev& D = P->dev;
+    D.W = T.W;
+    D.H = T.H;
+    D.nb = T.nb;
+    D.nth = T.nth;
+    D.cap = desc->max_particles;
+    D.emitter = desc->emitter ? 1 : 0;
+    D.wake_amp = (float)desc->wake_amp;
+    bin_geometry(*P);
+    const size_t cap = (size_t)D.cap;
+    D.nblk_c = (int)((cap + 1023) / 1024);
+    D.nblk_s = (int)((2 * cap + 4095) / 4096);
+    bool ok = true;
+    for (int k = 0; k < 2; ++k) {
+        D.x[k] = (int32_t*)dalloc(ctx, cap * 4);
+        D.y[k] = (int32_t*)dalloc(ctx, cap * 4);
+        D.bd[k] = (uint32_t*)dalloc(ctx, cap * 4);
+        D.keys[k] = (uint32_t*)dalloc(ctx, 2 * cap * 4);
+        D.vals[k] = (uint32_t*)dalloc(ctx, 2 * cap * 4);
+        ok = ok && D.x[k] && D.y[k] && D.bd[k] && D.keys[k] && D.vals[k];
+    }
+    D.count = (int32_t*)dalloc(ctx, 2 * sizeof(int32_t));
+    D.flags = (uint8_t*)dalloc(ctx, cap);
+    D.blk = (uint32_t*)dalloc(ctx, ((size_t)D.nblk_c + 1) * 4);
+    const size_t ng = (size_t)T.nb * T.nth;
+    D.vq = (int4*)dalloc(ctx, (ng + (D.emitter ? kWakeDirs : 0)) * sizeof(int4));
+    D.dirlist = (int16_t*)dalloc(ctx, (size_t)T.nb * 2 * T.nth * sizeof(int16_t));
+    D.amp = (float*)dalloc(ctx, ng * sizeof(float));
+    D.bk = (BucketDev*)dalloc(ctx, T.nb * sizeof(BucketDev));
+    D.hist = (uint32_t*)dalloc(ctx, (size_t)256 * D.nblk_s * 4);
+    D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
+    D.rec = (int4*)dalloc(ctx, 2 * cap * sizeof(int4));
+    D.out = (float*)dalloc(ctx, (size_t)3 * T.W * T.H * sizeof(float));
+    D.stats = (unsigned long long*)dalloc(ctx, (3 + (size_t)T.nb) * sizeof(unsigned long long));
+    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.hist &&
+         D.offsets && D.rec && D.out && D.stats;
+    if (!ok) {
+        delete P;
+        return fail(ctx, SCWP_E_NOMEM, "device allocation failed");
+    }
+    std::vector<float> ampf(ng);
+    for (size_t k = 0; k < ng; ++k) ampf[k] = (float)T.amp[k];
+    // prefill (reading: bucket shares proportional to (W Q + 2 R_i) / R_i^2)
+    std::vector<int32_t> px, py;
+    std::vector<uint32_t> pbd;
+    if (desc->prefill > 0) {
+        const int64_t Wq = (int64_t)T.W * kQ, Hq = (int64_t)T.H * kQ;
+        std::vector<double> w(T.nb);
+        double sw = 0.0;
+        for (int i = 0; i < T.nb; ++i) {
+            w[i] = (double)(Wq + 2 * (int64_t)T.R[i]) / ((double)T.R[i] * (double)T.R[i]);
+            sw += w[i];
+        }
+        for (int i = 0; i < T.nb; ++i) {
+            const int64_t pop = (int64_t)std::floor((double)desc->prefill * w[i] / sw + 0.5);
+            std::vector<int> valid;
+            for (int j = 0; j < T.nth; ++j)
+                if (T.amp[(size_t)i * T.nth + j] > 0) valid.push_back(j);
+            if (pop <= 0 || valid.empty()) continue;
+            const uint64_t R = (uint64_t)T.R[i];
+            for (int64_t n = 0; n < pop; ++n) {
+                const U4 u = philox4x32_10(0u, (uint32_t)P->index, (uint32_t)i | (3u << 16), (uint32_t)n,
+                                           ctx->d.seed);
+                const int32_t x = (int32_t)(-(int64_t)R + (int64_t)(((uint64_t)u.x * ((uint64_t)Wq + 2 * R)) >> 32));
+                const int32_t y = (int32_t)(-(int64_t)R + (int64_t)(((uint64_t)u.y * ((uint64_t)Hq + 2 * R)) >> 32));
+                px.push_back(x);
+                py.push_back(y);
+                pbd.push_back(((uint32_t)i << 16) | (uint32_t)valid[n % valid.size()]);
+            }
+        }
+    }
+    int32_t n0 = (int32_t)std::min<size_t>(px.size(), cap);
+    uint64_t flags0 = px.size() > cap ? kErrCapacity : 0;
+    int32_t counts[2] = {n0, n0};
+    CU(cudaMemcpyAsync(D.amp, ampf.data(), ng * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemcpyAsync(D.bk, P->bk.data(), T.nb * sizeof(BucketDev), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
+    CU(cudaMemsetAsync(D.stats, 0, (3 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
+    CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));
+    CU(cudaMemsetAsync(D.out, 0, (size_t)3 * T.W * T.H * sizeof(float), ctx->st));
+    if (n0 > 0) {
+        CU(cudaMemcpyAsync(D.x[0], px.data(), n0 * 4, cudaMemcpyHostToDevice, ctx->st));
+        CU(cudaMemcpyAsync(D.y[0], py.data(), n0 * 4, cudaMemcpyHostToDevice, ctx->st));
+        CU(cudaMemcpyAsync(D.bd[0], pbd.data(), n0 * 4, cudaMemcpyHostToDevice, ctx->st));
+    }
+    CU(cudaMemcpyAsync(D.count, counts, sizeof(counts), cudaMemcpyHostToDevice, ctx->st));
+    if (flags0) CU(cudaMemcpyAsync(D.stats + 2, &flags0, sizeof(flags0), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    P->carry.assign((size_t)T.nb * 2, 0.0);
+    P->energy.assign(T.nb, 0.0);
+    ctx->patches.push_back(P);
+    if (patch_id) *patch_id = P->index;
+    // velocity tables for the current dt (a provisional 1/60 s before the
+    // first step, so the trough offsets are valid for scwp_resynthesize)
+    P->T.set_dt(ctx->dt > 0 ? ctx->dt : 1.0 / 60.0);
+    s = upload_dt_tables(ctx, *P);
+    if (s != SCWP_OK) return s;
+    return SCWP_OK;
+}
+
+static scwp_status record(scwp_ctx* ctx, cudaEvent_t e, cudaStream_t st) {
+    CU(cudaEventRecord(e, st));
+    return SCWP_OK;
+}
+
+static scwp_status drain_ring(scwp_ctx* ctx) {
+    for (int i = 0; i < ctx->ring_n; ++i) {
+        FrameEvents& f = ctx->ring[i];
+        CU(cudaEventSynchronize(f.e[3]));
+        float a = 0, b = 0, c = 0, d = 0;
+        CU(cudaEventElapsedTime(&a, f.e[4], f.e[5]));
+        CU(cudaEventElapsedTime(&b, f.e[0], f.e[1]));
+        CU(cudaEventElapsedTime(&c, f.e[2], f.e[3]));
+        CU(cudaEventElapsedTime(&d, f.e[0], f.e[3]));
+        ctx->ms_sum[0] += a;
+        ctx->ms_sum[1] += b;
+        ctx->ms_sum[2] += c;
+        ctx->ms_sum[3] += d;
+        ctx->timed_frames += 1;
+    }
+    ctx->ring_n = 0;
+    return SCWP_OK;
+}
+
+static scwp_status step_impl(scwp_ctx* ctx, double dt);
+
+scwp_status scwp_step(scwp_ctx* ctx, double dt) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    const long long before = launches_total();
+    s = step_impl(ctx, dt);
+    ctx->launches += launches_total() - before;
+    return s;
+}
+
+static scwp_status step_impl(scwp_ctx* ctx, double dt) {
+    scwp_status s = SCWP_OK;
+    if (!(dt > 0)) return fail(ctx, SCWP_E_INVALID, "dt must be > 0");
+    if (dt != ctx->dt) {
+        ctx->dt = dt;
+        for (PatchHost* P : ctx->patches) {
+            if (dt == P->T.dt) continue;
+            P->T.set_dt(dt);
+            if ((s = upload_dt_tables(ctx, *P)) != SCWP_OK) return s;
+        }
+    }
+    ctx->frame += 1;
+    ctx->t += dt;
+    FrameEvents* fe = nullptr;
+    if (ctx->timing) {
+        if (ctx->ring_n == kTimingRing && (s = drain_ring(ctx)) != SCWP_OK) return s;
+        fe = &ctx->ring[ctx->ring_n++];
+        if ((s = record(ctx, fe->e[0], ctx->st)) != SCWP_OK) return s;
+    }
+    // background on the side stream, concurrent with the particle stages
+    CU(cudaEventRecord(ctx->ev_fork, ctx->st));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    if (fe && (s = record(ctx, fe->e[4], ctx->side)) != SCWP_OK) return s;
+    CU(launch_background(ctx->bg, ctx->t, ctx->side));
+    if (fe && (s = record(ctx, fe->e[5], ctx->side)) != SCWP_OK) return s;
+    CU(cudaEventRecord(ctx->ev_join, ctx->side));
+    ctx->bg_valid = true;
+
+    for (PatchHost* P : ctx->patches) {
+        PatchDev& D = P->dev;
+        const PatchTablesHost& T = P->T;
+        CU(launch_advect_flag(D, ctx->st));
+        CU(launch_compact(D, ctx->st));
+        D.cur ^= 1;
+        InjectParams ip{};
+        ip.frame = (uint32_t)ctx->frame;
+        ip.patch = (uint32_t)P->index;
+        ip.seed = ctx->d.seed;
+        ip.W = T.W;
+        ip.H = T.H;
+        ip.nth = T.nth;
+        int total = 0, nseg = 0;
+        for (int i = 0; i < T.nb; ++i)
+            for (int sp = 0; sp < 2; ++sp) {
+                double& acc = P->carry[(size_t)i * 2 + sp];
+                acc += T.injection_rate(i, sp);
+                const double m = std::floor(acc);
+                acc -= m;
+                const int nv = P->nvalid[i * 2 + sp];
+                if (m <= 0 || nv == 0) continue;
+                const int mi = (int)m;
+                Segment& g = ip.seg[nseg++];
+                g.bucket = i;
+                g.s = sp;
+                g.count = mi * nv;
+                g.first = total;
+                g.ndir = nv;
+                total += g.count;
+                double e = 0.0;
+                for (int k = 0; k < nv; ++k) {
+                    const int j = P->dirlist[((size_t)i * 2 + sp) * T.nth + k];
+                    const double A = T.amp[(size_t)i * T.nth + j];
+                    e += 0.125 * A * A * M_PI * T.r[i] * T.r[i];
+                }
+                P->energy[i] += mi * e;
+            }
+        if (D.emitter && P->d.wake_rate > 0) {
+            // reading of Sec. 4.3: object on a circle about the patch centre
+            const double dx = P->d.cell;
+            const double Rp = P->d.obj_path_radius / dx;
+            const double Om = P->d.obj_speed / P->d.obj_path_radius;
+            const double phi = Om * ctx->t;
+            ip.Px = T.W * 0.5 + Rp * std::cos(phi);
+            ip.Py = T.H * 0.5 + Rp * std::sin(phi);
+            const double psi = phi + M_PI / 2.0;
+            ip.rho = P->d.obj_radius / dx;
+            const double kelvin = M_PI / 2.0 - std::asin(1.0 / 3.0);
+            const double dpsi = 2.0 * M_PI / kWakeDirs;
+            for (int arm = 0; arm < 2; ++arm) {
+                const double sgn = arm == 0 ? 1.0 : -1.0;
+                const double psa = psi + sgn * kelvin;
+                int64_t a = (int64_t)std::floor(psa / dpsi + 0.5);
+                a = ((a % kWakeDirs) + kWakeDirs) % kWakeDirs;
+                ip.ca[arm] = T.wake_cos[a];
+                ip.sa[arm] = T.wake_sin[a];
+                Segment& g = ip.seg[nseg++];
+                g.bucket = T.wake_bucket;
+                g.s = 2;
+                g.count = P->d.wake_rate;
+                g.first = total;
+                g.ndir = P->d.wake_rate;
+                g.arm = arm;
+                g.wake_a = (int)a;
+                total += g.count;
+                const double rw = T.r[T.wake_bucket];
+                P->energy[T.wake_bucket] +=
+                    P->d.wake_rate * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
+            }
+        }
+        ip.nseg = nseg;
+        ip.total = total;
+        P->injected += total;
+        if (total > 0) CU(launch_inject(D, ip, ctx->st));
+        if ((s = reset_frame_stats(ctx, *P)) != SCWP_OK) return s;
+        CU(launch_bin(D, ctx->st));
+    }
+    if (fe && (s = record(ctx, fe->e[1], ctx->st)) != SCWP_OK) return s;
+    CU(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
+    if (fe && (s = record(ctx, fe->e[2], ctx->st)) != SCWP_OK) return s;
+    if ((s = synthesize(ctx, ctx->synth_mode)) != SCWP_OK) return s;
+    if (fe && (s = record(ctx, fe->e[3], ctx->st)) != SCWP_OK) return s;
+    CU(cudaGetLastError());
+    return SCWP_OK;
+}
+
+scwp_status scwp_launch_count(scwp_ctx* ctx, int64_t* n) {
+    if (!ctx || !n) return SCWP_E_INVALID;
+    *n = ctx->launches;
+    return SCWP_OK;
+}
+
+scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    const long long before = launches_total();
+    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED) return fail(ctx, SCWP_E_INVALID, "mode");
+    if (!ctx->bg_valid) {
+        CU(launch_background(ctx->bg, ctx->t, ctx->st));
+        ctx->bg_valid = true;
+    }
+    for (PatchHost* P : ctx->patches) {
+        if ((s = reset_frame_stats(ctx, *P)) != SCWP_OK) return s;
+        CU(launch_bin(P->dev, ctx->st));
+    }
+    if ((s = synthesize(ctx, mode)) != SCWP_OK) return s;
+    ctx->launches += launches_total() - before;
+    CU(cudaStreamSynchronize(ctx->st));
+    return SCWP_OK;
+}
+
+scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED) return fail(ctx, SCWP_E_INVALID, "mode");
+    ctx->synth_mode = mode;
+    return SCWP_OK;
+}
+
+scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field, float* dst, size_t dst_elems,
+                            int32_t dst_on_device) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (!dst || field < 0 || field > 2) return fail(ctx, SCWP_E_INVALID, "field or dst");
+    const float* src;
+    size_t n;
+    if (patch_id == -1) {
+        n = (size_t)ctx->d.fft_n * ctx->d.fft_n;
+        src = ctx->bgout + field * n;
+    } else {
+        if (patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "patch_id");
+        const PatchHost* P = ctx->patches[patch_id];
+        n = (size_t)P->T.W * P->T.H;
+        src = P->dev.out + field * n;
+    }
+    if (dst_elems < n) return fail(ctx, SCWP_E_INVALID, "dst too small");
+    if (dst_on_device) {
+        CU(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    } else {
+        CU(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    return SCWP_OK;
+}
+
+scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (!out || patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
+    PatchHost* P = ctx->patches[patch_id];
+    std::vector<unsigned long long> st(3 + P->T.nb);
+    int32_t cnt[2];
+    CU(cudaMemcpyAsync(st.data(), P->dev.stats, st.size() * 8, cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaMemcpyAsync(cnt, P->dev.count, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    memset(out, 0, sizeof(*out));
+    out->frame = ctx->frame;
+    out->time = ctx->t;
+    out->live_particles = cnt[0];
+    out->eval_count = (int64_t)st[0];
+    out->bumps_binned = (int64_t)st[1];
+    out->error_flags = (int32_t)st[2];
+    out->injected_total = P->injected;
+    out->n_buckets = P->T.nb;
+    for (int i = 0; i < P->T.nb; ++i) {
+        out->live_per_bucket[i] = (int64_t)st[3 + i];
+        out->injected_energy[i] = P->energy[i];
+    }
+    if (st[2] & kErrTimeout) return fail(ctx, SCWP_E_TIMEOUT, "a device wait timed out");
+    return SCWP_OK;
+}
+
+scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info* out) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (!out || patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
+    const PatchHost* P = ctx->patches[patch_id];
+    memset(out, 0, sizeof(*out));
+    out->n_buckets = P->T.nb;
+    out->n_theta = P->T.nth;
+    out->n_dirs = P->T.nth + (P->dev.emitter ? kWakeDirs : 0);
+    out->wake_bucket = P->T.wake_bucket;
+    out->width = P->T.W;
+    out->height = P->T.H;
+    out->total_bins = P->dev.total_bins;
+    out->capacity = P->dev.cap;
+    for (int i = 0; i < P->T.nb; ++i) {
+        out->bin_cells[i] = P->bin_cells[i];
+        out->nbx[i] = P->bk[i].nbx;
+        out->nby[i] = P->bk[i].nby;
+        out->bin_base[i] = P->bk[i].base;
+    }
+    return SCWP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+scwp_status copy_table(const PatchTablesHost& T, const std::vector<double>* carry, int32_t table, void* dst,
+                       size_t bytes, int64_t* count) {
+    const void* src = nullptr;
+    size_t n = 0, es = 0;
+    switch (table) {
+        case SCWP_TAB_OMEGA: src = T.omega.data(); n = T.omega.size(); es = 8; break;
+        case SCWP_TAB_K: src = T.k.data(); n = T.k.size(); es = 8; break;
+        case SCWP_TAB_C: src = T.c.data(); n = T.c.size(); es = 8; break;
+        case SCWP_TAB_R: src = T.r.data(); n = T.r.size(); es = 8; break;
+        case SCWP_TAB_E: src = T.E.data(); n = T.E.size(); es = 8; break;
+        case SCWP_TAB_EDGES: src = T.edges.data(); n = T.edges.size(); es = 8; break;
+        case SCWP_TAB_AMP: src = T.amp.data(); n = T.amp.size(); es = 8; break;
+        case SCWP_TAB_RQ: src = T.R.data(); n = T.R.size(); es = 4; break;
+        case SCWP_TAB_VX: src = T.vx.data(); n = T.vx.size(); es = 4; break;
+        case SCWP_TAB_VY: src = T.vy.data(); n = T.vy.size(); es = 4; break;
+        case SCWP_TAB_QX: src = T.qx.data(); n = T.qx.size(); es = 4; break;
+        case SCWP_TAB_QY: src = T.qy.data(); n = T.qy.size(); es = 4; break;
+        case SCWP_TAB_WAKE_VX: src = T.wvx.data(); n = T.wvx.size(); es = 4; break;
+        case SCWP_TAB_WAKE_VY: src = T.wvy.data(); n = T.wvy.size(); es = 4; break;
+        case SCWP_TAB_WAKE_QX: src = T.wqx.data(); n = T.wqx.size(); es = 4; break;
+        case SCWP_TAB_WAKE_QY: src = T.wqy.data(); n = T.wqy.size(); es = 4; break;
+        case SCWP_TAB_CARRY:
+            if (!carry) return SCWP_E_INVALID;
+            src = carry->data(); n = carry->size(); es = 8; break;
+        default: return SCWP_E_INVALID;
+    }
+    if (count) *count = (int64_t)n;
+    if (!dst) return SCWP_OK;
+    if (bytes < n * es) return SCWP_E_INVALID;
+    if (n) memcpy(dst, src, n * es);
+    return SCWP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+scwp_status scwp_get_table(scwp_ctx* ctx, int32_t patch_id, int32_t table, void* dst, size_t bytes) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "patch_id");
+    const PatchHost* P = ctx->patches[patch_id];
+    s = copy_table(P->T, &P->carry, table, dst, bytes, nullptr);
+    if (s != SCWP_OK) return fail(ctx, s, "table id or size");
+    return SCWP_OK;
+}
+
+scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_desc* pdesc, double dt,
+                            int32_t table, void* dst, size_t bytes, int64_t* count) {
+    std::string why;
+    if (check_spectrum_desc(sdesc, why) != SCWP_OK || check_patch_desc(pdesc, why) != SCWP_OK)
+        return SCWP_E_INVALID;
+    if (!(dt > 0) || table == SCWP_TAB_CARRY) return SCWP_E_INVALID;
+    SpectrumModel sm;
+    model_from_desc(*sdesc, sm);
+    std::vector<double> edges;
+    if (sdesc->bucket_edges) edges.assign(sdesc->bucket_edges, sdesc->bucket_edges + sdesc->n_buckets + 1);
+    PatchTablesHost T;
+    build_tables(*sdesc, edges, *pdesc, sm, T);
+    T.set_dt(dt);
+    return copy_table(T, nullptr, table, dst, bytes, count);
+}
+
+scwp_status scwp_get_particles(scwp_ctx* ctx, int32_t patch_id, int32_t* x, int32_t* y, uint32_t* bd,
+                               int64_t cap, int64_t* n) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (patch_id < 0 || patch_id >= (int)ctx->patches.size() || !n) return fail(ctx, SCWP_E_INVALID, "args");
+    const PatchDev& D = ctx->patches[patch_id]->dev;
+    int32_t cnt[2];
+    CU(cudaMemcpyAsync(cnt, D.count, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    *n = cnt[0];
+    const size_t m = (size_t)std::min<int64_t>(cap, cnt[0]);
+    if (m && x) CU(cudaMemcpyAsync(x, D.x[D.cur], m * 4, cudaMemcpyDeviceToHost, ctx->st));
+    if (m && y) CU(cudaMemcpyAsync(y, D.y[D.cur], m * 4, cudaMemcpyDeviceToHost, ctx->st));
+    if (m && bd) CU(cudaMemcpyAsync(bd, D.bd[D.cur], m * 4, cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return SCWP_OK;
+}
+
+scwp_status scwp_set_particles(scwp_ctx* ctx, int32_t patch_id, const int32_t* x, const int32_t* y,
+                               const uint32_t* bd, int64_t n) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (patch_id < 0 || patch_id >= (int)ctx->patches.size() || n < 0) return fail(ctx, SCWP_E_INVALID, "args");
+    PatchHost* P = ctx->patches[patch_id];
+    PatchDev& D = P->dev;
+    if (n > D.cap) return fail(ctx, SCWP_E_INVALID, "n exceeds capacity");
+    if (n > 0 && (!x || !y || !bd)) return fail(ctx, SCWP_E_INVALID, "null arrays");
+    const int ndirs = P->T.nth + (D.emitter ? kWakeDirs : 0);
+    for (int64_t i = 0; i < n; ++i)
+        if ((int)(bd[i] >> 16) >= P->T.nb || (int)(bd[i] & 0xFFFFu) >= ndirs)
+            return fail(ctx, SCWP_E_INVALID, "bucket or direction out of range");
+    int32_t cnt[2] = {(int32_t)n, (int32_t)n};
+    if (n) {
+        CU(cudaMemcpyAsync(D.x[D.cur], x, n * 4, cudaMemcpyHostToDevice, ctx->st));
+        CU(cudaMemcpyAsync(D.y[D.cur], y, n * 4, cudaMemcpyHostToDevice, ctx->st));
+        CU(cudaMemcpyAsync(D.bd[D.cur], bd, n * 4, cudaMemcpyHostToDevice, ctx->st));
+    }
+    CU(cudaMemcpyAsync(D.count, cnt, sizeof(cnt), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    return SCWP_OK;
+}
+
+scwp_status scwp_get_bins(scwp_ctx* ctx, int32_t patch_id, uint32_t* counts, uint32_t* offsets,
+                          uint32_t* entries, int64_t entries_cap, int64_t* n_entries) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
+    const PatchDev& D = ctx->patches[patch_id]->dev;
+    std::vector<uint32_t> off((size_t)D.total_bins + 1);
+    CU(cudaMemcpyAsync(off.data(), D.offsets, off.size() * 4, cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    const int64_t nv = off[D.total_bins];
+    if (n_entries) *n_entries = nv;
+    if (offsets) memcpy(offsets, off.data(), off.size() * 4);
+    if (counts)
+        for (int k = 0; k < D.total_bins; ++k) counts[k] = off[k + 1] - off[k];
+    if (entries && nv > 0) {
+        const int src = ((D.key_bits + 7) / 8) & 1;
+        const size_t m = (size_t)std::min<int64_t>(nv, entries_cap);
+        CU(cudaMemcpyAsync(entries, D.vals[src], m * 4, cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    return SCWP_OK;
+}
+
+scwp_status scwp_set_timing(scwp_ctx* ctx, int32_t enable) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (enable && ctx->ring.empty()) {
+        ctx->ring.resize(kTimingRing);
+        for (FrameEvents& f : ctx->ring)
+            for (int k = 0; k < 6; ++k) CU(cudaEventCreate(&f.e[k]));
+    }
+    if (!enable && (s = drain_ring(ctx)) != SCWP_OK) return s;
+    ctx->timing = enable != 0;
+    return SCWP_OK;
+}
+
+scwp_status scwp_timing_read(scwp_ctx* ctx, double ms_sum[4], int64_t* frames) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if ((s = drain_ring(ctx)) != SCWP_OK) return s;
+    for (int k = 0; k < 4; ++k) {
+        if (ms_sum) ms_sum[k] = ctx->ms_sum[k];
+        ctx->ms_sum[k] = 0;
+    }
+    if (frames) *frames = ctx->timed_frames;
+    ctx->timed_frames = 0;
+    return SCWP_OK;
+}
+
+void scwp_destroy(scwp_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->st || ctx->side) {
+        cudaStreamSynchronize(ctx->st);
+        if (ctx->side) cudaStreamSynchronize(ctx->side);
+    }
+    cudaGetLastError();
+    for (FrameEvents& f : ctx->ring)
+        for (int k = 0; k < 6; ++k)
+            if (f.e[k]) cudaEventDestroy(f.e[k]);
+    for (PatchHost* P : ctx->patches) delete P;
+    dfree_all(ctx);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

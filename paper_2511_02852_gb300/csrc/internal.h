@@ -1,0 +1,112 @@
+// Internal interfaces between the C ABI layer (api.cu) and the sm_103a
+// kernels of the hybrid ocean.  Nothing here crosses the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace scwp {
+
+constexpr int kMaxBuckets = 64;
+constexpr int kMaxSegments = 2 * kMaxBuckets + 2;
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+// Per-bucket constants read by the binning and synthesis kernels.
+struct BucketDev {
+    int32_t R;      // kernel half-width, Q16.16 cells
+    float invR;     // 1 / R (float)
+    int32_t C;      // bin side, Q16.16 cells
+    int32_t nbx, nby, base;  // bin grid and first key
+    int32_t pad0, pad1;
+};
+
+// Device state of one patch.
+struct PatchDev {
+    int W = 0, H = 0, nb = 0, nth = 0, cap = 0;
+    int emitter = 0;
+    int total_bins = 0;
+    float wake_amp = 0.f;
+    int cur = 0;                          // which SoA buffer is live
+    int32_t* x[2] = {nullptr, nullptr};
+    int32_t* y[2] = {nullptr, nullptr};
+    uint32_t* bd[2] = {nullptr, nullptr}; // bucket << 16 | direction
+    int32_t* count = nullptr;             // [0] live, [1] live after compaction
+    uint8_t* flags = nullptr;             // [cap] alive flags
+    uint32_t* blk = nullptr;              // [nblk_c + 1] compaction block sums
+    int nblk_c = 0;
+    int4* vq = nullptr;                   // [nb*nth (+4096)] (vx, vy, qx, qy)
+    int16_t* dirlist = nullptr;           // [nb][2][nth] valid directions per edge pair
+    float* amp = nullptr;                 // [nb*nth]
+    BucketDev* bk = nullptr;              // [nb]
+    uint32_t* keys[2] = {nullptr, nullptr};  // [2 cap] bin keys (sort ping-pong)
+    uint32_t* vals[2] = {nullptr, nullptr};  // [2 cap] bump ids
+    uint32_t* hist = nullptr;             // [256 * nblk_s]
+    int nblk_s = 0;
+    int key_bits = 16;
+    uint32_t* offsets = nullptr;          // [total_bins + 1]
+    int4* rec = nullptr;                  // [2 cap] bump records in bin order
+    float* out = nullptr;                 // [3][H][W] blended maps
+    unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..] live per bucket
+    float* layers = nullptr;              // layered variant scratch (lazy)
+    size_t layers_bytes = 0;
+};
+
+// One spawn segment of a frame's injection (Sec. 3.3 Eqs. 15-17 / Sec. 4.3).
+struct Segment {
+    int32_t bucket;
+    int32_t s;       // 0, 1: edge pairs; 2: wake arm
+    int32_t count;   // particles in the segment
+    int32_t first;   // prefix of counts
+    int32_t ndir;    // edge: number of valid directions; wake: rate
+    int32_t arm;     // wake: arm index (0: +, 1: -)
+    int32_t wake_a;  // wake: direction grid index
+    int32_t vn;      // unused padding
+};
+
+struct InjectParams {
+    int nseg;
+    int total;
+    uint32_t frame;
+    uint32_t patch;
+    uint64_t seed;
+    int W, H, nth;
+    // wake (float64 reading: rint((P + rho*(ca,sa) +- tau*(-sa,ca)) Q))
+    double Px, Py, rho;
+    double ca[2], sa[2];
+    Segment seg[kMaxSegments];
+};
+
+struct SynthParams {
+    int W, H, nb;
+    float lam_half;         // lambda_c / 2
+    float band;             // blend band in cells
+    float fx0, fy0, fsx;    // background coords: f = f0 + i * fs (grid units)
+    int N;                  // background grid size
+    const float* bg;        // [3][N][N]
+};
+
+// Every launcher reports how many kernels it enqueued (process-wide counter,
+// read by the ABI layer around each call).
+void count_launches(int n);
+long long launches_total();
+
+// ---- launchers (each enqueues on `st`) --------------------------------------
+cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st);
+cudaError_t launch_compact(const PatchDev& p, cudaStream_t st);
+cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st);
+cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
+cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
+cudaError_t launch_layered(PatchDev& p, const SynthParams& sp, cudaStream_t st);
+
+struct BgDev {
+    int N = 0;
+    const float2* h0 = nullptr;   // [N][N]
+    const double* omega = nullptr;// [N][N]
+    const float2* tw = nullptr;   // [N] e^{2 pi i m / N}
+    float2* G = nullptr;          // [2][N][N] row-pass output
+    float* out = nullptr;         // [3][N][N] h, Dx, Dy
+    float lam = 1.f, dk = 0.f;
+};
+cudaError_t launch_background(const BgDev& b, double t, cudaStream_t st);
+
+}  // namespace scwp

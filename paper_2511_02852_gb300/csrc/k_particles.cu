@@ -1,0 +1,482 @@
+// Wave-particle state kernels of the hybrid ocean (sm_103a):
+//   advection + expiry + stable compaction  (Sec. 3.1 Lagrangian propagation,
+//                                            Sec. 4.1 WP updates),
+//   boundary injection and wake emission     (Sec. 3.3 Eqs. 15-17, Sec. 4.3),
+//   per-bucket integer binning               (Sec. 4.2: the particles of a
+//                                            bucket share radius and kernel).
+// All particle state is integer (Q16.16 cell units); every decision is an
+// integer test, so the state is bit-exact against any other implementation of
+// the same rules.  No float atomics anywhere; integer atomics only for counts.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "philox.h"
+
+namespace scwp {
+namespace {
+
+constexpr int kTpb = 256;
+constexpr int kItems = 4;                 // per thread in the compaction tiles
+constexpr int kTileC = kTpb * kItems;     // 1024 particles per compaction block
+constexpr int kSortItems = 16;
+constexpr int kTileS = kTpb * kSortItems; // 4096 keys per sort block
+constexpr int32_t kQi = 65536, kHalfi = 32768;
+
+// Texel centres of [0, n) strictly inside (C - R, C + R) along one axis.
+__device__ __forceinline__ int span_count(int32_t C, int32_t R, int n) {
+    int64_t lo = (((int64_t)C - R - kHalfi) >> 16) + 1;
+    int64_t hi = ((int64_t)C + R - kHalfi - 1) >> 16;
+    if (lo < 0) lo = 0;
+    if (hi > n - 1) hi = n - 1;
+    return hi >= lo ? (int)(hi - lo + 1) : 0;
+}
+
+__device__ __forceinline__ int4 lookup_vq(const PatchDev& p, uint32_t bd) {
+    const int b = (int)(bd >> 16), j = (int)(bd & 0xFFFFu);
+    const int idx = j < p.nth ? b * p.nth + j : p.nb * p.nth + (j - p.nth);
+    return p.vq[idx];
+}
+
+__device__ __forceinline__ float lookup_amp(const PatchDev& p, uint32_t bd) {
+    const int b = (int)(bd >> 16), j = (int)(bd & 0xFFFFu);
+    return j < p.nth ? p.amp[b * p.nth + j] : p.wake_amp;
+}
+
+// Block-wide exclusive scan of one value per thread (kTpb threads).
+__device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kTpb / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kTpb / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[kTpb / 32 - 1];
+    const uint32_t before = warp ? s_warp[warp - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+// ---- a3: advect, expire ------------------------------------------------------
+__global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
+    __shared__ uint32_t s_warp[kTpb / 32];
+    const int n = p.count[0];
+    const int base = blockIdx.x * kTileC;
+    int32_t* X = p.x[p.cur];
+    int32_t* Y = p.y[p.cur];
+    const uint32_t* BD = p.bd[p.cur];
+    uint32_t alive_cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int i = base + threadIdx.x * kItems + k;
+        if (i < n) {
+            const uint32_t bd = BD[i];
+            const int4 vq = lookup_vq(p, bd);
+            const int32_t x = X[i] + vq.x, y = Y[i] + vq.y;
+            X[i] = x;
+            Y[i] = y;
+            const int32_t R = p.bk[bd >> 16].R;
+            const bool a = (span_count(x, R, p.W) > 0 && span_count(y, R, p.H) > 0) ||
+                           (span_count(x - vq.z, R, p.W) > 0 && span_count(y - vq.w, R, p.H) > 0);
+            p.flags[i] = a ? 1 : 0;
+            alive_cnt += a ? 1u : 0u;
+        }
+    }
+    uint32_t total;
+    block_exscan(alive_cnt, s_warp, total);
+    if (threadIdx.x == 0) p.blk[blockIdx.x] = total;
+}
+
+// exclusive scan of the per-block survivor counts (one block, in place)
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blk, int nblk, int32_t* count) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int start = 0; start < nblk; start += 1024) {
+        const int i = start + threadIdx.x;
+        const uint32_t v = i < nblk ? blk[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_warp[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t carry = s_carry;
+        const uint32_t excl = carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
+        if (i < nblk) blk[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        count[0] = (int32_t)s_carry;
+        count[1] = (int32_t)s_carry;
+    }
+}
+
+__global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
+    __shared__ uint32_t s_warp[kTpb / 32];
+    const int base = blockIdx.x * kTileC;
+    const int32_t* Xs = p.x[p.cur];
+    const int32_t* Ys = p.y[p.cur];
+    const uint32_t* Bs = p.bd[p.cur];
+    int32_t* Xd = p.x[1 - p.cur];
+    int32_t* Yd = p.y[1 - p.cur];
+    uint32_t* Bd = p.bd[1 - p.cur];
+    // flags past the pre-compaction live count are zero (cleared after every
+    // compaction), so only this frame's survivors are moved.
+    uint8_t f[kItems];
+    uint32_t mine = 0;
+    const uint32_t blk_off = p.blk[blockIdx.x];
+    const uint32_t blk_end = (blockIdx.x + 1 < (unsigned)p.nblk_c) ? p.blk[blockIdx.x + 1]
+                                                                   : (uint32_t)p.count[1];
+    const uint32_t blk_cnt = blk_end - blk_off;
+    if (blk_cnt == 0) return;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int i = base + threadIdx.x * kItems + k;
+        f[k] = (i < p.cap) ? p.flags[i] : 0;
+        mine += f[k];
+    }
+    uint32_t total;
+    uint32_t off = block_exscan(mine, s_warp, total) + blk_off;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        if (f[k]) {
+            const int i = base + threadIdx.x * kItems + k;
+            Xd[off] = Xs[i];
+            Yd[off] = Ys[i];
+            Bd[off] = Bs[i];
+            ++off;
+        }
+    }
+}
+
+__global__ void k_clear_flags(uint8_t* flags, int cap) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+        flags[i] = 0;
+}
+
+// ---- a4 + a5: injection and wake emission -------------------------------------
+__global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) {
+    const int base = p.count[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t want = (int64_t)base + ip.total;
+        p.count[0] = (int32_t)(want > p.cap ? p.cap : want);
+        if (want > p.cap) atomicOr(&p.stats[2], (unsigned long long)kErrCapacity);
+    }
+    int32_t* X = p.x[p.cur];
+    int32_t* Y = p.y[p.cur];
+    uint32_t* BD = p.bd[p.cur];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ip.total; e += gridDim.x * blockDim.x) {
+        const int64_t idx = (int64_t)base + e;
+        if (idx >= p.cap) break;
+        int sidx = 0;
+        while (sidx + 1 < ip.nseg && ip.seg[sidx + 1].first <= e) ++sidx;
+        const Segment sg = ip.seg[sidx];
+        const int le = e - sg.first;
+        int32_t x, y;
+        uint32_t bd;
+        if (sg.s < 2) {
+            const int g = le / sg.ndir, kk = le - g * sg.ndir;
+            const int j = p.dirlist[(sg.bucket * 2 + sg.s) * p.nth + kk];
+            const uint32_t ord = (uint32_t)(g * ip.nth + j);
+            const U4 u = philox4x32_10(ip.frame, ip.patch, (uint32_t)sg.bucket | ((uint32_t)sg.s << 16),
+                                       ord, ip.seed);
+            const int4 vq = p.vq[sg.bucket * p.nth + j];
+            const int32_t vn = sg.s == 0 ? vq.x : vq.y;
+            const uint64_t avn = (uint64_t)(vn < 0 ? -(int64_t)vn : (int64_t)vn);
+            const uint64_t len = (uint64_t)(sg.s == 0 ? ip.H : ip.W) * (uint64_t)kQi;
+            const int32_t along = (int32_t)(((uint64_t)u.x * len) >> 32);
+            const int32_t off = (int32_t)(((uint64_t)u.y * avn) >> 32);
+            const int32_t far = (sg.s == 0 ? ip.W : ip.H) * kQi;
+            const int32_t across = vn > 0 ? off : far - off;
+            x = sg.s == 0 ? across : along;
+            y = sg.s == 0 ? along : across;
+            bd = ((uint32_t)sg.bucket << 16) | (uint32_t)j;
+        } else {
+            const uint32_t ord = (uint32_t)(sg.arm * sg.ndir + le);
+            const U4 u = philox4x32_10(ip.frame, ip.patch, (uint32_t)sg.bucket | (2u << 16), ord, ip.seed);
+            const double ca = ip.ca[sg.arm], sa = ip.sa[sg.arm];
+            // tau = ((u 2^-32 - 1/2) 2) rho ; explicit rounding, no contraction
+            double tau = __dmul_rn(__dmul_rn(__dsub_rn(__dmul_rn((double)u.x, 0x1p-32), 0.5), 2.0), ip.rho);
+            const double fx = __dmul_rn(__dsub_rn(__dadd_rn(ip.Px, __dmul_rn(ip.rho, ca)), __dmul_rn(tau, sa)), 65536.0);
+            const double fy = __dmul_rn(__dadd_rn(__dadd_rn(ip.Py, __dmul_rn(ip.rho, sa)), __dmul_rn(tau, ca)), 65536.0);
+            x = (int32_t)__double2ll_rn(fx);
+            y = (int32_t)__double2ll_rn(fy);
+            bd = ((uint32_t)sg.bucket << 16) | (uint32_t)(ip.nth + sg.wake_a);
+        }
+        X[idx] = x;
+        Y[idx] = y;
+        BD[idx] = bd;
+    }
+}
+
+// ---- a6: binning ---------------------------------------------------------------
+__global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, uint32_t* vals) {
+    __shared__ unsigned long long s_ev[kTpb / 32];
+    __shared__ unsigned int s_bin[kTpb / 32];
+    __shared__ unsigned int s_live[kMaxBuckets];
+    for (int i = threadIdx.x; i < p.nb; i += blockDim.x) s_live[i] = 0;
+    __syncthreads();
+    const int n = p.count[0];
+    const int32_t* X = p.x[p.cur];
+    const int32_t* Y = p.y[p.cur];
+    const uint32_t* BD = p.bd[p.cur];
+    unsigned long long ev = 0;
+    unsigned int binned = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t bd = BD[i];
+        const int b = (int)(bd >> 16);
+        const int4 vq = lookup_vq(p, bd);
+        const BucketDev bk = p.bk[b];
+        atomicAdd(&s_live[b], 1u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int32_t cx = k ? X[i] - vq.z : X[i];
+            const int32_t cy = k ? Y[i] - vq.w : Y[i];
+            const int nx = span_count(cx, bk.R, p.W), ny = span_count(cy, bk.R, p.H);
+            uint32_t key = (uint32_t)p.total_bins;
+            if (nx > 0 && ny > 0) {
+                const int bx = (int)(((int64_t)cx + bk.R) / bk.C);
+                const int by = (int)(((int64_t)cy + bk.R) / bk.C);
+                key = (uint32_t)(bk.base + by * bk.nbx + bx);
+                ev += (unsigned long long)nx * (unsigned long long)ny;
+                ++binned;
+            }
+            keys[2 * i + k] = key;
+            vals[2 * i + k] = (uint32_t)(2 * i + k);
+        }
+    }
+    // block reductions (integers: order-independent)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_down_sync(0xffffffffu, ev, o);
+        binned += __shfl_down_sync(0xffffffffu, binned, o);
+    }
+    if (lane == 0) {
+        s_ev[warp] = ev;
+        s_bin[warp] = binned;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long e = 0;
+        unsigned long long bb = 0;
+        for (int w = 0; w < kTpb / 32; ++w) {
+            e += s_ev[w];
+            bb += s_bin[w];
+        }
+        if (e) atomicAdd(&p.stats[0], e);
+        if (bb) atomicAdd(&p.stats[1], bb);
+    }
+    for (int i = threadIdx.x; i < p.nb; i += blockDim.x)
+        if (s_live[i]) atomicAdd(&p.stats[3 + i], (unsigned long long)s_live[i]);
+}
+
+// LSD radix sort pass, 8-bit digit, stable.  Per-block digit histograms.
+__global__ void __launch_bounds__(kTpb) k_radix_hist(const uint32_t* keys, const int32_t* count,
+                                                     int shift, uint32_t* hist, int nblk) {
+    __shared__ uint32_t s_h[256];
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const int n = 2 * count[0];
+    const int base = blockIdx.x * kTileS;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int i = base + k * kTpb + threadIdx.x;
+        if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblk + blockIdx.x] = s_h[threadIdx.x];
+}
+
+// exclusive scan of the digit-major histogram (one block)
+__global__ void __launch_bounds__(1024) k_scan_hist(uint32_t* h, int n) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int start = 0; start < n; start += 1024) {
+        const int i = start + threadIdx.x;
+        const uint32_t v = i < n ? h[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_warp[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t carry = s_carry;
+        if (i < n) h[i] = carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
+        __syncthreads();
+    }
+}
+
+// stable scatter: items ranked in index order within the block, round by round
+__global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, const uint32_t* vin,
+                                                        uint32_t* kout, uint32_t* vout,
+                                                        const int32_t* count, int shift,
+                                                        const uint32_t* hist, int nblk) {
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wc[kTpb / 32][256];
+    const int n = 2 * count[0];
+    const int base = blockIdx.x * kTileS;
+    s_base[threadIdx.x] = hist[threadIdx.x * nblk + blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int i = base + k * kTpb + threadIdx.x;
+        const bool act = i < n;
+        uint32_t key = 0, val = 0, d = 0x100u + (uint32_t)warp;  // inactive sentinel
+        if (act) {
+            key = kin[i];
+            val = vin[i];
+            d = (key >> shift) & 255u;
+        }
+#pragma unroll
+        for (int w = 0; w < kTpb / 32; ++w) s_wc[w][threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (act && rank == 0) s_wc[warp][d] = __popc(peers);
+        __syncthreads();
+        if (act) {
+            uint32_t off = s_base[d] + rank;
+            for (int w = 0; w < warp; ++w) off += s_wc[w][d];
+            kout[off] = key;
+            vout[off] = val;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+#pragma unroll
+        for (int w = 0; w < kTpb / 32; ++w) add += s_wc[w][threadIdx.x];
+        s_base[threadIdx.x] += add;
+        __syncthreads();
+    }
+}
+
+// offsets[k] = first sorted position with key >= k (k = 0..total_bins)
+__global__ void k_bin_offsets(const uint32_t* keys, const int32_t* count, uint32_t* offsets,
+                              int total_bins) {
+    const int n = 2 * count[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= total_bins; k += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (keys[mid] < (uint32_t)k) lo = mid + 1; else hi = mid;
+        }
+        offsets[k] = (uint32_t)lo;
+    }
+}
+
+// bump records in bin order: (X, Y, signed amplitude bits, bump id)
+__global__ void k_records(PatchDev p, const uint32_t* vals) {
+    const int nvalid = (int)p.offsets[p.total_bins];
+    const int32_t* X = p.x[p.cur];
+    const int32_t* Y = p.y[p.cur];
+    const uint32_t* BD = p.bd[p.cur];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nvalid; e += gridDim.x * blockDim.x) {
+        const uint32_t id = vals[e];
+        const int i = (int)(id >> 1);
+        const bool trough = id & 1u;
+        const uint32_t bd = BD[i];
+        const int4 vq = lookup_vq(p, bd);
+        const float A = lookup_amp(p, bd);
+        int4 r;
+        r.x = trough ? X[i] - vq.z : X[i];
+        r.y = trough ? Y[i] - vq.w : Y[i];
+        r.z = __float_as_int(trough ? -A : A);
+        r.w = (int)id;
+        p.rec[e] = r;
+    }
+}
+
+}  // namespace
+
+// ---- launchers -------------------------------------------------------------------
+cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st) {
+    k_advect_flag<<<p.nblk_c, kTpb, 0, st>>>(p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const PatchDev& p, cudaStream_t st) {
+    k_scan_blocks<<<1, 1024, 0, st>>>(p.blk, p.nblk_c, p.count);
+    k_compact_scatter<<<p.nblk_c, kTpb, 0, st>>>(p);
+    k_clear_flags<<<(p.cap + 1023) / 1024 < 1024 ? (p.cap + 1023) / 1024 : 1024, 1024, 0, st>>>(p.flags, p.cap);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st) {
+    int blocks = (ip.total + kTpb - 1) / kTpb;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    k_inject<<<blocks, kTpb, 0, st>>>(p, ip);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
+    int kb = (p.cap + kTpb - 1) / kTpb;
+    if (kb > 152 * 8) kb = 152 * 8;
+    if (kb < 1) kb = 1;
+    k_bin_keys<<<kb, kTpb, 0, st>>>(p, p.keys[0], p.vals[0]);
+    const int passes = (p.key_bits + 7) / 8;
+    int src = 0;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = 8 * ps;
+        k_radix_hist<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.count, shift, p.hist, p.nblk_s);
+        k_scan_hist<<<1, 1024, 0, st>>>(p.hist, 256 * p.nblk_s);
+        k_radix_scatter<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.vals[src], p.keys[1 - src],
+                                                   p.vals[1 - src], p.count, shift, p.hist, p.nblk_s);
+        src = 1 - src;
+    }
+    int ob = (p.total_bins + 1 + kTpb - 1) / kTpb;
+    k_bin_offsets<<<ob, kTpb, 0, st>>>(p.keys[src], p.count, p.offsets, p.total_bins);
+    int rb = (2 * p.cap + kTpb - 1) / kTpb;
+    if (rb > 152 * 16) rb = 152 * 16;
+    k_records<<<rb, kTpb, 0, st>>>(p, p.vals[src]);
+    count_launches(3 + 3 * passes);
+    return cudaGetLastError();
+}
+
+int sorted_buffer_index(const PatchDev& p) { return ((p.key_bits + 7) / 8) & 1; }
+
+}  // namespace scwp
