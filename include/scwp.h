@@ -244,6 +244,29 @@ scwp_status scwp_timing_read(scwp_ctx* ctx, double ms_sum[4], int64_t* frames);
 scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_desc* pdesc,
                             double dt, int32_t table, void* dst, size_t bytes, int64_t* count);
 
+/* Background step without any device allocation, for callers that cannot
+ * call cudaMalloc (code in host callbacks or real-time threads where an
+ * allocation would synchronise the device, runtimes that only hand out
+ * pre-registered buffers, plug-ins whose host owns every allocation).  The
+ * paper has no counterpart: this is a deployment variant of the background
+ * update of scwp_step (spectrum evolution + inverse 2-D FFT).
+ *   h0     device, float32 complex interleaved [n][n] (FFT-natural order)
+ *   omega  device, float64 [n][n] dispersion w(k)
+ *   n      grid size: power of two, 8 <= n <= 512; larger grids are refused
+ *          with SCWP_E_INVALID (the scratch is sized for 512 x 512)
+ *   out    device, float32 [3][n][n]: h, Dx, Dy at x_j = j fft_L / n
+ *   stream cudaStream_t (NULL: the legacy stream); asynchronous
+ * The scratch (4 MiB + 4 KiB) is one static __device__ array of the library:
+ * every GPU that loads the library holds it until the process exits, and
+ * every call shares it, so calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The first call
+ * on a device does a one-time set-up (looks up the array's address and
+ * copies the twiddle table with a synchronous cudaMemcpy): make that first
+ * call before any stream capture.  Returns SCWP_E_INVALID on bad arguments,
+ * SCWP_E_CUDA if the set-up or a launch fails. */
+scwp_status scwp_background_noalloc(const float* h0, const double* omega, int32_t n, double fft_L,
+                                    double choppiness, double t, float* out, void* stream);
+
 /* Number of kernels this context has enqueued since creation (every
  * kernel of scwp_step / scwp_resynthesize counts once). */
 scwp_status scwp_launch_count(scwp_ctx* ctx, int64_t* n);

@@ -1,0 +1,106 @@
+// scwp_background_noalloc: the background FFT step (spectrum update + inverse
+// 2-D FFT) for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc at all: code running inside a host
+// callback or a real-time render/audio thread where an allocation would
+// synchronise the device, runtimes that hand out only pre-registered
+// buffers, or plug-ins whose host application owns every allocation.  This
+// entry point lets them evolve and transform a background spectrum they
+// already hold in device memory.  Its scratch (the row-pass intermediate and
+// the twiddle table) lives in one file-scope __device__ array below, sized
+// for grids up to kNoAllocMaxN x kNoAllocMaxN; every GPU that loads this
+// library holds that array (4 MiB + 4 KiB) until the process exits.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "../../include/scwp.h"
+#include "internal.h"
+
+namespace {
+
+constexpr int kNoAllocMaxN = 512;
+constexpr size_t kScratchElems = 2 * (size_t)kNoAllocMaxN * kNoAllocMaxN + kNoAllocMaxN;
+
+// [0, 2 N^2): row-pass output of the two transformed planes;
+// [2 N^2, 2 N^2 + N): e^{2 pi i m / N} for N = kNoAllocMaxN.
+static __device__ __align__(256) float2 g_noalloc_scratch[kScratchElems];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+float2* g_scratch_ptr[kMaxDevices] = {};
+
+// One-time set-up per device (the caller's current device): look up the
+// array's device address and fill the twiddle table.  Runs on the first call
+// on that device; the copy below is a synchronous cudaMemcpy, so that first
+// call must not happen inside a stream capture.
+cudaError_t setup_device(int dev, float2** out) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_ptr[dev]) {
+        *out = g_scratch_ptr[dev];
+        return cudaSuccess;
+    }
+    float2* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    static float2 tw[kNoAllocMaxN];   // host staging, no heap allocation
+    for (int m = 0; m < kNoAllocMaxN; ++m) {
+        const double a = 2.0 * M_PI * m / kNoAllocMaxN;
+        tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    e = cudaMemcpy(ptr + 2 * (size_t)kNoAllocMaxN * kNoAllocMaxN, tw,
+                   kNoAllocMaxN * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = ptr;
+    *out = ptr;
+    return cudaSuccess;
+}
+
+// twiddles of a smaller power-of-two grid: every (N_max / N)-th entry
+__global__ void k_gather_twiddles(const float2* full, float2* dst, int n, int stride) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+        dst[m] = full[m * stride];
+}
+
+}  // namespace
+
+extern "C" scwp_status scwp_background_noalloc(const float* h0, const double* omega, int32_t n,
+                                               double fft_L, double choppiness, double t, float* out,
+                                               void* stream) {
+    if (!h0 || !omega || !out || !(fft_L > 0)) return SCWP_E_INVALID;
+    if (n < 8 || n > kNoAllocMaxN || (n & (n - 1)) != 0) return SCWP_E_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return SCWP_E_CUDA;
+    }
+    float2* scratch = nullptr;
+    if (setup_device(dev, &scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return SCWP_E_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = (size_t)kNoAllocMaxN * kNoAllocMaxN;
+    const float2* full_tw = scratch + 2 * nn;
+    // the row-pass buffer holds 2 n^2 values; for n < N_max its tail keeps
+    // this grid's twiddles (written before, read by, the FFT of this call)
+    const float2* tw = full_tw;
+    if (n < kNoAllocMaxN) {
+        float2* small = scratch + 2 * (size_t)n * n;
+        k_gather_twiddles<<<1, 256, 0, st>>>(full_tw, small, n, kNoAllocMaxN / n);
+        tw = small;
+    }
+    scwp::BgDev bg;
+    bg.N = n;
+    bg.h0 = reinterpret_cast<const float2*>(h0);
+    bg.omega = omega;
+    bg.tw = tw;
+    bg.G = scratch;
+    bg.out = out;
+    bg.lam = (float)choppiness;
+    bg.dk = (float)(2.0 * M_PI / fft_L);
+    if (scwp::launch_background(bg, t, st) != cudaSuccess) return SCWP_E_CUDA;
+    return SCWP_OK;
+}

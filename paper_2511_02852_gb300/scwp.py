@@ -93,6 +93,8 @@ EXPORTS = {
     "scwp_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "scwp_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "scwp_background_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                          C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "scwp_last_error": (C.c_char_p, [C.c_void_p]),
     "scwp_version": (C.c_char_p, []),
     "scwp_destroy": (None, [C.c_void_p]),
