@@ -277,8 +277,24 @@ scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P) {
 scwp_status synthesize(scwp_ctx* ctx, int mode) {
     for (PatchHost* P : ctx->patches) {
         const SynthParams sp = synth_params(ctx, *P);
-        if (mode == SCWP_SYNTH_LAYERED) CU(launch_layered(P->dev, sp, ctx->st));
-        else CU(launch_synth_gather(P->dev, sp, ctx->st));
+        if (mode == SCWP_SYNTH_LAYERED) {
+            PatchDev& D = P->dev;
+            const size_t need = layered_scratch_bytes(D, P->T.R.data());
+            if (D.layers_bytes < need) {
+                // lazily sized on the first layered synthesis of this patch
+                D.layers = (float*)dalloc(ctx, need);
+                if (!D.layers) return fail(ctx, SCWP_E_NOMEM, "layered scratch");
+                D.layers_bytes = need;
+            }
+            std::vector<int> base(P->T.nb), nbins(P->T.nb);
+            for (int i = 0; i < P->T.nb; ++i) {
+                base[i] = P->bk[i].base;
+                nbins[i] = P->bk[i].nbx * P->bk[i].nby;
+            }
+            CU(launch_layered(D, sp, P->T.R.data(), base.data(), nbins.data(), ctx->st));
+        } else {
+            CU(launch_synth_gather(P->dev, sp, ctx->st));
+        }
     }
     return SCWP_OK;
 }
@@ -395,12 +411,27 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     D.dirlist = (int16_t*)dalloc(ctx, (size_t)T.nb * 2 * T.nth * sizeof(int16_t));
     D.amp = (float*)dalloc(ctx, ng * sizeof(float));
     D.bk = (BucketDev*)dalloc(ctx, T.nb * sizeof(BucketDev));
+    D.rot = (float2*)dalloc(ctx, (size_t)T.nb * kRotN * sizeof(float2));
     D.hist = (uint32_t*)dalloc(ctx, (size_t)256 * D.nblk_s * 4);
     D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
     D.rec = (int4*)dalloc(ctx, 2 * cap * sizeof(int4));
     D.out = (float*)dalloc(ctx, (size_t)3 * T.W * T.H * sizeof(float));
+    {
+        // split the synthesis into bucket groups so that a frame has enough
+        // CTAs to fill every SM several times over (about 4 waves of 3 CTAs
+        // per SM on 152 SMs); each group writes its own partial sums
+        const int tiles = ((T.W + 63) / 64) * ((T.H + 63) / 64);
+        int G = (4 * 152 * 3 + tiles - 1) / tiles;
+        if (G > T.nb) G = T.nb;
+        if (G < 1) G = 1;
+        D.groups = G;
+        if (G > 1) {
+            D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
+            ok = ok && D.partial;
+        }
+    }
     D.stats = (unsigned long long*)dalloc(ctx, (3 + (size_t)T.nb) * sizeof(unsigned long long));
-    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.hist &&
+    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.hist &&
          D.offsets && D.rec && D.out && D.stats;
     if (!ok) {
         delete P;
@@ -442,6 +473,14 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     int32_t counts[2] = {n0, n0};
     CU(cudaMemcpyAsync(D.amp, ampf.data(), ng * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(D.bk, P->bk.data(), T.nb * sizeof(BucketDev), cudaMemcpyHostToDevice, ctx->st));
+    // per-bucket phase steps of n texels: e^{i pi n Q / R_i}, n < kRotN
+    std::vector<float2> rot((size_t)T.nb * kRotN);
+    for (int i = 0; i < T.nb; ++i)
+        for (int n = 0; n < kRotN; ++n) {
+            const double a = M_PI * (double)n * (double)kQ / (double)T.R[i];
+            rot[(size_t)i * kRotN + n] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    CU(cudaMemcpyAsync(D.rot, rot.data(), rot.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
     CU(cudaMemsetAsync(D.stats, 0, (3 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));

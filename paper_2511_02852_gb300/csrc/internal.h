@@ -7,6 +7,7 @@
 namespace scwp {
 
 constexpr int kMaxBuckets = 64;
+constexpr int kRotN = 128;          // per-bucket phase-rotation table length
 constexpr int kMaxSegments = 2 * kMaxBuckets + 2;
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
@@ -38,6 +39,7 @@ struct PatchDev {
     int16_t* dirlist = nullptr;           // [nb][2][nth] valid directions per edge pair
     float* amp = nullptr;                 // [nb*nth]
     BucketDev* bk = nullptr;              // [nb]
+    float2* rot = nullptr;                // [nb][kRotN] (cos, sin)(pi n Q / R_i)
     uint32_t* keys[2] = {nullptr, nullptr};  // [2 cap] bin keys (sort ping-pong)
     uint32_t* vals[2] = {nullptr, nullptr};  // [2 cap] bump ids
     uint32_t* hist = nullptr;             // [256 * nblk_s]
@@ -46,6 +48,8 @@ struct PatchDev {
     uint32_t* offsets = nullptr;          // [total_bins + 1]
     int4* rec = nullptr;                  // [2 cap] bump records in bin order
     float* out = nullptr;                 // [3][H][W] blended maps
+    float* partial = nullptr;             // [groups][3][H][W] per-bucket-group sums (groups > 1)
+    int groups = 1;                       // bucket groups the synthesis is split into
     unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..] live per bucket
     float* layers = nullptr;              // layered variant scratch (lazy)
     size_t layers_bytes = 0;
@@ -96,7 +100,13 @@ cudaError_t launch_compact(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st);
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
-cudaError_t launch_layered(PatchDev& p, const SynthParams& sp, cudaStream_t st);
+// sum `groups` partial [3][H][W] planes at src (in order), blend, store to p.out
+cudaError_t launch_blend(const PatchDev& p, const SynthParams& sp, const float* src, int groups,
+                         cudaStream_t st);
+// layered variant: scratch (p.layers) must hold layered_scratch_bytes()
+size_t layered_scratch_bytes(const PatchDev& p, const int32_t* R_host);
+cudaError_t launch_layered(const PatchDev& p, const SynthParams& sp, const int32_t* R_host,
+                           const int* base_host, const int* nbins_host, cudaStream_t st);
 
 struct BgDev {
     int N = 0;

@@ -242,3 +242,31 @@ def test_rerun_is_deterministic():
             assert np.array_equal(u, v)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("make_cfg", [wl.tiny, wl.small_jonswap, wl.small_two_patches])
+def test_layered_variant_matches_oracle(make_cfg):
+    """Layer splat + separable x/y passes + layer sum (Sec. 4.2) against the
+    oracle's layered restatement, after a few frames."""
+    from paper_2511_02852_gb300 import scwp
+    from oracle.synth import blend, layered_maps
+    cfg = make_cfg()
+    sc = make(cfg)
+    orc = OracleScene(cfg)
+    for _ in range(3):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    sc.resynthesize(scwp.SYNTH_LAYERED)
+    bg = orc.background()
+    for p in range(len(cfg["patches"])):
+        ps = orc.patches[p]
+        bm = ps.bumps()
+        wp = layered_maps(ps.T.W, ps.T.H, bm, orc.lam, ps.T.nb, ps.T.R)
+        ref = blend(cfg["patches"][p], wp, bg, orc.L)
+        compare_maps(sc.maps(p), ref, orc.spec.Hs(), f"layered {cfg['name']} patch {p}")
+    # and the default path still reproduces the gather afterwards
+    sc.resynthesize(scwp.SYNTH_GATHER)
+    ref, _ = orc.patch_maps(0, bg)
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), "gather after layered")
+    sc.close()
+
