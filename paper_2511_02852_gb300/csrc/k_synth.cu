@@ -3,25 +3,29 @@
 // displacement from the kernel gradient, and the distance-weighted blend into
 // the FFT background.
 //
-// Tile gather.  One CTA (4 warps) owns a 64 x 64 texel tile and keeps its
-// h, Dx, Dy sums in registers (8 x 4 texels per thread).  For each bucket it walks the
-// integer bins that can reach the tile; the bump records of each bin row are
-// contiguous in memory and are staged into shared memory with bulk async
-// copies (cp.async.bulk, completion on an mbarrier), double-buffered so the
-// copy of the next chunk overlaps the arithmetic of the current one.
-//
-// The bump kernel is separable, K = k(u) k(v), k(u) = 1/2 (1 + cos(pi u/R)),
-// so for each staged bump the CTA evaluates k and sin once per tile column and
-// once per tile row (shared memory) — one accurate sincospi per bump and
-// axis at the tile's first texel, then the angle-addition rotation by the
-// bucket's per-texel phase step e^{i pi Q / R} (a 64-entry float64-built
-// table) — and each thread does the outer product:
-//   h  += (A k(v)) * k(u)                 Dx += (A k(v)) * (lam/2) sin(pi u/R)
-//   Dy += (A (lam/2) sin(pi v/R)) * k(u)
-// i.e. 3 FMAs per bump-texel.  A warp skips bumps whose support misses its
-// 32 x 32 sub-tile.  The epilogue applies the smoothstep blend weight and the
-// bilinear background sample and writes the three maps (no atomics).
+// Tile gather, warp-specialised.  One CTA owns a 64 x 64 texel tile (and one
+// group of its buckets) with six warps:
+//   * two producer warps walk the integer bins that can reach the tile, stage
+//     each chunk of 32 bump records into shared memory with a bulk async copy
+//     (cp.async.bulk, completion on an mbarrier), and turn it into the
+//     separable kernel factors of the tile: per bump one accurate sincospi
+//     per axis at the tile's first texel, then the angle-addition rotation by
+//     the bucket's per-texel phase step e^{i pi n Q / R} (a float64-built
+//     table), giving per column k(u), (lam/2) sin(pi u/R) and per row
+//     A k(v), A (lam/2) sin(pi v/R), plus a mask of the warps whose
+//     32 x 32 sub-tile the bump reaches;
+//   * four consumer warps keep the tile's h, Dx, Dy sums in registers
+//     (8 x 4 texels per thread) and do the outer products
+//       h  += (A k(v)) k(u)    Dx += (A k(v)) (lam/2) sin(pi u/R)
+//       Dy += (A (lam/2) sin(pi v/R)) k(u)
+//     i.e. 3 FMAs per bump-texel, skipping bumps outside their sub-tile.
+// Producers and consumers meet in a ring of factor slots guarded by
+// full/empty mbarriers (no block-wide barrier in the steady state).  Every
+// wait is bounded in time; a timeout sets an error flag and the CTA stops.
+// The epilogue writes the group's partial sums, or (one group) applies the
+// smoothstep blend weight and the bilinear background sample (no atomics).
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "internal.h"
@@ -29,18 +33,30 @@
 namespace scwp {
 namespace {
 
-constexpr int kRPT = 8;            // texel rows per thread
-constexpr int kCPT = 4;            // texel columns per thread
-constexpr int kWR = 4 * kRPT;      // warp sub-tile: 4 x 8 threads
+constexpr int kRPT = 8;            // texel rows per consumer thread
+constexpr int kCPT = 4;            // texel columns per consumer thread
+constexpr int kWR = 4 * kRPT;      // consumer warp sub-tile: 4 x 8 threads
 constexpr int kWC = 8 * kCPT;
-constexpr int kTY = 2 * kWR;       // CTA tile: 2 x 2 warps (64 rows)
-constexpr int kTX = 2 * kWC;       //                       (64 columns)
-constexpr int kSlots = kTX + kTY;  // axis samples per bump
-constexpr int kThreads = 128;
-constexpr int kCH = 32;            // bumps per staged chunk
+constexpr int kTY = 2 * kWR;       // CTA tile: 2 x 2 consumer warps (64 rows)
+constexpr int kTX = 2 * kWC;       //                                (64 columns)
+constexpr int kConsumers = 4;      // warps
+constexpr int kProducers = 2;      // warps
+constexpr int kPThreads = 32 * kProducers;
+constexpr int kThreads = 32 * (kConsumers + kProducers);
+constexpr int kCH = 32;            // bumps per chunk
+constexpr int kSlotsRing = 3;      // factor slots in flight
 constexpr int kMaxRanges = 64;     // bin rows per bucket batch
 constexpr int32_t kQi = 65536, kHalfi = 32768;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+struct __align__(16) FactorSlot {
+    float kx[kCH][kTX];            // k(u) per column
+    float kd[kCH][kTX];            // (lam/2) sin(pi u / R) per column
+    float ay[kCH][kTY];            // A k(v) per row
+    float cy[kCH][kTY];            // A (lam/2) sin(pi v / R) per row
+    uint32_t mask[kCH];            // consumer warps whose sub-tile the bump reaches
+    int n;                         // bumps in the slot; -1 ends the stream
+};
 
 struct BumpBase {                  // per bump and axis
     float c0, s0;                  // cos, sin of pi u0 / R at the tile's first texel
@@ -49,18 +65,26 @@ struct BumpBase {                  // per bump and axis
 };
 
 struct SynthSmem {
+    FactorSlot slot[kSlotsRing];
     int4 rec[2][kCH];              // staged bump records (16-byte aligned)
-    unsigned long long bar[2];     // mbarriers
+    unsigned long long rbar[2];    // record copies: complete_tx
+    unsigned long long full[kSlotsRing];   // producers -> consumers (kPThreads arrivals)
+    unsigned long long empty[kSlotsRing];  // consumers -> producers (kConsumers arrivals)
     BumpBase base[kCH][2];
-    float kx[kCH][kTX];            // k(u) per column
-    float kd[kCH][kTX];            // (lam/2) sin(pi u / R) per column
-    float ay[kCH][kTY];            // A k(v) per row
-    float cy[kCH][kTY];            // A (lam/2) sin(pi v / R) per row
-    uint32_t mask[kCH];            // warps whose sub-tile the bump reaches
     int rstart[kMaxRanges];        // bin-row ranges of the current bucket batch
     int rlen[kMaxRanges];
     int cpre[kMaxRanges + 1];      // chunk prefix per range
+    int stop;                      // producers: a wait timed out
 };
+// float4 loads from every slot and bulk copies into rec need 16-byte alignment
+static_assert(sizeof(FactorSlot) % 16 == 0, "factor slot alignment");
+static_assert(offsetof(SynthSmem, rec) % 16 == 0, "record staging alignment");
+static_assert(offsetof(SynthSmem, rbar) % 8 == 0 && offsetof(SynthSmem, full) % 8 == 0 &&
+                  offsetof(SynthSmem, empty) % 8 == 0,
+              "mbarrier alignment");
+static_assert(offsetof(FactorSlot, kd) % 16 == 0 && offsetof(FactorSlot, ay) % 16 == 0 &&
+                  offsetof(FactorSlot, cy) % 16 == 0,
+              "factor array alignment");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -103,10 +127,27 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // returns false (the caller abandons the tile).
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity,
                                                   unsigned long long* err) {
-    for (long long it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(err, (unsigned long long)kErrTimeout);
-    return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(err, (unsigned long long)kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// named barrier among the producer warps only
+__device__ __forceinline__ void producer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kPThreads) : "memory");
 }
 
 __device__ __forceinline__ int span_lo(int32_t C, int32_t R) {
@@ -210,196 +251,211 @@ __global__ void __launch_bounds__(256) k_blend_groups(PatchDev p, SynthParams sp
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_synth_gather(PatchDev p, SynthParams sp) {
+__global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthParams sp) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SynthSmem& S = *reinterpret_cast<SynthSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
-    // warp w covers rows kWR (w >> 1) .. +kWR, columns kWC (w & 1) .. +kWC
+    const int G = gridDim.z, g = blockIdx.z;
+    const int b_begin = (g * sp.nb) / G, b_end = ((g + 1) * sp.nb) / G;
+
+    if (tid == 0) {
+        mbar_init(&S.rbar[0], 1);
+        mbar_init(&S.rbar[1], 1);
+        for (int k = 0; k < kSlotsRing; ++k) {
+            mbar_init(&S.full[k], kPThreads);
+            mbar_init(&S.empty[k], kConsumers);
+        }
+        S.stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp >= kConsumers) {
+        // ======================= producers ===================================
+        const int ptid = tid - 32 * kConsumers;
+        const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
+        const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
+        const float lamh = sp.lam_half;
+        uint32_t rpar[2] = {0u, 0u};
+        int produced = 0;                  // chunks pushed into the ring
+        bool dead = false;
+        for (int bi = b_begin; bi < b_end && !dead; ++bi) {
+            const BucketDev bk = p.bk[bi];
+            int bx_lo = (int)(((int64_t)Xlo) / bk.C);
+            int bx_hi = (int)(((int64_t)Xhi + 2 * (int64_t)bk.R - 1) / bk.C);
+            int by_lo = (int)(((int64_t)Ylo) / bk.C);
+            int by_hi = (int)(((int64_t)Yhi + 2 * (int64_t)bk.R - 1) / bk.C);
+            if (bx_lo < 0) bx_lo = 0;
+            if (by_lo < 0) by_lo = 0;
+            if (bx_hi > bk.nbx - 1) bx_hi = bk.nbx - 1;
+            if (by_hi > bk.nby - 1) by_hi = bk.nby - 1;
+            if (bx_lo > bx_hi || by_lo > by_hi) continue;
+            const float invR = bk.invR;
+            const int32_t R = bk.R;
+            // rotation steps of this thread's column and row: e^{i pi n Q / R}
+            const float2 rot = p.rot[bi * kRotN + ptid];
+            for (int byb = by_lo; byb <= by_hi && !dead; byb += kMaxRanges) {
+                const int nr = min(kMaxRanges, by_hi - byb + 1);
+                for (int k = ptid; k < nr; k += kPThreads) {
+                    const int key0 = bk.base + (byb + k) * bk.nbx;
+                    const int s = (int)p.offsets[key0 + bx_lo];
+                    const int e = (int)p.offsets[key0 + bx_hi + 1];
+                    S.rstart[k] = s;
+                    S.rlen[k] = e - s;
+                }
+                producer_sync();
+                if (ptid == 0) {
+                    int acc = 0;
+                    for (int k = 0; k < nr; ++k) {
+                        S.cpre[k] = acc;
+                        acc += (S.rlen[k] + kCH - 1) / kCH;
+                    }
+                    S.cpre[nr] = acc;
+                }
+                producer_sync();
+                const int nchunks = S.cpre[nr];
+                if (nchunks == 0) continue;
+                auto chunk = [&](int c, int& off, int& n) {
+                    int k = 0;
+                    while (S.cpre[k + 1] <= c) ++k;
+                    off = S.rstart[k] + (c - S.cpre[k]) * kCH;
+                    n = min(kCH, S.rstart[k] + S.rlen[k] - off);
+                };
+                if (ptid == 0) {
+                    int off, n;
+                    chunk(0, off, n);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive_expect(&S.rbar[0], (uint32_t)n * 16u);
+                    bulk_g2s(&S.rec[0][0], p.rec + off, (uint32_t)n * 16u, &S.rbar[0]);
+                }
+                for (int c = 0; c < nchunks; ++c) {
+                    const int rs = c & 1;
+                    int off, n;
+                    chunk(c, off, n);
+                    const bool ok_r = mbar_wait_bounded(&S.rbar[rs], rpar[rs], p.stats + 2);
+                    rpar[rs] ^= 1u;
+                    if (!ok_r) S.stop = 1;
+                    // bases (warp 0 of the producers: x, warp 1: y) and masks
+                    if (lane < n && !S.stop) {
+                        const int4 rc = S.rec[rs][lane];
+                        const int ax = ptid >> 5;
+                        const int32_t u0 = ax ? Ylo - rc.y : Xlo - rc.x;
+                        float sn, cs;
+                        sincospif((float)u0 * invR, &sn, &cs);
+                        BumpBase bb;
+                        bb.c0 = cs;
+                        bb.s0 = sn;
+                        bb.u0 = u0;
+                        bb.amp = ax ? __int_as_float(rc.z) : 1.f;
+                        S.base[lane][ax] = bb;
+                    }
+                    const int fs = produced % kSlotsRing;
+                    const uint32_t epar = ((produced / kSlotsRing) & 1u) ^ 1u;
+                    const bool ok_e = mbar_wait_bounded(&S.empty[fs], epar, p.stats + 2);
+                    if (!ok_e) S.stop = 1;
+                    FactorSlot& F = S.slot[fs];
+                    if (ptid < n && !S.stop) {
+                        const int4 rc = S.rec[rs][ptid];
+                        const int xl = span_lo(rc.x, R) - tx0, xh = span_hi(rc.x, R) - tx0;
+                        const int yl = span_lo(rc.y, R) - ty0, yh = span_hi(rc.y, R) - ty0;
+                        uint32_t m = 0;
+#pragma unroll
+                        for (int w = 0; w < kConsumers; ++w) {
+                            const int c0 = kWC * (w & 1), r0 = kWR * (w >> 1);
+                            if (xl <= c0 + kWC - 1 && xh >= c0 && yl <= r0 + kWR - 1 && yh >= r0) m |= 1u << w;
+                        }
+                        F.mask[ptid] = m;
+                    }
+                    producer_sync();   // bases visible; record slot rs free
+                    if (S.stop) {
+                        dead = true;
+                        break;
+                    }
+                    if (ptid == 0 && c + 1 < nchunks) {
+                        int off2, n2;
+                        chunk(c + 1, off2, n2);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_arrive_expect(&S.rbar[rs ^ 1], (uint32_t)n2 * 16u);
+                        bulk_g2s(&S.rec[rs ^ 1][0], p.rec + off2, (uint32_t)n2 * 16u, &S.rbar[rs ^ 1]);
+                    }
+                    // factors: column ptid and row ptid of every bump
+                    for (int b = 0; b < n; ++b) {
+                        {
+                            const BumpBase bb = S.base[b][0];
+                            const int32_t u = bb.u0 + ptid * kQi;
+                            const bool in = u > -R && u < R;
+                            const float cs = bb.c0 * rot.x - bb.s0 * rot.y;
+                            const float sn = bb.s0 * rot.x + bb.c0 * rot.y;
+                            F.kx[b][ptid] = in ? 0.5f + 0.5f * cs : 0.f;
+                            F.kd[b][ptid] = in ? lamh * sn : 0.f;
+                        }
+                        {
+                            const BumpBase bb = S.base[b][1];
+                            const int32_t v = bb.u0 + ptid * kQi;
+                            const bool in = v > -R && v < R;
+                            const float cs = bb.c0 * rot.x - bb.s0 * rot.y;
+                            const float sn = bb.s0 * rot.x + bb.c0 * rot.y;
+                            F.ay[b][ptid] = in ? bb.amp * (0.5f + 0.5f * cs) : 0.f;
+                            F.cy[b][ptid] = in ? bb.amp * lamh * sn : 0.f;
+                        }
+                    }
+                    if (ptid == 0) F.n = n;
+                    mbar_arrive(&S.full[fs]);
+                    ++produced;
+                    producer_sync();   // every producer done with S.base before the next chunk
+                }
+            }
+        }
+        // end of stream (also after a timeout, so the consumers stop)
+        const int fs = produced % kSlotsRing;
+        const uint32_t epar = ((produced / kSlotsRing) & 1u) ^ 1u;
+        mbar_wait_bounded(&S.empty[fs], epar, p.stats + 2);
+        if (ptid == 0) S.slot[fs].n = -1;
+        mbar_arrive(&S.full[fs]);
+        return;
+    }
+
+    // ========================= consumers =======================================
     const int tc = 8 * (warp & 1) + (lane & 7);     // column group 0..15
     const int tr = 4 * (warp >> 1) + (lane >> 3);   // row group 0..7
-
     float h[kRPT][kCPT], dx[kRPT][kCPT], dy[kRPT][kCPT];
 #pragma unroll
     for (int r = 0; r < kRPT; ++r)
 #pragma unroll
         for (int c = 0; c < kCPT; ++c) h[r][c] = dx[r][c] = dy[r][c] = 0.f;
-
-    if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
-    bool aborted = false;   // block-uniform (decided by __syncthreads_or)
-    const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
-    const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
-    const float lamh = sp.lam_half;
-    // this thread's sample slots in the generation phase: slot s < kTX is
-    // column s, slot s >= kTX is row s - kTX; thread t owns slots t, t + 128
-    constexpr int kSlotsPT = (kSlots + kThreads - 1) / kThreads;
-
-    // bucket group of this CTA: buckets [b_begin, b_end)
-    const int G = gridDim.z, g = blockIdx.z;
-    const int b_begin = (g * sp.nb) / G, b_end = ((g + 1) * sp.nb) / G;
-    for (int bi = b_begin; bi < b_end && !aborted; ++bi) {
-        const BucketDev bk = p.bk[bi];
-        int bx_lo = (int)(((int64_t)Xlo) / bk.C);
-        int bx_hi = (int)(((int64_t)Xhi + 2 * (int64_t)bk.R - 1) / bk.C);
-        int by_lo = (int)(((int64_t)Ylo) / bk.C);
-        int by_hi = (int)(((int64_t)Yhi + 2 * (int64_t)bk.R - 1) / bk.C);
-        if (bx_lo < 0) bx_lo = 0;
-        if (by_lo < 0) by_lo = 0;
-        if (bx_hi > bk.nbx - 1) bx_hi = bk.nbx - 1;
-        if (by_hi > bk.nby - 1) by_hi = bk.nby - 1;
-        if (bx_lo > bx_hi || by_lo > by_hi) continue;
-        const float invR = bk.invR;
-        const int32_t R = bk.R;
-        // rotation steps of this thread's sample slots: e^{i pi n Q / R}
-        float2 rot[kSlotsPT];
+    for (int k = 0;; ++k) {
+        const int fs = k % kSlotsRing;
+        const uint32_t fpar = (k / kSlotsRing) & 1u;
+        if (!mbar_wait_bounded(&S.full[fs], fpar, p.stats + 2)) break;
+        const FactorSlot& F = S.slot[fs];
+        const int n = F.n;
+        if (n < 0) break;
+        uint32_t todo = __ballot_sync(0xffffffffu, lane < n && ((F.mask[lane] >> warp) & 1u));
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const float4 kx4 = *reinterpret_cast<const float4*>(&F.kx[b][kCPT * tc]);
+            const float4 kd4 = *reinterpret_cast<const float4*>(&F.kd[b][kCPT * tc]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&F.ay[b][kRPT * tr]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&F.ay[b][kRPT * tr + 4]);
+            const float4 c0 = *reinterpret_cast<const float4*>(&F.cy[b][kRPT * tr]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&F.cy[b][kRPT * tr + 4]);
+            const float kxv[4] = {kx4.x, kx4.y, kx4.z, kx4.w};
+            const float kdv[4] = {kd4.x, kd4.y, kd4.z, kd4.w};
+            const float ayv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float cyv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-        for (int q = 0; q < kSlotsPT; ++q) {
-            const int sl = tid + q * kThreads;
-            rot[q] = sl < kSlots ? p.rot[bi * kRotN + (sl < kTX ? sl : sl - kTX)] : make_float2(1.f, 0.f);
+            for (int r = 0; r < kRPT; ++r)
+#pragma unroll
+                for (int cc = 0; cc < kCPT; ++cc) {
+                    h[r][cc] = fmaf(ayv[r], kxv[cc], h[r][cc]);
+                    dx[r][cc] = fmaf(ayv[r], kdv[cc], dx[r][cc]);
+                    dy[r][cc] = fmaf(cyv[r], kxv[cc], dy[r][cc]);
+                }
         }
-        for (int byb = by_lo; byb <= by_hi && !aborted; byb += kMaxRanges) {
-            const int nr = min(kMaxRanges, by_hi - byb + 1);
-            for (int k = tid; k < nr; k += kThreads) {
-                const int key0 = bk.base + (byb + k) * bk.nbx;
-                const int s = (int)p.offsets[key0 + bx_lo];
-                const int e = (int)p.offsets[key0 + bx_hi + 1];
-                S.rstart[k] = s;
-                S.rlen[k] = e - s;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int acc = 0;
-                for (int k = 0; k < nr; ++k) {
-                    S.cpre[k] = acc;
-                    acc += (S.rlen[k] + kCH - 1) / kCH;
-                }
-                S.cpre[nr] = acc;
-            }
-            __syncthreads();
-            const int nchunks = S.cpre[nr];
-            if (nchunks == 0) continue;
-            // chunk c -> (source offset, count), computable by any thread
-            auto chunk = [&](int c, int& off, int& n) {
-                int k = 0;
-                while (S.cpre[k + 1] <= c) ++k;
-                off = S.rstart[k] + (c - S.cpre[k]) * kCH;
-                n = min(kCH, S.rstart[k] + S.rlen[k] - off);
-            };
-            if (tid == 0) {
-                int off, n;
-                chunk(0, off, n);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive_expect(&S.bar[0], (uint32_t)n * 16u);
-                bulk_g2s(&S.rec[0][0], p.rec + off, (uint32_t)n * 16u, &S.bar[0]);
-            }
-            for (int c = 0; c < nchunks; ++c) {
-                const int slot = c & 1;
-                int off, n;
-                chunk(c, off, n);
-                const bool late = !mbar_wait_bounded(&S.bar[slot], parity[slot], p.stats + 2);
-                parity[slot] ^= 1u;
-                if (__syncthreads_or(late)) {
-                    aborted = true;
-                    break;
-                }
-                if (tid == 0 && c + 1 < nchunks) {
-                    int off2, n2;
-                    chunk(c + 1, off2, n2);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_arrive_expect(&S.bar[slot ^ 1], (uint32_t)n2 * 16u);
-                    bulk_g2s(&S.rec[slot ^ 1][0], p.rec + off2, (uint32_t)n2 * 16u, &S.bar[slot ^ 1]);
-                }
-                // (1) per bump and axis: the phase at the tile's first texel;
-                //     per bump: which warps' sub-tiles its support reaches
-                if (tid < 2 * n) {
-                    const int b = tid >> 1, ax = tid & 1;
-                    const int4 rc = S.rec[slot][b];
-                    const int32_t u0 = ax ? Ylo - rc.y : Xlo - rc.x;
-                    float sn, cs;
-                    sincospif((float)u0 * invR, &sn, &cs);
-                    BumpBase bb;
-                    bb.c0 = cs;
-                    bb.s0 = sn;
-                    bb.u0 = u0;
-                    bb.amp = ax ? __int_as_float(rc.z) : 1.f;
-                    S.base[b][ax] = bb;
-                } else if (tid >= 64 && tid < 64 + n) {
-                    const int b = tid - 64;
-                    const int4 rc = S.rec[slot][b];
-                    const int xl = span_lo(rc.x, R) - tx0, xh = span_hi(rc.x, R) - tx0;
-                    const int yl = span_lo(rc.y, R) - ty0, yh = span_hi(rc.y, R) - ty0;
-                    uint32_t m = 0;
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const int c0 = kWC * (w & 1), r0 = kWR * (w >> 1);
-                        if (xl <= c0 + kWC - 1 && xh >= c0 && yl <= r0 + kWR - 1 && yh >= r0) m |= 1u << w;
-                    }
-                    S.mask[b] = m;
-                }
-                __syncthreads();
-                // (2) samples by phase rotation of the bump's base phase
-                for (int b = 0; b < n; ++b) {
-#pragma unroll
-                    for (int q = 0; q < kSlotsPT; ++q) {
-                        const int sl = tid + q * kThreads;
-                        if (sl >= kSlots) break;
-                        const bool col = sl < kTX;
-                        const int k = col ? sl : sl - kTX;
-                        const BumpBase bb = S.base[b][col ? 0 : 1];
-                        const int32_t u = bb.u0 + k * kQi;
-                        const bool in = u > -R && u < R;
-                        const float cs = bb.c0 * rot[q].x - bb.s0 * rot[q].y;
-                        const float sn = bb.s0 * rot[q].x + bb.c0 * rot[q].y;
-                        const float kv = in ? bb.amp * (0.5f + 0.5f * cs) : 0.f;
-                        const float dv = in ? bb.amp * lamh * sn : 0.f;
-                        if (col) {
-                            S.kx[b][k] = kv;
-                            S.kd[b][k] = dv;
-                        } else {
-                            S.ay[b][k] = kv;
-                            S.cy[b][k] = dv;
-                        }
-                    }
-                }
-                uint32_t todo = __ballot_sync(0xffffffffu, lane < n && ((S.mask[lane] >> warp) & 1u));
-                __syncthreads();
-                // (3) outer products: kRPT x kCPT texels x 3 fields per thread
-                while (todo) {
-                    const int b = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    float kxv[kCPT], kdv[kCPT], ayv[kRPT], cyv[kRPT];
-#pragma unroll
-                    for (int q = 0; q < kCPT / 4; ++q) {
-                        const float4 a = *reinterpret_cast<const float4*>(&S.kx[b][kCPT * tc + 4 * q]);
-                        const float4 d = *reinterpret_cast<const float4*>(&S.kd[b][kCPT * tc + 4 * q]);
-                        kxv[4 * q] = a.x; kxv[4 * q + 1] = a.y; kxv[4 * q + 2] = a.z; kxv[4 * q + 3] = a.w;
-                        kdv[4 * q] = d.x; kdv[4 * q + 1] = d.y; kdv[4 * q + 2] = d.z; kdv[4 * q + 3] = d.w;
-                    }
-#pragma unroll
-                    for (int q = 0; q < kRPT / 4; ++q) {
-                        const float4 a = *reinterpret_cast<const float4*>(&S.ay[b][kRPT * tr + 4 * q]);
-                        const float4 c = *reinterpret_cast<const float4*>(&S.cy[b][kRPT * tr + 4 * q]);
-                        ayv[4 * q] = a.x; ayv[4 * q + 1] = a.y; ayv[4 * q + 2] = a.z; ayv[4 * q + 3] = a.w;
-                        cyv[4 * q] = c.x; cyv[4 * q + 1] = c.y; cyv[4 * q + 2] = c.z; cyv[4 * q + 3] = c.w;
-                    }
-#pragma unroll
-                    for (int r = 0; r < kRPT; ++r)
-#pragma unroll
-                        for (int cc = 0; cc < kCPT; ++cc) {
-                            h[r][cc] = fmaf(ayv[r], kxv[cc], h[r][cc]);
-                            dx[r][cc] = fmaf(ayv[r], kdv[cc], dx[r][cc]);
-                            dy[r][cc] = fmaf(cyv[r], kxv[cc], dy[r][cc]);
-                        }
-                }
-                __syncthreads();
-            }
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[fs]);
     }
 
     // ---- epilogue ------------------------------------------------------------------
@@ -412,13 +468,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_synth_gather(PatchDev p, SynthP
         for (int r = 0; r < kRPT; ++r) {
             const int iy = ty0 + kRPT * tr + r;
             if (iy >= sp.H) continue;
-#pragma unroll
-            for (int q = 0; q < kCPT / 4; ++q) {
-                const float o[3][4] = {{h[r][4 * q], h[r][4 * q + 1], h[r][4 * q + 2], h[r][4 * q + 3]},
-                                       {dx[r][4 * q], dx[r][4 * q + 1], dx[r][4 * q + 2], dx[r][4 * q + 3]},
-                                       {dy[r][4 * q], dy[r][4 * q + 1], dy[r][4 * q + 2], dy[r][4 * q + 3]}};
-                store_row4(dst, plane, sp.W, iy, tx0 + kCPT * tc + 4 * q, o);
-            }
+            const float o[3][4] = {{h[r][0], h[r][1], h[r][2], h[r][3]},
+                                   {dx[r][0], dx[r][1], dx[r][2], dx[r][3]},
+                                   {dy[r][0], dy[r][1], dy[r][2], dy[r][3]}};
+            store_row4(dst, plane, sp.W, iy, tx0 + kCPT * tc, o);
         }
         return;
     }
@@ -426,20 +479,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_synth_gather(PatchDev p, SynthP
     for (int r = 0; r < kRPT; ++r) {
         const int iy = ty0 + kRPT * tr + r;
         if (iy >= sp.H) continue;
+        float o[3][4];
 #pragma unroll
-        for (int q = 0; q < kCPT / 4; ++q) {
-            float o[3][4];
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int ix = tx0 + kCPT * tc + 4 * q + cc;
-                float bgv[3];
-                const float w = blend_at(sp, ix, iy, bgv);
-                o[0][cc] = w * h[r][4 * q + cc] + (1.f - w) * bgv[0];
-                o[1][cc] = w * dx[r][4 * q + cc] + (1.f - w) * bgv[1];
-                o[2][cc] = w * dy[r][4 * q + cc] + (1.f - w) * bgv[2];
-            }
-            store_row4(p.out, plane, sp.W, iy, tx0 + kCPT * tc + 4 * q, o);
+        for (int cc = 0; cc < 4; ++cc) {
+            const int ix = tx0 + kCPT * tc + cc;
+            float bgv[3];
+            const float w = blend_at(sp, ix, iy, bgv);
+            o[0][cc] = w * h[r][cc] + (1.f - w) * bgv[0];
+            o[1][cc] = w * dx[r][cc] + (1.f - w) * bgv[1];
+            o[2][cc] = w * dy[r][cc] + (1.f - w) * bgv[2];
         }
+        store_row4(p.out, plane, sp.W, iy, tx0 + kCPT * tc, o);
     }
 }
 
