@@ -55,7 +55,10 @@ enum { SCWP_SPECTRUM_JONSWAP = 0, SCWP_SPECTRUM_PHILLIPS = 1 };
 enum { SCWP_SPREAD_COS2S_MITSUYASU = 0, SCWP_SPREAD_COS2 = 1 };
 enum { SCWP_AMP_NORMALIZED = 0, SCWP_AMP_LITERAL = 1 };
 enum { SCWP_FIELD_H = 0, SCWP_FIELD_DX = 1, SCWP_FIELD_DY = 2 };
-enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1 };
+/* synthesis of the patch maps: the tile gather on the tensor cores (default;
+ * tcgen05 TF32 MMAs with a hi/lo split, FP32-accurate), the same gather on
+ * the FP32 CUDA cores, or the paper's layered-texture formulation */
+enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1, SCWP_SYNTH_GATHER_FP32 = 2 };
 
 #define SCWP_MAX_BUCKETS 64
 #define SCWP_MAX_THETA 256
@@ -221,8 +224,9 @@ scwp_status scwp_get_bins(scwp_ctx* ctx, int32_t patch_id, uint32_t* counts, uin
 
 /* Recompute the synthesis and blend of every patch from the current
  * particles and background without advancing the frame (the bins are
- * rebuilt).  mode: SCWP_SYNTH_GATHER (tile gather, the default path of
- * scwp_step) or SCWP_SYNTH_LAYERED (per-bucket layer splat + separable
+ * rebuilt).  mode: SCWP_SYNTH_GATHER (tile gather on the tensor cores, the
+ * default path of scwp_step), SCWP_SYNTH_GATHER_FP32 (the same gather on the
+ * FP32 CUDA cores) or SCWP_SYNTH_LAYERED (per-bucket layer splat + separable
  * x / y passes + layer sum, Sec. 4.2). */
 scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode);
 

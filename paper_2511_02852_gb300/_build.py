@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libscwp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-CU_SOURCES = ["api.cu", "k_particles.cu", "k_fft.cu", "k_synth.cu", "k_layered.cu", "noalloc.cu"]
+CU_SOURCES = ["api.cu", "k_particles.cu", "k_fft.cu", "k_synth.cu", "k_synth_tc.cu", "k_layered.cu",
+              "noalloc.cu"]
 CXX_SOURCES = ["host_spectrum.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

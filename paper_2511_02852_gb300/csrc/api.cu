@@ -292,8 +292,10 @@ scwp_status synthesize(scwp_ctx* ctx, int mode) {
                 nbins[i] = P->bk[i].nbx * P->bk[i].nby;
             }
             CU(launch_layered(D, sp, P->T.R.data(), base.data(), nbins.data(), ctx->st));
-        } else {
+        } else if (mode == SCWP_SYNTH_GATHER_FP32) {
             CU(launch_synth_gather(P->dev, sp, ctx->st));
+        } else {
+            CU(launch_synth_tc(P->dev, sp, ctx->st));
         }
     }
     return SCWP_OK;
@@ -420,11 +422,14 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         // split the synthesis into bucket groups so that a frame has enough
         // CTAs to fill every SM several times over (about 4 waves of 3 CTAs
         // per SM on 152 SMs); each group writes its own partial sums
-        const int tiles = ((T.W + 63) / 64) * ((T.H + 63) / 64);
-        int G = (4 * 152 * 3 + tiles - 1) / tiles;
-        if (G > T.nb) G = T.nb;
-        if (G < 1) G = 1;
-        D.groups = G;
+        auto groups_for = [&](int tiles, int ctas_per_sm) {
+            int G = (4 * 152 * ctas_per_sm + tiles - 1) / tiles;
+            if (G > T.nb) G = T.nb;
+            return G < 1 ? 1 : G;
+        };
+        D.groups = groups_for(((T.W + 63) / 64) * ((T.H + 63) / 64), 2);       // CUDA-core tiles
+        D.groups_tc = groups_for(((T.W + 63) / 64) * ((T.H + 63) / 64), 2);    // tensor-core tiles
+        const int G = D.groups > D.groups_tc ? D.groups : D.groups_tc;
         if (G > 1) {
             D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
             ok = ok && D.partial;
@@ -665,7 +670,8 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
     const long long before = launches_total();
-    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED) return fail(ctx, SCWP_E_INVALID, "mode");
+    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32)
+        return fail(ctx, SCWP_E_INVALID, "mode");
     if (!ctx->bg_valid) {
         CU(launch_background(ctx->bg, ctx->t, ctx->st));
         ctx->bg_valid = true;
@@ -683,7 +689,8 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
 scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
-    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED) return fail(ctx, SCWP_E_INVALID, "mode");
+    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32)
+        return fail(ctx, SCWP_E_INVALID, "mode");
     ctx->synth_mode = mode;
     return SCWP_OK;
 }

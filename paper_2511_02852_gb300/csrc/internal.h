@@ -49,7 +49,8 @@ struct PatchDev {
     int4* rec = nullptr;                  // [2 cap] bump records in bin order
     float* out = nullptr;                 // [3][H][W] blended maps
     float* partial = nullptr;             // [groups][3][H][W] per-bucket-group sums (groups > 1)
-    int groups = 1;                       // bucket groups the synthesis is split into
+    int groups = 1;                       // bucket groups of the CUDA-core synthesis
+    int groups_tc = 1;                    // bucket groups of the tensor-core synthesis
     unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..] live per bucket
     float* layers = nullptr;              // layered variant scratch (lazy)
     size_t layers_bytes = 0;
@@ -100,6 +101,7 @@ cudaError_t launch_compact(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st);
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
+cudaError_t launch_synth_tc(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
 // sum `groups` partial [3][H][W] planes at src (in order), blend, store to p.out
 cudaError_t launch_blend(const PatchDev& p, const SynthParams& sp, const float* src, int groups,
                          cudaStream_t st);

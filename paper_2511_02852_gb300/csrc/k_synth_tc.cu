@@ -1,0 +1,449 @@
+// Tensor-core tile gather of the wave-particle synthesis (sm_103a tcgen05),
+// Sec. 4.2.  Same sums as the CUDA-core kernel: for a tile of texel columns
+// x and rows y and the bumps b that reach it,
+//   h(x,y)  = sum_b k_b(u_x) A_b k_b(v_y)
+//   Dx(x,y) = sum_b (lam/2) sin(pi u_x/R) A_b k_b(v_y)
+//   Dy(x,y) = sum_b k_b(u_x) A_b (lam/2) sin(pi v_y/R)
+// are one dense contraction over bumps,
+//   D[m][n] = sum_b Aop[m][b] Bop[n][b],
+//   Aop = [ k(u_x) ; (lam/2) sin(pi u_x/R) ]           (128 x K: 64 columns x 2)
+//   Bop = [ A k(v_y) ; A (lam/2) sin(pi v_y/R) ]       (128 x K: 64 rows x 2)
+// whose quadrants are h^T, Dx^T, Dy^T (the fourth is unused), computed by
+// tcgen05.mma (M = 128, N = 128, K = 8, kind::tf32) into FP32 accumulators in
+// tensor memory.  Each operand is split as hi + lo, both rounded to TF32 to
+// nearest (hi = tf32(x), lo = tf32(x - hi): 22 significant bits together);
+// hi*hi accumulates in one accumulator and the small corrections
+// hi*lo + lo*hi in a second one, so the large sum takes one rounding per step
+// and the two are added in FP32 when read out.
+//
+// Warps 0-3 produce the operands of each 16-bump chunk into a 2-stage ring in
+// shared memory (no-swizzle K-major canonical layout: 8-row x 16-byte core
+// matrices, 128 B apart along K, 512 B apart along rows), from bump records
+// staged by bulk async copy and one sincospi per bump and axis rotated by the
+// bucket's e^{i pi n Q / R} table.  One thread of warp 4 issues the MMAs and
+// commits each stage back to the producers; after the last stage the
+// producer warps read the accumulator out of tensor memory (tcgen05.ld) and
+// write the bucket group's partial sums, or the blended maps.  All waits are
+// bounded in time; a timeout sets an error flag.
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace scwp {
+namespace {
+
+constexpr int kTX = 64;            // tile columns (x): the MMA's M = 2 * kTX
+constexpr int kTY = 64;            // tile rows (y):    the MMA's N = 2 * kTY
+constexpr int kKc = 16;            // bumps per stage (two K = 8 steps)
+constexpr int kStages = 3;
+constexpr int kProdThreads = 128;  // warps 0-3
+constexpr int kThreads = kProdThreads + 32;
+constexpr int kMaxRanges = 64;
+constexpr int kTmemCols = 256;     // main accumulator at column 0, corrections at 2 * kTY
+constexpr uint32_t kCorrCol = 2 * kTY;
+constexpr int32_t kQi = 65536, kHalfi = 32768;
+constexpr long long kWaitCycles = 4000000000ll;
+constexpr uint32_t kSBO = (kKc / 4) * 128;   // bytes between 8-row groups
+
+struct __align__(1024) TcStage {
+    float Ahi[2 * kTX * kKc];      // rows 0..63 k(u), 64..127 (lam/2) sin
+    float Alo[2 * kTX * kKc];
+    float Bhi[2 * kTY * kKc];      // rows 0..63 A k(v), 64..127 A (lam/2) sin
+    float Blo[2 * kTY * kKc];
+};
+
+struct BumpBase {
+    float c0, s0;
+    int32_t u0;
+    float amp;
+};
+
+struct TcSmem {
+    TcStage st[kStages];
+    int4 rec[2][kKc];
+    BumpBase base[kKc][2];
+    unsigned long long rbar[2];
+    unsigned long long full[kStages];    // producers -> MMA thread (128 arrivals)
+    unsigned long long empty[kStages];   // MMA commit -> producers (1 arrival)
+    unsigned long long done;             // final MMA commit -> epilogue
+    int stage_n[kStages];                // bumps in the stage; -1 ends the stream
+    int rstart[kMaxRanges];
+    int rlen[kMaxRanges];
+    int cpre[kMaxRanges + 1];
+    uint32_t tmem;
+    int stop;
+};
+static_assert(sizeof(TcStage) % 1024 == 0, "stage alignment");
+static_assert(offsetof(TcSmem, rec) % 16 == 0, "record staging alignment");
+static_assert(offsetof(TcSmem, rbar) % 8 == 0, "mbarrier alignment");
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+    asm volatile("{\n\t.reg .b64 s;\n\tmbarrier.arrive.shared::cta.b64 s, [%0];\n\t}" ::"r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_tx(unsigned long long* b, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 s;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 s, [%0], %1;\n\t}" ::"r"(sa(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long* b, uint32_t par) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(sa(b)), "r"(par)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t par, unsigned long long* err) {
+    if (bar_try(b, par)) return true;
+    const long long t0 = clock64();
+    while (!bar_try(b, par))
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(err, (unsigned long long)kErrTimeout);
+            return false;
+        }
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sa(dst)),
+                 "l"(src), "r"(bytes), "r"(sa(b))
+                 : "memory");
+}
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory"); }
+
+// shared-memory matrix descriptor: no swizzle, K-major canonical layout
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((sa(p) & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// byte offset of element (row r, k) in a K-major canonical operand
+__device__ __forceinline__ int canon(int r, int kq) { return kq * 128 + (r >> 3) * (int)kSBO + (r & 7) * 16; }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// blend weight at (ix, iy) and the bilinear background sample of one field
+__device__ __forceinline__ float blend1(const SynthParams& sp, int ix, int iy, int f, float wp) {
+    const float d = fminf(fminf((float)ix + 0.5f, (float)sp.W - (float)ix - 0.5f),
+                          fminf((float)iy + 0.5f, (float)sp.H - (float)iy - 0.5f));
+    const float t = fminf(fmaxf(d / sp.band, 0.f), 1.f);
+    const float w = t * t * (3.f - 2.f * t);
+    if (w >= 1.f) return wp;
+    const int N = sp.N;
+    const float fx = sp.fx0 + (float)ix * sp.fsx, fy = sp.fy0 + (float)iy * sp.fsx;
+    const float flx = floorf(fx), fly = floorf(fy);
+    const float a = fx - flx, b = fy - fly;
+    int x0 = (int)flx % N, y0 = (int)fly % N;
+    if (x0 < 0) x0 += N;
+    if (y0 < 0) y0 += N;
+    const int x1 = (x0 + 1) % N, y1 = (y0 + 1) % N;
+    const float* g = sp.bg + (size_t)f * N * N;
+    const float bg = (1.f - a) * (1.f - b) * g[(size_t)y0 * N + x0] + a * (1.f - b) * g[(size_t)y0 * N + x1] +
+                     (1.f - a) * b * g[(size_t)y1 * N + x0] + a * b * g[(size_t)y1 * N + x1];
+    return w * wp + (1.f - w) * bg;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParams sp) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
+    const int G = gridDim.z, g = blockIdx.z;
+    const int b_begin = (g * sp.nb) / G, b_end = ((g + 1) * sp.nb) / G;
+
+    if (tid == 0) {
+        bar_init(&S.rbar[0], 1);
+        bar_init(&S.rbar[1], 1);
+        for (int k = 0; k < kStages; ++k) {
+            bar_init(&S.full[k], kProdThreads);
+            bar_init(&S.empty[k], 1);
+        }
+        bar_init(&S.done, 1);
+        S.stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem)),
+                     "n"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem;
+
+    if (warp == 4) {
+        // ======================= MMA issuer ==================================
+        if (lane == 0) {
+            const uint32_t idesc =
+                (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);
+            uint32_t acc = 0, acc2 = 0;
+            for (int k = 0;; ++k) {
+                const int fs = k % kStages;
+                if (!bar_wait(&S.full[fs], (k / kStages) & 1u, p.stats + 2)) break;
+                if (S.stage_n[fs] < 0) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const TcStage& T = S.st[fs];
+#pragma unroll
+                for (int s = 0; s < kKc / 8; ++s) {
+                    const uint32_t off = (uint32_t)s * 256u;   // two 16-byte K chunks per step
+                    const uint64_t ah = smem_desc((const char*)T.Ahi + off, 128, kSBO);
+                    const uint64_t al = smem_desc((const char*)T.Alo + off, 128, kSBO);
+                    const uint64_t bh = smem_desc((const char*)T.Bhi + off, 128, kSBO);
+                    const uint64_t bl = smem_desc((const char*)T.Blo + off, 128, kSBO);
+                    mma_tf32(tmem, ah, bh, idesc, acc);
+                    mma_tf32(tmem + kCorrCol, ah, bl, idesc, acc2);
+                    mma_tf32(tmem + kCorrCol, al, bh, idesc, 1);
+                    acc = acc2 = 1;
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 sa(&S.empty[fs]))
+                             : "memory");
+            }
+            // arrives once every MMA issued above has completed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             sa(&S.done))
+                         : "memory");
+        }
+        __syncwarp();
+    } else {
+        // ======================= producers ===================================
+        const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
+        const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
+        const float lamh = sp.lam_half;
+        uint32_t rpar[2] = {0u, 0u};
+        int produced = 0;
+        bool dead = false;
+        // threads 0..63 build row tid (A k(v), A (lam/2) sin);
+        // threads 64..127 build column tid - 64 (k(u), (lam/2) sin)
+        const bool is_row = tid < kTY;
+        const int idx = is_row ? tid : tid - kTY;
+        for (int bi = b_begin; bi < b_end && !dead; ++bi) {
+            const BucketDev bk = p.bk[bi];
+            int bx_lo = (int)(((int64_t)Xlo) / bk.C);
+            int bx_hi = (int)(((int64_t)Xhi + 2 * (int64_t)bk.R - 1) / bk.C);
+            int by_lo = (int)(((int64_t)Ylo) / bk.C);
+            int by_hi = (int)(((int64_t)Yhi + 2 * (int64_t)bk.R - 1) / bk.C);
+            if (bx_lo < 0) bx_lo = 0;
+            if (by_lo < 0) by_lo = 0;
+            if (bx_hi > bk.nbx - 1) bx_hi = bk.nbx - 1;
+            if (by_hi > bk.nby - 1) by_hi = bk.nby - 1;
+            if (bx_lo > bx_hi || by_lo > by_hi) continue;
+            const float invR = bk.invR;
+            const int32_t R = bk.R;
+            const float2 rot = p.rot[bi * kRotN + idx];   // e^{i pi idx Q / R}
+            for (int byb = by_lo; byb <= by_hi && !dead; byb += kMaxRanges) {
+                const int nr = min(kMaxRanges, by_hi - byb + 1);
+                for (int k = tid; k < nr; k += kProdThreads) {
+                    const int key0 = bk.base + (byb + k) * bk.nbx;
+                    const int s = (int)p.offsets[key0 + bx_lo];
+                    const int e = (int)p.offsets[key0 + bx_hi + 1];
+                    S.rstart[k] = s;
+                    S.rlen[k] = e - s;
+                }
+                prod_sync();
+                if (tid == 0) {
+                    int a = 0;
+                    for (int k = 0; k < nr; ++k) {
+                        S.cpre[k] = a;
+                        a += (S.rlen[k] + kKc - 1) / kKc;
+                    }
+                    S.cpre[nr] = a;
+                }
+                prod_sync();
+                const int nchunks = S.cpre[nr];
+                if (nchunks == 0) continue;
+                auto chunk = [&](int c, int& off, int& n) {
+                    int k = 0;
+                    while (S.cpre[k + 1] <= c) ++k;
+                    off = S.rstart[k] + (c - S.cpre[k]) * kKc;
+                    n = min(kKc, S.rstart[k] + S.rlen[k] - off);
+                };
+                if (tid == 0) {
+                    int off, n;
+                    chunk(0, off, n);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_arrive_tx(&S.rbar[0], (uint32_t)n * 16u);
+                    bulk_g2s(&S.rec[0][0], p.rec + off, (uint32_t)n * 16u, &S.rbar[0]);
+                }
+                for (int c = 0; c < nchunks; ++c) {
+                    const int rs = c & 1;
+                    int off, n;
+                    chunk(c, off, n);
+                    if (!bar_wait(&S.rbar[rs], rpar[rs], p.stats + 2)) S.stop = 1;
+                    rpar[rs] ^= 1u;
+                    if (tid < 2 * kKc) {
+                        const int b = tid & (kKc - 1), ax = tid >> 4;
+                        BumpBase bb;
+                        if (b < n && !S.stop) {
+                            const int4 rc = S.rec[rs][b];
+                            const int32_t u0 = ax ? Ylo - rc.y : Xlo - rc.x;
+                            float sn, cs;
+                            sincospif((float)u0 * invR, &sn, &cs);
+                            bb.c0 = cs;
+                            bb.s0 = sn;
+                            bb.u0 = u0;
+                            bb.amp = ax ? __int_as_float(rc.z) : 1.f;
+                        } else {
+                            bb.c0 = bb.s0 = 0.f;
+                            bb.u0 = 0x40000000;      // outside every support: the factor is 0
+                            bb.amp = 0.f;
+                        }
+                        S.base[b][ax] = bb;
+                    }
+                    const int fs = produced % kStages;
+                    if (!bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2)) S.stop = 1;
+                    prod_sync();   // bases visible, record slot rs free
+                    if (S.stop) {
+                        dead = true;
+                        break;
+                    }
+                    if (tid == 0 && c + 1 < nchunks) {
+                        int off2, n2;
+                        chunk(c + 1, off2, n2);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        bar_arrive_tx(&S.rbar[rs ^ 1], (uint32_t)n2 * 16u);
+                        bulk_g2s(&S.rec[rs ^ 1][0], p.rec + off2, (uint32_t)n2 * 16u, &S.rbar[rs ^ 1]);
+                    }
+                    TcStage& T = S.st[fs];
+#pragma unroll
+                    for (int q = 0; q < kKc / 4; ++q) {
+                        float f0[4], f1[4];   // (k or A k, (lam/2) sin or A (lam/2) sin)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const BumpBase bb = S.base[4 * q + j][is_row ? 1 : 0];
+                            const int32_t u = bb.u0 + idx * kQi;
+                            const bool in = u > -R && u < R;
+                            const float cs = bb.c0 * rot.x - bb.s0 * rot.y;
+                            const float sn = bb.s0 * rot.x + bb.c0 * rot.y;
+                            f0[j] = in ? bb.amp * (0.5f + 0.5f * cs) : 0.f;
+                            f1[j] = in ? bb.amp * lamh * sn : 0.f;
+                        }
+                        float* hi0 = is_row ? T.Bhi : T.Ahi;
+                        float* lo0 = is_row ? T.Blo : T.Alo;
+                        float h4[4], l4[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            h4[j] = tf32_hi(f0[j]);
+                            l4[j] = tf32_hi(f0[j] - h4[j]);
+                        }
+                        const int o0 = canon(idx, q);
+                        *reinterpret_cast<float4*>((char*)hi0 + o0) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                        *reinterpret_cast<float4*>((char*)lo0 + o0) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            h4[j] = tf32_hi(f1[j]);
+                            l4[j] = tf32_hi(f1[j] - h4[j]);
+                        }
+                        const int o1 = canon(kTX + idx, q);   // kTX == kTY: second half of either operand
+                        *reinterpret_cast<float4*>((char*)hi0 + o1) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                        *reinterpret_cast<float4*>((char*)lo0 + o1) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+                    }
+                    if (tid == 0) S.stage_n[fs] = n;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_arrive(&S.full[fs]);
+                    ++produced;
+                    prod_sync();   // bases consumed before the next chunk rewrites them
+                }
+            }
+        }
+        // end of the stream for the MMA thread
+        {
+            const int fs = produced % kStages;
+            bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
+            if (tid == 0) S.stage_n[fs] = -1;
+            bar_arrive(&S.full[fs]);
+        }
+        // ======================= epilogue ====================================
+        bar_wait(&S.done, 0u, p.stats + 2);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool any = produced > 0;   // otherwise no MMA ever wrote the accumulator
+        const int m = tid;                        // accumulator row (TMEM lane)
+        const int x = tx0 + (m & (kTX - 1));
+        const bool lowm = m < kTX;                // h / Dy rows; else Dx rows
+        const int nblk = lowm ? (2 * kTY) / 32 : kTY / 32;
+        const size_t plane = (size_t)sp.W * sp.H;
+        for (int cb = 0; cb < (2 * kTY) / 32; ++cb) {
+            // warp-uniform: warps 2, 3 (Dx rows) stop after the first half
+            if (cb >= nblk) break;
+            uint32_t r[32], c[32];
+            if (any) {
+                const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cb);
+                tmem_ld32(lane_base, r);
+                tmem_ld32(lane_base + kCorrCol, c);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) r[j] = c[j] = 0u;
+            }
+            const int f = cb < kTY / 32 ? (lowm ? 0 : 1) : 2;
+            const int y0 = ty0 + 32 * (cb & (kTY / 32 - 1));
+            if (x >= sp.W) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int y = y0 + j;
+                if (y < sp.H) {
+                    const float v = __uint_as_float(r[j]) + __uint_as_float(c[j]);
+                    const size_t o = (size_t)y * sp.W + x;
+                    if (G > 1) p.partial[((size_t)g * 3 + f) * plane + o] = v;
+                    else p.out[(size_t)f * plane + o] = blend1(sp, x, y, f, v);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+cudaError_t launch_synth_tc(const PatchDev& p, const SynthParams& sp, cudaStream_t st) {
+    const size_t sm = sizeof(TcSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int G = p.groups_tc > 1 && p.partial ? p.groups_tc : 1;
+    dim3 grid((p.W + kTX - 1) / kTX, (p.H + kTY - 1) / kTY, G);
+    k_synth_tc<<<grid, kThreads, sm, st>>>(p, sp);
+    count_launches(1);
+    if (G > 1) return launch_blend(p, sp, p.partial, G, st);
+    return cudaGetLastError();
+}
+
+}  // namespace scwp

@@ -68,8 +68,9 @@ def compare_maps(got, ref, hs, tag=""):
         mx = np.abs(g - r).max()
         rel = np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-300)
         errs.append((name, mx / hs, rel))
-        assert mx <= MAX_ABS * hs, f"{tag} {name}: max|d| = {mx:.3e} ({mx / hs:.2e} Hs)"
-        assert rel <= REL_L2, f"{tag} {name}: rel L2 = {rel:.3e}"
+    for name, mx, rel in errs:
+        assert mx <= MAX_ABS, f"{tag} {name}: max|d| = {mx:.2e} Hs  (all: {errs})"
+        assert rel <= REL_L2, f"{tag} {name}: rel L2 = {rel:.3e}  (all: {errs})"
     return errs
 
 
@@ -270,3 +271,20 @@ def test_layered_variant_matches_oracle(make_cfg):
     compare_maps(sc.maps(0), ref, orc.spec.Hs(), "gather after layered")
     sc.close()
 
+
+
+@pytest.mark.parametrize("mode_name", ["SYNTH_GATHER", "SYNTH_GATHER_FP32"])
+def test_both_gather_kernels_match_oracle(mode_name):
+    """The tensor-core gather (default) and the CUDA-core gather give the
+    oracle's maps within the contract on the same frames."""
+    from paper_2511_02852_gb300 import scwp
+    cfg = wl.small_jonswap()
+    sc = make(cfg)
+    sc.set_synth_mode(getattr(scwp, mode_name))
+    orc = OracleScene(cfg)
+    for _ in range(4):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    ref, _ = orc.patch_maps(0)
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), mode_name)
+    sc.close()
