@@ -21,6 +21,18 @@ struct BucketDev {
     int32_t pad0, pad1;
 };
 
+// A bump in bin order, as the synthesis kernels stage it (32 bytes).
+// (cx, sx) = e^{-i pi (x mod 2R) / R}, (cy, sy) likewise for y: the bump's
+// share of every kernel phase pi (X - x) / R, reduced exactly modulo 2R.
+struct __align__(16) BumpRec {
+    int32_t x;        // centre x, Q16.16 cells
+    float cx, sx;
+    uint32_t id;      // bump id 2 p + k
+    int32_t y;        // centre y
+    float cy, sy;
+    float amp;        // signed amplitude (+A crest, -A trough)
+};
+
 // Device state of one patch.
 struct PatchDev {
     int W = 0, H = 0, nb = 0, nth = 0, cap = 0;
@@ -46,7 +58,7 @@ struct PatchDev {
     int nblk_s = 0;
     int key_bits = 16;
     uint32_t* offsets = nullptr;          // [total_bins + 1]
-    int4* rec = nullptr;                  // [2 cap] bump records in bin order
+    BumpRec* rec = nullptr;               // [2 cap] bump records in bin order
     float* out = nullptr;                 // [3][H][W] blended maps
     float* partial = nullptr;             // [groups][3][H][W] per-bucket-group sums (groups > 1)
     int groups = 1;                       // bucket groups of the CUDA-core synthesis

@@ -35,16 +35,16 @@ struct LayerGeom {
     float lamh;
 };
 
-__global__ void k_layer_splat(const int4* rec, const uint32_t* offsets, int key0, int key1,
+__global__ void k_layer_splat(const BumpRec* rec, const uint32_t* offsets, int key0, int key1,
                               unsigned long long* layer, LayerGeom g) {
     const int e0 = (int)offsets[key0], e1 = (int)offsets[key1];
     for (int e = e0 + blockIdx.x * blockDim.x + threadIdx.x; e < e1; e += gridDim.x * blockDim.x) {
-        const int4 r = rec[e];
+        const BumpRec r = rec[e];
         const int64_t px = (int64_t)r.x - kHalfi, py = (int64_t)r.y - kHalfi;
         const int x0 = (int)(px >> 16), y0 = (int)(py >> 16);
         const double fx = (double)(px & 0xFFFF) * (1.0 / 65536.0);
         const double fy = (double)(py & 0xFFFF) * (1.0 / 65536.0);
-        const double a = (double)__int_as_float(r.z);
+        const double a = (double)r.amp;
         const double w[4] = {(1.0 - fx) * (1.0 - fy), fx * (1.0 - fy), (1.0 - fx) * fy, fx * fy};
         const int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
 #pragma unroll

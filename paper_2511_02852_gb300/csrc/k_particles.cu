@@ -418,11 +418,24 @@ __global__ void k_records(PatchDev p, const uint32_t* vals) {
         const uint32_t bd = BD[i];
         const int4 vq = lookup_vq(p, bd);
         const float A = lookup_amp(p, bd);
-        int4 r;
+        const int32_t R = p.bk[bd >> 16].R;
+        BumpRec r;
         r.x = trough ? X[i] - vq.z : X[i];
         r.y = trough ? Y[i] - vq.w : Y[i];
-        r.z = __float_as_int(trough ? -A : A);
-        r.w = (int)id;
+        r.amp = trough ? -A : A;
+        r.id = id;
+        // e^{-i pi (x mod 2R)/R}: exact integer reduction, then sincospi
+        const int64_t R2 = 2 * (int64_t)R;
+        int64_t xm = (int64_t)r.x % R2, ym = (int64_t)r.y % R2;
+        if (xm < 0) xm += R2;
+        if (ym < 0) ym += R2;
+        float s, c;
+        sincospif((float)((double)xm / (double)R), &s, &c);
+        r.cx = c;
+        r.sx = -s;
+        sincospif((float)((double)ym / (double)R), &s, &c);
+        r.cy = c;
+        r.sy = -s;
         p.rec[e] = r;
     }
 }

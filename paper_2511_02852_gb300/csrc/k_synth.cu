@@ -66,7 +66,7 @@ struct BumpBase {                  // per bump and axis
 
 struct SynthSmem {
     FactorSlot slot[kSlotsRing];
-    int4 rec[2][kCH];              // staged bump records (16-byte aligned)
+    BumpRec rec[2][kCH];           // staged bump records (16-byte aligned)
     unsigned long long rbar[2];    // record copies: complete_tx
     unsigned long long full[kSlotsRing];   // producers -> consumers (kPThreads arrivals)
     unsigned long long empty[kSlotsRing];  // consumers -> producers (kConsumers arrivals)
@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthP
                     int off, n;
                     chunk(0, off, n);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_arrive_expect(&S.rbar[0], (uint32_t)n * 16u);
-                    bulk_g2s(&S.rec[0][0], p.rec + off, (uint32_t)n * 16u, &S.rbar[0]);
+                    mbar_arrive_expect(&S.rbar[0], (uint32_t)(n * sizeof(BumpRec)));
+                    bulk_g2s(&S.rec[0][0], p.rec + off, (uint32_t)(n * sizeof(BumpRec)), &S.rbar[0]);
                 }
                 for (int c = 0; c < nchunks; ++c) {
                     const int rs = c & 1;
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthP
                     if (!ok_r) S.stop = 1;
                     // bases (warp 0 of the producers: x, warp 1: y) and masks
                     if (lane < n && !S.stop) {
-                        const int4 rc = S.rec[rs][lane];
+                        const BumpRec rc = S.rec[rs][lane];
                         const int ax = ptid >> 5;
                         const int32_t u0 = ax ? Ylo - rc.y : Xlo - rc.x;
                         float sn, cs;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthP
                         bb.c0 = cs;
                         bb.s0 = sn;
                         bb.u0 = u0;
-                        bb.amp = ax ? __int_as_float(rc.z) : 1.f;
+                        bb.amp = ax ? rc.amp : 1.f;
                         S.base[lane][ax] = bb;
                     }
                     const int fs = produced % kSlotsRing;
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthP
                     if (!ok_e) S.stop = 1;
                     FactorSlot& F = S.slot[fs];
                     if (ptid < n && !S.stop) {
-                        const int4 rc = S.rec[rs][ptid];
+                        const BumpRec rc = S.rec[rs][ptid];
                         const int xl = span_lo(rc.x, R) - tx0, xh = span_hi(rc.x, R) - tx0;
                         const int yl = span_lo(rc.y, R) - ty0, yh = span_hi(rc.y, R) - ty0;
                         uint32_t m = 0;
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthP
                         int off2, n2;
                         chunk(c + 1, off2, n2);
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        mbar_arrive_expect(&S.rbar[rs ^ 1], (uint32_t)n2 * 16u);
-                        bulk_g2s(&S.rec[rs ^ 1][0], p.rec + off2, (uint32_t)n2 * 16u, &S.rbar[rs ^ 1]);
+                        mbar_arrive_expect(&S.rbar[rs ^ 1], (uint32_t)(n2 * sizeof(BumpRec)));
+                        bulk_g2s(&S.rec[rs ^ 1][0], p.rec + off2, (uint32_t)(n2 * sizeof(BumpRec)), &S.rbar[rs ^ 1]);
                     }
                     // factors: column ptid and row ptid of every bump
                     for (int b = 0; b < n; ++b) {

@@ -16,11 +16,15 @@
 // hi*lo + lo*hi in a second one, so the large sum takes one rounding per step
 // and the two are added in FP32 when read out.
 //
-// Warps 0-3 produce the operands of each 16-bump chunk into a 2-stage ring in
+// Warps 0-3 produce the operands of each 16-bump chunk into a 3-stage ring in
 // shared memory (no-swizzle K-major canonical layout: 8-row x 16-byte core
-// matrices, 128 B apart along K, 512 B apart along rows), from bump records
-// staged by bulk async copy and one sincospi per bump and axis rotated by the
-// bucket's e^{i pi n Q / R} table.  One thread of warp 4 issues the MMAs and
+// matrices, 128 B apart along K, 512 B apart along rows) from bump records
+// staged two chunks ahead by bulk async copy.  Each producer thread owns one
+// tile row or column; the kernel phase pi (X_n - x_b)/R of its sample is the
+// product of its own e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the
+// bump's e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half
+// per role), so a sample costs one complex multiply and an integer support
+// test.  One thread of warp 4 issues the MMAs and
 // commits each stage back to the producers; after the last stage the
 // producer warps read the accumulator out of tensor memory (tcgen05.ld) and
 // write the bucket group's partial sums, or the blended maps.  All waits are
@@ -38,6 +42,7 @@ constexpr int kTX = 64;            // tile columns (x): the MMA's M = 2 * kTX
 constexpr int kTY = 64;            // tile rows (y):    the MMA's N = 2 * kTY
 constexpr int kKc = 16;            // bumps per stage (two K = 8 steps)
 constexpr int kStages = 3;
+constexpr int kRecSlots = 3;       // staged record chunks (prefetch distance 2)
 constexpr int kProdThreads = 128;  // warps 0-3
 constexpr int kThreads = kProdThreads + 32;
 constexpr int kMaxRanges = 64;
@@ -54,17 +59,11 @@ struct __align__(1024) TcStage {
     float Blo[2 * kTY * kKc];
 };
 
-struct BumpBase {
-    float c0, s0;
-    int32_t u0;
-    float amp;
-};
-
 struct TcSmem {
     TcStage st[kStages];
-    int4 rec[2][kKc];
-    BumpBase base[kKc][2];
-    unsigned long long rbar[2];
+    BumpRec rec[kRecSlots][kKc];
+    unsigned long long rbar[kRecSlots];  // record copies (complete_tx)
+    unsigned long long rfree[kRecSlots]; // producers done with a record chunk (128 arrivals)
     unsigned long long full[kStages];    // producers -> MMA thread (128 arrivals)
     unsigned long long empty[kStages];   // MMA commit -> producers (1 arrival)
     unsigned long long done;             // final MMA commit -> epilogue
@@ -73,7 +72,6 @@ struct TcSmem {
     int rlen[kMaxRanges];
     int cpre[kMaxRanges + 1];
     uint32_t tmem;
-    int stop;
 };
 static_assert(sizeof(TcStage) % 1024 == 0, "stage alignment");
 static_assert(offsetof(TcSmem, rec) % 16 == 0, "record staging alignment");
@@ -187,14 +185,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     const int b_begin = (g * sp.nb) / G, b_end = ((g + 1) * sp.nb) / G;
 
     if (tid == 0) {
-        bar_init(&S.rbar[0], 1);
-        bar_init(&S.rbar[1], 1);
+        for (int k = 0; k < kRecSlots; ++k) {
+            bar_init(&S.rbar[k], 1);
+            bar_init(&S.rfree[k], kProdThreads);
+        }
         for (int k = 0; k < kStages; ++k) {
             bar_init(&S.full[k], kProdThreads);
             bar_init(&S.empty[k], 1);
         }
         bar_init(&S.done, 1);
-        S.stop = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 4) {
@@ -247,13 +246,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
         const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
         const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
         const float lamh = sp.lam_half;
-        uint32_t rpar[2] = {0u, 0u};
-        int produced = 0;
-        bool dead = false;
         // threads 0..63 build row tid (A k(v), A (lam/2) sin);
         // threads 64..127 build column tid - 64 (k(u), (lam/2) sin)
         const bool is_row = tid < kTY;
         const int idx = is_row ? tid : tid - kTY;
+        const int32_t pos = (is_row ? Ylo : Xlo) + idx * kQi;   // this thread's texel centre
+        int produced = 0;      // stages filled
+        int gc = 0;            // record chunks consumed (ring position)
+        int issued = 0;        // record chunks whose copy was issued (thread 0)
+        bool dead = false;
+        // issue the bulk copy of chunk `c` of the current batch into its slot
+        auto issue = [&](int c, int g_abs) {
+            int k = 0;
+            while (S.cpre[k + 1] <= c) ++k;
+            const int off = S.rstart[k] + (c - S.cpre[k]) * kKc;
+            const int n = min(kKc, S.rstart[k] + S.rlen[k] - off);
+            const int slot = g_abs % kRecSlots;
+            if (g_abs >= kRecSlots)   // the slot's previous chunk must be fully read
+                bar_wait(&S.rfree[slot], (uint32_t)((g_abs / kRecSlots - 1) & 1), p.stats + 2);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
+            bulk_g2s(&S.rec[slot][0], p.rec + off, (uint32_t)(n * sizeof(BumpRec)), &S.rbar[slot]);
+            issued = g_abs + 1;
+        };
         for (int bi = b_begin; bi < b_end && !dead; ++bi) {
             const BucketDev bk = p.bk[bi];
             int bx_lo = (int)(((int64_t)Xlo) / bk.C);
@@ -265,9 +280,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
             if (bx_hi > bk.nbx - 1) bx_hi = bk.nbx - 1;
             if (by_hi > bk.nby - 1) by_hi = bk.nby - 1;
             if (bx_lo > bx_hi || by_lo > by_hi) continue;
-            const float invR = bk.invR;
             const int32_t R = bk.R;
-            const float2 rot = p.rot[bi * kRotN + idx];   // e^{i pi idx Q / R}
+            // this thread's phase factor e^{i pi (pos mod 2R) / R}
+            float st, ct;
+            {
+                const int64_t R2 = 2 * (int64_t)R;
+                int64_t pm = (int64_t)pos % R2;
+                if (pm < 0) pm += R2;
+                sincospif((float)((double)pm / (double)R), &st, &ct);
+            }
             for (int byb = by_lo; byb <= by_hi && !dead; byb += kMaxRanges) {
                 const int nr = min(kMaxRanges, by_hi - byb + 1);
                 for (int k = tid; k < nr; k += kProdThreads) {
@@ -289,74 +310,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                 prod_sync();
                 const int nchunks = S.cpre[nr];
                 if (nchunks == 0) continue;
-                auto chunk = [&](int c, int& off, int& n) {
+                if (tid == 0) {
+                    issue(0, gc);
+                    if (nchunks > 1) issue(1, gc + 1);
+                }
+                for (int c = 0; c < nchunks; ++c, ++gc) {
                     int k = 0;
                     while (S.cpre[k + 1] <= c) ++k;
-                    off = S.rstart[k] + (c - S.cpre[k]) * kKc;
-                    n = min(kKc, S.rstart[k] + S.rlen[k] - off);
-                };
-                if (tid == 0) {
-                    int off, n;
-                    chunk(0, off, n);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_arrive_tx(&S.rbar[0], (uint32_t)n * 16u);
-                    bulk_g2s(&S.rec[0][0], p.rec + off, (uint32_t)n * 16u, &S.rbar[0]);
-                }
-                for (int c = 0; c < nchunks; ++c) {
-                    const int rs = c & 1;
-                    int off, n;
-                    chunk(c, off, n);
-                    if (!bar_wait(&S.rbar[rs], rpar[rs], p.stats + 2)) S.stop = 1;
-                    rpar[rs] ^= 1u;
-                    if (tid < 2 * kKc) {
-                        const int b = tid & (kKc - 1), ax = tid >> 4;
-                        BumpBase bb;
-                        if (b < n && !S.stop) {
-                            const int4 rc = S.rec[rs][b];
-                            const int32_t u0 = ax ? Ylo - rc.y : Xlo - rc.x;
-                            float sn, cs;
-                            sincospif((float)u0 * invR, &sn, &cs);
-                            bb.c0 = cs;
-                            bb.s0 = sn;
-                            bb.u0 = u0;
-                            bb.amp = ax ? __int_as_float(rc.z) : 1.f;
-                        } else {
-                            bb.c0 = bb.s0 = 0.f;
-                            bb.u0 = 0x40000000;      // outside every support: the factor is 0
-                            bb.amp = 0.f;
-                        }
-                        S.base[b][ax] = bb;
-                    }
+                    const int n = min(kKc, S.rlen[k] - (c - S.cpre[k]) * kKc);
+                    const int rs = gc % kRecSlots;
+                    bool ok = bar_wait(&S.rbar[rs], (uint32_t)((gc / kRecSlots) & 1), p.stats + 2);
                     const int fs = produced % kStages;
-                    if (!bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2)) S.stop = 1;
-                    prod_sync();   // bases visible, record slot rs free
-                    if (S.stop) {
-                        dead = true;
+                    ok = ok && bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        dead = true;   // this warp stops; the others time out in turn
                         break;
                     }
-                    if (tid == 0 && c + 1 < nchunks) {
-                        int off2, n2;
-                        chunk(c + 1, off2, n2);
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        bar_arrive_tx(&S.rbar[rs ^ 1], (uint32_t)n2 * 16u);
-                        bulk_g2s(&S.rec[rs ^ 1][0], p.rec + off2, (uint32_t)n2 * 16u, &S.rbar[rs ^ 1]);
-                    }
                     TcStage& T = S.st[fs];
+                    // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp}
+                    const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
+                    float* hi0 = is_row ? T.Bhi : T.Ahi;
+                    float* lo0 = is_row ? T.Blo : T.Alo;
 #pragma unroll
                     for (int q = 0; q < kKc / 4; ++q) {
                         float f0[4], f1[4];   // (k or A k, (lam/2) sin or A (lam/2) sin)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const BumpBase bb = S.base[4 * q + j][is_row ? 1 : 0];
-                            const int32_t u = bb.u0 + idx * kQi;
-                            const bool in = u > -R && u < R;
-                            const float cs = bb.c0 * rot.x - bb.s0 * rot.y;
-                            const float sn = bb.s0 * rot.x + bb.c0 * rot.y;
-                            f0[j] = in ? bb.amp * (0.5f + 0.5f * cs) : 0.f;
-                            f1[j] = in ? bb.amp * lamh * sn : 0.f;
+                            const int b = 4 * q + j;
+                            const float4 r = rc[2 * b];
+                            const int32_t u = pos - __float_as_int(r.x);
+                            const bool in = b < n && u > -R && u < R;
+                            const float amp = is_row ? r.w : 1.f;
+                            const float cs = ct * r.y - st * r.z;   // cos pi u / R
+                            const float sn = st * r.y + ct * r.z;   // sin pi u / R
+                            f0[j] = in ? amp * (0.5f + 0.5f * cs) : 0.f;
+                            f1[j] = in ? amp * lamh * sn : 0.f;
                         }
-                        float* hi0 = is_row ? T.Bhi : T.Ahi;
-                        float* lo0 = is_row ? T.Blo : T.Alo;
                         float h4[4], l4[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
@@ -375,14 +364,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                         *reinterpret_cast<float4*>((char*)hi0 + o1) = make_float4(h4[0], h4[1], h4[2], h4[3]);
                         *reinterpret_cast<float4*>((char*)lo0 + o1) = make_float4(l4[0], l4[1], l4[2], l4[3]);
                     }
+                    bar_arrive(&S.rfree[rs]);
                     if (tid == 0) S.stage_n[fs] = n;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(&S.full[fs]);
                     ++produced;
-                    prod_sync();   // bases consumed before the next chunk rewrites them
+                    // prefetch two chunks ahead; the slot last held chunk c - 1
+                    if (tid == 0 && c + 2 < nchunks) issue(c + 2, gc + 2);
                 }
+                prod_sync();   // every producer done with this batch's chunk list
             }
         }
+        // after a timeout, let any record copy still in flight land before
+        // this CTA's shared memory can be reused
+        if (tid == 0)
+            for (int g2 = gc; g2 < issued; ++g2)
+                bar_wait(&S.rbar[g2 % kRecSlots], (uint32_t)((g2 / kRecSlots) & 1), p.stats + 2);
         // end of the stream for the MMA thread
         {
             const int fs = produced % kStages;
