@@ -43,7 +43,8 @@ constexpr int kTY = 64;            // tile rows (y):    the MMA's N = 2 * kTY
 constexpr int kKc = 16;            // bumps per stage (two K = 8 steps)
 constexpr int kStages = 3;
 constexpr int kRecSlots = 3;       // staged record chunks (prefetch distance 2)
-constexpr int kProdThreads = 128;  // warps 0-3
+constexpr int kProdThreads = 256;  // warps 0-7: two halves of each chunk
+constexpr int kMmaWarp = kProdThreads / 32;
 constexpr int kThreads = kProdThreads + 32;
 constexpr int kMaxRanges = 64;
 constexpr int kTmemCols = 256;     // main accumulator at column 0, corrections at 2 * kTY
@@ -63,14 +64,14 @@ struct TcSmem {
     TcStage st[kStages];
     BumpRec rec[kRecSlots][kKc];
     unsigned long long rbar[kRecSlots];  // record copies (complete_tx)
-    unsigned long long rfree[kRecSlots]; // producers done with a record chunk (128 arrivals)
-    unsigned long long full[kStages];    // producers -> MMA thread (128 arrivals)
+    unsigned long long rfree[kRecSlots]; // producers done with a record chunk (kProdThreads arrivals)
+    unsigned long long full[kStages];    // producers -> MMA thread (kProdThreads arrivals)
     unsigned long long empty[kStages];   // MMA commit -> producers (1 arrival)
     unsigned long long done;             // final MMA commit -> epilogue
     int stage_n[kStages];                // bumps in the stage; -1 ends the stream
     int rstart[kMaxRanges];
     int rlen[kMaxRanges];
-    int cpre[kMaxRanges + 1];
+    int cum[kMaxRanges + 1];             // prefix of the range lengths
     uint32_t tmem;
 };
 static_assert(sizeof(TcStage) % 1024 == 0, "stage alignment");
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
         bar_init(&S.done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem)),
                      "n"(kTmemCols)
                      : "memory");
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = S.tmem;
 
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         // ======================= MMA issuer ==================================
         if (lane == 0) {
             const uint32_t idesc =
@@ -246,27 +247,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
         const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
         const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
         const float lamh = sp.lam_half;
-        // threads 0..63 build row tid (A k(v), A (lam/2) sin);
-        // threads 64..127 build column tid - 64 (k(u), (lam/2) sin)
-        const bool is_row = tid < kTY;
-        const int idx = is_row ? tid : tid - kTY;
+        // producer thread t builds bumps 8 (t >> 7) .. +7 of each chunk for
+        // row (t & 127) (A k(v), A (lam/2) sin) if (t & 127) < 64, else for
+        // column (t & 127) - 64 (k(u), (lam/2) sin)
+        const int half = tid >> 7, tq = tid & 127;
+        const bool is_row = tq < kTY;
+        const int idx = is_row ? tq : tq - kTY;
         const int32_t pos = (is_row ? Ylo : Xlo) + idx * kQi;   // this thread's texel centre
         int produced = 0;      // stages filled
         int gc = 0;            // record chunks consumed (ring position)
         int issued = 0;        // record chunks whose copy was issued (thread 0)
         bool dead = false;
-        // issue the bulk copy of chunk `c` of the current batch into its slot
-        auto issue = [&](int c, int g_abs) {
-            int k = 0;
-            while (S.cpre[k + 1] <= c) ++k;
-            const int off = S.rstart[k] + (c - S.cpre[k]) * kKc;
-            const int n = min(kKc, S.rstart[k] + S.rlen[k] - off);
+        // issue the bulk copies of chunk `c` of the current batch into its slot:
+        // bumps [16c, 16c + n) of the batch's concatenated bin-row ranges
+        auto issue = [&](int c, int g_abs, int total) {
+            const int lo = c * kKc, n = min(kKc, total - lo);
             const int slot = g_abs % kRecSlots;
             if (g_abs >= kRecSlots)   // the slot's previous chunk must be fully read
                 bar_wait(&S.rfree[slot], (uint32_t)((g_abs / kRecSlots - 1) & 1), p.stats + 2);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
-            bulk_g2s(&S.rec[slot][0], p.rec + off, (uint32_t)(n * sizeof(BumpRec)), &S.rbar[slot]);
+            int k = 0;
+            while (S.cum[k + 1] <= lo) ++k;
+            for (int at = lo; at < lo + n; ++k) {
+                const int e = min(S.cum[k + 1], lo + n);
+                if (e > at) {
+                    bulk_g2s(&S.rec[slot][at - lo], p.rec + S.rstart[k] + (at - S.cum[k]),
+                             (uint32_t)((e - at) * sizeof(BumpRec)), &S.rbar[slot]);
+                    at = e;
+                }
+            }
             issued = g_abs + 1;
         };
         for (int bi = b_begin; bi < b_end && !dead; ++bi) {
@@ -302,22 +312,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                 if (tid == 0) {
                     int a = 0;
                     for (int k = 0; k < nr; ++k) {
-                        S.cpre[k] = a;
-                        a += (S.rlen[k] + kKc - 1) / kKc;
+                        S.cum[k] = a;
+                        a += S.rlen[k];
                     }
-                    S.cpre[nr] = a;
+                    S.cum[nr] = a;
                 }
                 prod_sync();
-                const int nchunks = S.cpre[nr];
-                if (nchunks == 0) continue;
+                const int total = S.cum[nr];
+                const int nchunks = (total + kKc - 1) / kKc;
+                if (nchunks == 0) {
+                    prod_sync();
+                    continue;
+                }
                 if (tid == 0) {
-                    issue(0, gc);
-                    if (nchunks > 1) issue(1, gc + 1);
+                    issue(0, gc, total);
+                    if (nchunks > 1) issue(1, gc + 1, total);
                 }
                 for (int c = 0; c < nchunks; ++c, ++gc) {
-                    int k = 0;
-                    while (S.cpre[k + 1] <= c) ++k;
-                    const int n = min(kKc, S.rlen[k] - (c - S.cpre[k]) * kKc);
+                    const int n = min(kKc, total - c * kKc);
                     const int rs = gc % kRecSlots;
                     bool ok = bar_wait(&S.rbar[rs], (uint32_t)((gc / kRecSlots) & 1), p.stats + 2);
                     const int fs = produced % kStages;
@@ -332,7 +344,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                     float* hi0 = is_row ? T.Bhi : T.Ahi;
                     float* lo0 = is_row ? T.Blo : T.Alo;
 #pragma unroll
-                    for (int q = 0; q < kKc / 4; ++q) {
+                    for (int qq = 0; qq < kKc / 8; ++qq) {
+                        const int q = 2 * half + qq;
                         float f0[4], f1[4];   // (k or A k, (lam/2) sin or A (lam/2) sin)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
@@ -370,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                     bar_arrive(&S.full[fs]);
                     ++produced;
                     // prefetch two chunks ahead; the slot last held chunk c - 1
-                    if (tid == 0 && c + 2 < nchunks) issue(c + 2, gc + 2);
+                    if (tid == 0 && c + 2 < nchunks) issue(c + 2, gc + 2, total);
                 }
                 prod_sync();   // every producer done with this batch's chunk list
             }
@@ -391,17 +404,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
         bar_wait(&S.done, 0u, p.stats + 2);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool any = produced > 0;   // otherwise no MMA ever wrote the accumulator
-        const int m = tid;                        // accumulator row (TMEM lane)
+        // warp w reads TMEM lane quarter w & 3 (accumulator rows); the two
+        // groups of four warps split the column blocks of those rows
+        const int quarter = warp & 3, grp = warp >> 2;
+        const int m = 32 * quarter + lane;        // accumulator row (TMEM lane)
         const int x = tx0 + (m & (kTX - 1));
         const bool lowm = m < kTX;                // h / Dy rows; else Dx rows
         const int nblk = lowm ? (2 * kTY) / 32 : kTY / 32;
+        const int cb_lo = grp * (nblk / 2), cb_hi = cb_lo + nblk / 2;
         const size_t plane = (size_t)sp.W * sp.H;
-        for (int cb = 0; cb < (2 * kTY) / 32; ++cb) {
-            // warp-uniform: warps 2, 3 (Dx rows) stop after the first half
-            if (cb >= nblk) break;
+        for (int cb = cb_lo; cb < cb_hi; ++cb) {
             uint32_t r[32], c[32];
             if (any) {
-                const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cb);
+                const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * cb);
                 tmem_ld32(lane_base, r);
                 tmem_ld32(lane_base + kCorrCol, c);
             } else {
@@ -425,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 4)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
 }
 
