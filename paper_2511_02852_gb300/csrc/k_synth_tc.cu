@@ -19,7 +19,7 @@
 // Warps 0-3 produce the operands of each 16-bump chunk into a 3-stage ring in
 // shared memory (no-swizzle K-major canonical layout: 8-row x 16-byte core
 // matrices, 128 B apart along K, 512 B apart along rows) from bump records
-// staged two chunks ahead by bulk async copy.  Each producer thread owns one
+// staged six chunks ahead by bulk async copy.  Each producer thread owns one
 // tile row or column; the kernel phase pi (X_n - x_b)/R of its sample is the
 // product of its own e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the
 // bump's e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half
@@ -42,7 +42,8 @@ constexpr int kTX = 64;            // tile columns (x): the MMA's M = 2 * kTX
 constexpr int kTY = 64;            // tile rows (y):    the MMA's N = 2 * kTY
 constexpr int kKc = 16;            // bumps per stage (two K = 8 steps)
 constexpr int kStages = 3;
-constexpr int kRecSlots = 3;       // staged record chunks (prefetch distance 2)
+constexpr int kRecSlots = 8;       // staged record chunks
+constexpr int kAhead = 6;          // record prefetch distance (chunks)
 constexpr int kProdThreads = 256;  // warps 0-7: two halves of each chunk
 constexpr int kMmaWarp = kProdThreads / 32;
 constexpr int kThreads = kProdThreads + 32;
@@ -143,6 +144,58 @@ __device__ __forceinline__ float tf32_hi(float x) {
 
 // byte offset of element (row r, k) in a K-major canonical operand
 __device__ __forceinline__ int canon(int r, int kq) { return kq * 128 + (r >> 3) * (int)kSBO + (r & 7) * 16; }
+
+// Operand rows of one producer thread for its 8 bumps of a chunk.  ROW: the
+// tile row whose B rows are A k(v) and A (lam/2) sin(pi v/R); otherwise the
+// tile column whose A rows are k(u) and (lam/2) sin(pi u/R).  `rec` points at
+// this role's 16-byte half of each 32-byte record: {x, cx, sx, id} or
+// {y, cy, sy, amp}; (ct, st) = e^{i pi (pos mod 2R)/R}.
+template <bool ROW>
+__device__ __forceinline__ void gen_half_chunk(float* hi, float* lo, const float4* rec, int half, int idx,
+                                               int32_t pos, int32_t R, float ct, float st, float lamh) {
+    const uint32_t span = (uint32_t)(2 * R - 1);
+#pragma unroll
+    for (int qq = 0; qq < kKc / 8; ++qq) {
+        const int q = 2 * half + qq;
+        float f0[4], f1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 r = rec[2 * (4 * q + j)];
+            const int32_t u = pos - __float_as_int(r.x);
+            const bool in = (uint32_t)(u + R - 1) < span;          // -R < u < R
+            const float cs = ct * r.y - st * r.z;                  // cos pi u / R
+            const float sn = st * r.y + ct * r.z;                  // sin pi u / R
+            float a0, a1;
+            if (ROW) {
+                const float ha = 0.5f * r.w;
+                a0 = fmaf(ha, cs, ha);
+                a1 = (r.w * lamh) * sn;
+            } else {
+                a0 = fmaf(0.5f, cs, 0.5f);
+                a1 = lamh * sn;
+            }
+            f0[j] = in ? a0 : 0.f;
+            f1[j] = in ? a1 : 0.f;
+        }
+        float h4[4], l4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            h4[j] = tf32_hi(f0[j]);
+            l4[j] = tf32_hi(f0[j] - h4[j]);
+        }
+        const int o0 = canon(idx, q);
+        *reinterpret_cast<float4*>((char*)hi + o0) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+        *reinterpret_cast<float4*>((char*)lo + o0) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            h4[j] = tf32_hi(f1[j]);
+            l4[j] = tf32_hi(f1[j] - h4[j]);
+        }
+        const int o1 = canon(kTX + idx, q);   // kTX == kTY: second half of either operand
+        *reinterpret_cast<float4*>((char*)hi + o1) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+        *reinterpret_cast<float4*>((char*)lo + o1) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+    }
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
     asm volatile(
@@ -265,6 +318,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
             const int slot = g_abs % kRecSlots;
             if (g_abs >= kRecSlots)   // the slot's previous chunk must be fully read
                 bar_wait(&S.rfree[slot], (uint32_t)((g_abs / kRecSlots - 1) & 1), p.stats + 2);
+            for (int b = n; b < kKc; ++b) {   // sentinels: far outside every support
+                BumpRec z;
+                z.x = z.y = 0x40000000;
+                z.cx = z.sx = z.cy = z.sy = z.amp = 0.f;
+                z.id = 0xFFFFFFFFu;
+                S.rec[slot][b] = z;
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
             int k = 0;
@@ -324,10 +384,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                     prod_sync();
                     continue;
                 }
-                if (tid == 0) {
-                    issue(0, gc, total);
-                    if (nchunks > 1) issue(1, gc + 1, total);
-                }
+                if (tid == 0)
+                    for (int c0 = 0; c0 < nchunks && c0 < kAhead; ++c0) issue(c0, gc + c0, total);
                 for (int c = 0; c < nchunks; ++c, ++gc) {
                     const int n = min(kKc, total - c * kKc);
                     const int rs = gc % kRecSlots;
@@ -339,51 +397,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                         break;
                     }
                     TcStage& T = S.st[fs];
-                    // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp}
+                    // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp};
+                    // slots past n hold sentinel records outside every support
                     const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
-                    float* hi0 = is_row ? T.Bhi : T.Ahi;
-                    float* lo0 = is_row ? T.Blo : T.Alo;
-#pragma unroll
-                    for (int qq = 0; qq < kKc / 8; ++qq) {
-                        const int q = 2 * half + qq;
-                        float f0[4], f1[4];   // (k or A k, (lam/2) sin or A (lam/2) sin)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int b = 4 * q + j;
-                            const float4 r = rc[2 * b];
-                            const int32_t u = pos - __float_as_int(r.x);
-                            const bool in = b < n && u > -R && u < R;
-                            const float amp = is_row ? r.w : 1.f;
-                            const float cs = ct * r.y - st * r.z;   // cos pi u / R
-                            const float sn = st * r.y + ct * r.z;   // sin pi u / R
-                            f0[j] = in ? amp * (0.5f + 0.5f * cs) : 0.f;
-                            f1[j] = in ? amp * lamh * sn : 0.f;
-                        }
-                        float h4[4], l4[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            h4[j] = tf32_hi(f0[j]);
-                            l4[j] = tf32_hi(f0[j] - h4[j]);
-                        }
-                        const int o0 = canon(idx, q);
-                        *reinterpret_cast<float4*>((char*)hi0 + o0) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-                        *reinterpret_cast<float4*>((char*)lo0 + o0) = make_float4(l4[0], l4[1], l4[2], l4[3]);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            h4[j] = tf32_hi(f1[j]);
-                            l4[j] = tf32_hi(f1[j] - h4[j]);
-                        }
-                        const int o1 = canon(kTX + idx, q);   // kTX == kTY: second half of either operand
-                        *reinterpret_cast<float4*>((char*)hi0 + o1) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-                        *reinterpret_cast<float4*>((char*)lo0 + o1) = make_float4(l4[0], l4[1], l4[2], l4[3]);
-                    }
+                    if (is_row)
+                        gen_half_chunk<true>(T.Bhi, T.Blo, rc, half, idx, pos, R, ct, st, lamh);
+                    else
+                        gen_half_chunk<false>(T.Ahi, T.Alo, rc, half, idx, pos, R, ct, st, lamh);
                     bar_arrive(&S.rfree[rs]);
                     if (tid == 0) S.stage_n[fs] = n;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(&S.full[fs]);
                     ++produced;
-                    // prefetch two chunks ahead; the slot last held chunk c - 1
-                    if (tid == 0 && c + 2 < nchunks) issue(c + 2, gc + 2, total);
+                    // prefetch kAhead chunks ahead into the slot that last
+                    // held chunk c + kAhead - kRecSlots
+                    if (tid == 0 && c + kAhead < nchunks) issue(c + kAhead, gc + kAhead, total);
                 }
                 prod_sync();   // every producer done with this batch's chunk list
             }

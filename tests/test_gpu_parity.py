@@ -68,6 +68,7 @@ def compare_maps(got, ref, hs, tag=""):
         mx = np.abs(g - r).max()
         rel = np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-300)
         errs.append((name, mx / hs, rel))
+    print(f"[parity] {tag}: " + ", ".join(f"{n} max {m:.2e} Hs rel {r:.2e}" for n, m, r in errs))
     for name, mx, rel in errs:
         assert mx <= MAX_ABS, f"{tag} {name}: max|d| = {mx:.2e} Hs  (all: {errs})"
         assert rel <= REL_L2, f"{tag} {name}: rel L2 = {rel:.3e}  (all: {errs})"
