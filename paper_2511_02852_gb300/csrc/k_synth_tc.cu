@@ -6,29 +6,35 @@
 //   Dy(x,y) = sum_b k_b(u_x) A_b (lam/2) sin(pi v_y/R)
 // are one dense contraction over bumps,
 //   D[m][n] = sum_b Aop[m][b] Bop[n][b],
-//   Aop = [ k(u_x) ; (lam/2) sin(pi u_x/R) ]           (128 x K: 64 columns x 2)
-//   Bop = [ A k(v_y) ; A (lam/2) sin(pi v_y/R) ]       (128 x K: 64 rows x 2)
-// whose quadrants are h^T, Dx^T, Dy^T (the fourth is unused), computed by
+//   Aop = [ 1 + cos(pi u_x/R) ; sin(pi u_x/R) ]              (128 x K: 64 columns x 2)
+//   Bop = [ A (1 + cos(pi v_y/R)) ; A sin(pi v_y/R) ]        (128 x K: 64 rows x 2)
+// whose quadrants are 4 h^T, (2/lam) Dx^T, (2/lam) Dy^T (the fourth is
+// unused; the constant factors are applied when the sums are read out),
+// computed by
 // tcgen05.mma (M = 128, N = 128, K = 8, kind::tf32) into FP32 accumulators in
-// tensor memory.  Each operand is split as hi + lo, both rounded to TF32 to
-// nearest (hi = tf32(x), lo = tf32(x - hi): 22 significant bits together);
+// tensor memory.  Each operand is split as hi + lo, hi = x truncated to TF32
+// and lo = x - hi (exact; the MMA takes its TF32 bits: 22 significant bits
+// together);
 // hi*hi accumulates in one accumulator and the small corrections
 // hi*lo + lo*hi in a second one, so the large sum takes one rounding per step
 // and the two are added in FP32 when read out.
 //
-// Warps 0-3 produce the operands of each 16-bump chunk into a 3-stage ring in
+// Warps 0-7 produce the operands of each 16-bump chunk into a 3-stage ring in
 // shared memory (no-swizzle K-major canonical layout: 8-row x 16-byte core
 // matrices, 128 B apart along K, 512 B apart along rows) from bump records
-// staged six chunks ahead by bulk async copy.  Each producer thread owns one
-// tile row or column; the kernel phase pi (X_n - x_b)/R of its sample is the
-// product of its own e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the
-// bump's e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half
-// per role), so a sample costs one complex multiply and an integer support
-// test.  One thread of warp 4 issues the MMAs and
-// commits each stage back to the producers; after the last stage the
-// producer warps read the accumulator out of tensor memory (tcgen05.ld) and
-// write the bucket group's partial sums, or the blended maps.  All waits are
-// bounded in time; a timeout sets an error flag.
+// that warp 9 stages in an eight-slot ring: it walks the bin ranges that
+// reach the tile, bucket by bucket, and bulk-copies each chunk's records with
+// the chunk's size and kernel radius beside them.  Each producer thread owns
+// one tile row or column and one half of the chunk's bumps; the kernel phase
+// pi (X_n - x_b)/R of its sample is the product of its own
+// e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the bump's
+// e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half per
+// role), so a sample costs one complex multiply and an integer support test.
+// One thread of warp 8 issues the MMAs and commits each stage back to the
+// producers; after the last stage the producer warps read the accumulator
+// out of tensor memory (tcgen05.ld) and write the bucket group's partial
+// sums, or the blended maps.  All waits are bounded in time; a timeout sets
+// an error flag.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -43,11 +49,12 @@ constexpr int kTY = 64;            // tile rows (y):    the MMA's N = 2 * kTY
 constexpr int kKc = 16;            // bumps per stage (two K = 8 steps)
 constexpr int kStages = 3;
 constexpr int kRecSlots = 8;       // staged record chunks
-constexpr int kAhead = 6;          // record prefetch distance (chunks)
 constexpr int kProdThreads = 256;  // warps 0-7: two halves of each chunk
-constexpr int kMmaWarp = kProdThreads / 32;
-constexpr int kThreads = kProdThreads + 32;
-constexpr int kMaxRanges = 64;
+constexpr int kProdWarps = kProdThreads / 32;
+constexpr int kMmaWarp = kProdWarps;        // warp 8: MMA issue
+constexpr int kLoadWarp = kProdWarps + 1;   // warp 9: bin ranges and record copies
+constexpr int kThreads = kProdThreads + 64;
+constexpr int kBatchRows = 32;     // bin rows per range batch: one per loader lane
 constexpr int kTmemCols = 256;     // main accumulator at column 0, corrections at 2 * kTY
 constexpr uint32_t kCorrCol = 2 * kTY;
 constexpr int32_t kQi = 65536, kHalfi = 32768;
@@ -61,23 +68,29 @@ struct __align__(1024) TcStage {
     float Blo[2 * kTY * kKc];
 };
 
+// what the loader tells the producers about a staged record chunk
+struct ChunkMeta {
+    int n;          // bumps in the chunk (the rest of the slot holds sentinels); -1 ends the stream
+    int32_t R;      // kernel radius of the chunk's bucket (Q16.16)
+};
+
 struct TcSmem {
     TcStage st[kStages];
     BumpRec rec[kRecSlots][kKc];
-    unsigned long long rbar[kRecSlots];  // record copies (complete_tx)
-    unsigned long long rfree[kRecSlots]; // producers done with a record chunk (kProdThreads arrivals)
-    unsigned long long full[kStages];    // producers -> MMA thread (kProdThreads arrivals)
+    ChunkMeta meta[kRecSlots];
+    unsigned long long rbar[kRecSlots];  // loader -> producers: metadata and record copies (complete_tx)
+    unsigned long long rfree[kRecSlots]; // producers done with a record chunk (one arrival per warp)
+    unsigned long long full[kStages];    // producers -> MMA thread (one arrival per warp)
     unsigned long long empty[kStages];   // MMA commit -> producers (1 arrival)
     unsigned long long done;             // final MMA commit -> epilogue
     int stage_n[kStages];                // bumps in the stage; -1 ends the stream
-    int rstart[kMaxRanges];
-    int rlen[kMaxRanges];
-    int cum[kMaxRanges + 1];             // prefix of the range lengths
     uint32_t tmem;
 };
 static_assert(sizeof(TcStage) % 1024 == 0, "stage alignment");
 static_assert(offsetof(TcSmem, rec) % 16 == 0, "record staging alignment");
 static_assert(offsetof(TcSmem, rbar) % 8 == 0, "mbarrier alignment");
+static_assert(kKc <= 32 && kBatchRows == 32, "the loader warp covers a chunk's sentinels and a batch's rows");
+static_assert(offsetof(TcSmem, meta) % 8 == 0, "chunk metadata alignment");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -117,7 +130,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(sa(b))
                  : "memory");
 }
-__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory"); }
 
 // shared-memory matrix descriptor: no swizzle, K-major canonical layout
 __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
@@ -136,23 +148,23 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
         : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+// TF32 part of x by truncation (sign, exponent and the top 10 mantissa
+// bits); x - tf32_hi(x) is exact in FP32 and smaller than 2^-10 |x|
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // byte offset of element (row r, k) in a K-major canonical operand
 __device__ __forceinline__ int canon(int r, int kq) { return kq * 128 + (r >> 3) * (int)kSBO + (r & 7) * 16; }
 
 // Operand rows of one producer thread for its 8 bumps of a chunk.  ROW: the
-// tile row whose B rows are A k(v) and A (lam/2) sin(pi v/R); otherwise the
-// tile column whose A rows are k(u) and (lam/2) sin(pi u/R).  `rec` points at
-// this role's 16-byte half of each 32-byte record: {x, cx, sx, id} or
-// {y, cy, sy, amp}; (ct, st) = e^{i pi (pos mod 2R)/R}.
+// tile row whose B rows are A (1 + cos(pi v/R)) and A sin(pi v/R); otherwise
+// the tile column whose A rows are 1 + cos(pi u/R) and sin(pi u/R); zero
+// outside the support |u| < R.  `rec` points at this role's 16-byte half of
+// each 32-byte record: {x, cx, sx, id} or {y, cy, sy, amp};
+// (ct, st) = e^{i pi (pos mod 2R)/R}.  The low part of the split is left in
+// FP32: the MMA reads only its TF32 bits.
 template <bool ROW>
 __device__ __forceinline__ void gen_half_chunk(float* hi, float* lo, const float4* rec, int half, int idx,
-                                               int32_t pos, int32_t R, float ct, float st, float lamh) {
+                                               int32_t pos, int32_t R, float ct, float st) {
     const uint32_t span = (uint32_t)(2 * R - 1);
 #pragma unroll
     for (int qq = 0; qq < kKc / 8; ++qq) {
@@ -165,23 +177,15 @@ __device__ __forceinline__ void gen_half_chunk(float* hi, float* lo, const float
             const bool in = (uint32_t)(u + R - 1) < span;          // -R < u < R
             const float cs = ct * r.y - st * r.z;                  // cos pi u / R
             const float sn = st * r.y + ct * r.z;                  // sin pi u / R
-            float a0, a1;
-            if (ROW) {
-                const float ha = 0.5f * r.w;
-                a0 = fmaf(ha, cs, ha);
-                a1 = (r.w * lamh) * sn;
-            } else {
-                a0 = fmaf(0.5f, cs, 0.5f);
-                a1 = lamh * sn;
-            }
-            f0[j] = in ? a0 : 0.f;
-            f1[j] = in ? a1 : 0.f;
+            const float m = in ? (ROW ? r.w : 1.f) : 0.f;          // A, or 1; 0 outside the support
+            f0[j] = fmaf(m, cs, m);
+            f1[j] = m * sn;
         }
         float h4[4], l4[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             h4[j] = tf32_hi(f0[j]);
-            l4[j] = tf32_hi(f0[j] - h4[j]);
+            l4[j] = f0[j] - h4[j];
         }
         const int o0 = canon(idx, q);
         *reinterpret_cast<float4*>((char*)hi + o0) = make_float4(h4[0], h4[1], h4[2], h4[3]);
@@ -189,7 +193,7 @@ __device__ __forceinline__ void gen_half_chunk(float* hi, float* lo, const float
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             h4[j] = tf32_hi(f1[j]);
-            l4[j] = tf32_hi(f1[j] - h4[j]);
+            l4[j] = f1[j] - h4[j];
         }
         const int o1 = canon(kTX + idx, q);   // kTX == kTY: second half of either operand
         *reinterpret_cast<float4*>((char*)hi + o1) = make_float4(h4[0], h4[1], h4[2], h4[3]);
@@ -241,10 +245,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     if (tid == 0) {
         for (int k = 0; k < kRecSlots; ++k) {
             bar_init(&S.rbar[k], 1);
-            bar_init(&S.rfree[k], kProdThreads);
+            bar_init(&S.rfree[k], kProdWarps);
         }
         for (int k = 0; k < kStages; ++k) {
-            bar_init(&S.full[k], kProdThreads);
+            bar_init(&S.full[k], kProdWarps);
             bar_init(&S.empty[k], 1);
         }
         bar_init(&S.done, 1);
@@ -295,51 +299,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                          : "memory");
         }
         __syncwarp();
-    } else {
-        // ======================= producers ===================================
+    } else if (warp == kLoadWarp) {
+        // ======================= record loader ===============================
+        // Walks this CTA's buckets and, per batch of up to 32 bin rows (one
+        // per lane), the bin ranges that reach the tile; cuts their
+        // concatenation into chunks of kKc bumps and stages each chunk in the
+        // next record slot: metadata by lane 0, one bulk copy per range piece
+        // by the lane owning the range.
         const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
         const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
-        const float lamh = sp.lam_half;
-        // producer thread t builds bumps 8 (t >> 7) .. +7 of each chunk for
-        // row (t & 127) (A k(v), A (lam/2) sin) if (t & 127) < 64, else for
-        // column (t & 127) - 64 (k(u), (lam/2) sin)
-        const int half = tid >> 7, tq = tid & 127;
-        const bool is_row = tq < kTY;
-        const int idx = is_row ? tq : tq - kTY;
-        const int32_t pos = (is_row ? Ylo : Xlo) + idx * kQi;   // this thread's texel centre
-        int produced = 0;      // stages filled
-        int gc = 0;            // record chunks consumed (ring position)
-        int issued = 0;        // record chunks whose copy was issued (thread 0)
-        bool dead = false;
-        // issue the bulk copies of chunk `c` of the current batch into its slot:
-        // bumps [16c, 16c + n) of the batch's concatenated bin-row ranges
-        auto issue = [&](int c, int g_abs, int total) {
-            const int lo = c * kKc, n = min(kKc, total - lo);
-            const int slot = g_abs % kRecSlots;
-            if (g_abs >= kRecSlots)   // the slot's previous chunk must be fully read
-                bar_wait(&S.rfree[slot], (uint32_t)((g_abs / kRecSlots - 1) & 1), p.stats + 2);
-            for (int b = n; b < kKc; ++b) {   // sentinels: far outside every support
-                BumpRec z;
-                z.x = z.y = 0x40000000;
-                z.cx = z.sx = z.cy = z.sy = z.amp = 0.f;
-                z.id = 0xFFFFFFFFu;
-                S.rec[slot][b] = z;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
-            int k = 0;
-            while (S.cum[k + 1] <= lo) ++k;
-            for (int at = lo; at < lo + n; ++k) {
-                const int e = min(S.cum[k + 1], lo + n);
-                if (e > at) {
-                    bulk_g2s(&S.rec[slot][at - lo], p.rec + S.rstart[k] + (at - S.cum[k]),
-                             (uint32_t)((e - at) * sizeof(BumpRec)), &S.rbar[slot]);
-                    at = e;
-                }
-            }
-            issued = g_abs + 1;
+        int gc = 0;        // chunks published
+        bool ok = true;
+        // slot of chunk gc once the producers are done with its previous chunk
+        auto claim = [&]() -> int {
+            const int slot = gc % kRecSlots;
+            bool got = true;
+            if (gc >= kRecSlots && lane == 0)
+                got = bar_wait(&S.rfree[slot], (uint32_t)((gc / kRecSlots - 1) & 1), p.stats + 2);
+            ok = ok && __shfl_sync(0xffffffffu, (int)got, 0) != 0;
+            return slot;
         };
-        for (int bi = b_begin; bi < b_end && !dead; ++bi) {
+        for (int bi = b_begin; bi < b_end && ok; ++bi) {
             const BucketDev bk = p.bk[bi];
             int bx_lo = (int)(((int64_t)Xlo) / bk.C);
             int bx_hi = (int)(((int64_t)Xhi + 2 * (int64_t)bk.R - 1) / bk.C);
@@ -350,83 +330,126 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
             if (bx_hi > bk.nbx - 1) bx_hi = bk.nbx - 1;
             if (by_hi > bk.nby - 1) by_hi = bk.nby - 1;
             if (bx_lo > bx_hi || by_lo > by_hi) continue;
-            const int32_t R = bk.R;
-            // this thread's phase factor e^{i pi (pos mod 2R) / R}
-            float st, ct;
-            {
+            for (int byb = by_lo; byb <= by_hi && ok; byb += kBatchRows) {
+                const int nr = min(kBatchRows, by_hi - byb + 1);
+                int rs = 0, rl = 0;
+                if (lane < nr) {
+                    const int key0 = bk.base + (byb + lane) * bk.nbx;
+                    rs = (int)p.offsets[key0 + bx_lo];
+                    rl = (int)p.offsets[key0 + bx_hi + 1] - rs;
+                }
+                int inc = rl;   // inclusive prefix of the range lengths over the lanes
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                const int cum = inc - rl;
+                const int total = __shfl_sync(0xffffffffu, inc, 31);
+                for (int lo = 0; lo < total; lo += kKc) {
+                    const int n = min(kKc, total - lo);
+                    const int slot = claim();
+                    if (!ok) break;
+                    if (n < kKc) {   // sentinels: far outside every support
+                        if (lane >= n && lane < kKc) {
+                            BumpRec z;
+                            z.x = z.y = 0x40000000;
+                            z.cx = z.sx = z.cy = z.sy = z.amp = 0.f;
+                            z.id = 0xFFFFFFFFu;
+                            S.rec[slot][lane] = z;
+                        }
+                        // ordered before any later bulk copy into this slot
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    }
+                    if (lane == 0) {
+                        S.meta[slot].n = n;
+                        S.meta[slot].R = bk.R;
+                    }
+                    __syncwarp();
+                    if (lane == 0) bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
+                    __syncwarp();
+                    // this lane's range covers [cum, cum + rl) of the batch
+                    const int a = max(lo, cum), b = min(lo + n, cum + rl);
+                    if (a < b)
+                        bulk_g2s(&S.rec[slot][a - lo], p.rec + rs + (a - cum), (uint32_t)((b - a) * sizeof(BumpRec)),
+                                 &S.rbar[slot]);
+                    ++gc;
+                }
+            }
+        }
+        if (ok) {   // end of the stream
+            const int slot = claim();
+            if (ok) {
+                if (lane == 0) {
+                    S.meta[slot].n = -1;
+                    S.meta[slot].R = 0;
+                }
+                __syncwarp();
+                if (lane == 0) bar_arrive(&S.rbar[slot]);
+                ++gc;
+            }
+        }
+        // every copy issued above lands before this CTA's shared memory can
+        // be reused (the last kRecSlots chunks hold the only ones that can
+        // still be in flight)
+        if (lane == 0)
+            for (int g2 = max(0, gc - kRecSlots); g2 < gc; ++g2)
+                bar_wait(&S.rbar[g2 % kRecSlots], (uint32_t)((g2 / kRecSlots) & 1), p.stats + 2);
+        __syncwarp();
+    } else {
+        // ======================= producers ===================================
+        const int32_t Xlo = tx0 * kQi + kHalfi, Ylo = ty0 * kQi + kHalfi;
+        // producer thread t builds bumps 8 (t >> 7) .. +7 of each chunk for
+        // row (t & 127) if (t & 127) < 64, else for column (t & 127) - 64
+        const int half = tid >> 7, tq = tid & 127;
+        const bool is_row = tq < kTY;
+        const int idx = is_row ? tq : tq - kTY;
+        const int32_t pos = (is_row ? Ylo : Xlo) + idx * kQi;   // this thread's texel centre
+        int produced = 0;      // stages filled
+        int32_t R = 0;         // radius of the current bucket
+        float st = 0.f, ct = 1.f;
+        for (int gc = 0;; ++gc) {
+            const int rs = gc % kRecSlots;
+            bool ok = bar_wait(&S.rbar[rs], (uint32_t)((gc / kRecSlots) & 1), p.stats + 2);
+            if (__any_sync(0xffffffffu, !ok)) break;   // this warp stops; the others time out in turn
+            const ChunkMeta m = S.meta[rs];
+            if (m.n < 0) break;
+            if (m.R != R) {   // new bucket: this thread's phase factor e^{i pi (pos mod 2R) / R}
+                R = m.R;
                 const int64_t R2 = 2 * (int64_t)R;
                 int64_t pm = (int64_t)pos % R2;
                 if (pm < 0) pm += R2;
                 sincospif((float)((double)pm / (double)R), &st, &ct);
             }
-            for (int byb = by_lo; byb <= by_hi && !dead; byb += kMaxRanges) {
-                const int nr = min(kMaxRanges, by_hi - byb + 1);
-                for (int k = tid; k < nr; k += kProdThreads) {
-                    const int key0 = bk.base + (byb + k) * bk.nbx;
-                    const int s = (int)p.offsets[key0 + bx_lo];
-                    const int e = (int)p.offsets[key0 + bx_hi + 1];
-                    S.rstart[k] = s;
-                    S.rlen[k] = e - s;
-                }
-                prod_sync();
-                if (tid == 0) {
-                    int a = 0;
-                    for (int k = 0; k < nr; ++k) {
-                        S.cum[k] = a;
-                        a += S.rlen[k];
-                    }
-                    S.cum[nr] = a;
-                }
-                prod_sync();
-                const int total = S.cum[nr];
-                const int nchunks = (total + kKc - 1) / kKc;
-                if (nchunks == 0) {
-                    prod_sync();
-                    continue;
-                }
-                if (tid == 0)
-                    for (int c0 = 0; c0 < nchunks && c0 < kAhead; ++c0) issue(c0, gc + c0, total);
-                for (int c = 0; c < nchunks; ++c, ++gc) {
-                    const int n = min(kKc, total - c * kKc);
-                    const int rs = gc % kRecSlots;
-                    bool ok = bar_wait(&S.rbar[rs], (uint32_t)((gc / kRecSlots) & 1), p.stats + 2);
-                    const int fs = produced % kStages;
-                    ok = ok && bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
-                    if (__any_sync(0xffffffffu, !ok)) {
-                        dead = true;   // this warp stops; the others time out in turn
-                        break;
-                    }
-                    TcStage& T = S.st[fs];
-                    // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp};
-                    // slots past n hold sentinel records outside every support
-                    const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
-                    if (is_row)
-                        gen_half_chunk<true>(T.Bhi, T.Blo, rc, half, idx, pos, R, ct, st, lamh);
-                    else
-                        gen_half_chunk<false>(T.Ahi, T.Alo, rc, half, idx, pos, R, ct, st, lamh);
-                    bar_arrive(&S.rfree[rs]);
-                    if (tid == 0) S.stage_n[fs] = n;
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_arrive(&S.full[fs]);
-                    ++produced;
-                    // prefetch kAhead chunks ahead into the slot that last
-                    // held chunk c + kAhead - kRecSlots
-                    if (tid == 0 && c + kAhead < nchunks) issue(c + kAhead, gc + kAhead, total);
-                }
-                prod_sync();   // every producer done with this batch's chunk list
+            const int fs = produced % kStages;
+            ok = bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
+            if (__any_sync(0xffffffffu, !ok)) break;
+            TcStage& T = S.st[fs];
+            // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp};
+            // slots past n hold sentinel records outside every support
+            const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
+            if (is_row)
+                gen_half_chunk<true>(T.Bhi, T.Blo, rc, half, idx, pos, R, ct, st);
+            else
+                gen_half_chunk<false>(T.Ahi, T.Alo, rc, half, idx, pos, R, ct, st);
+            if (tid == 0) S.stage_n[fs] = m.n;
+            // every lane's operand stores visible to the tensor core, then
+            // one arrival for the warp on each barrier
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                bar_arrive(&S.rfree[rs]);
+                bar_arrive(&S.full[fs]);
             }
+            ++produced;
         }
-        // after a timeout, let any record copy still in flight land before
-        // this CTA's shared memory can be reused
-        if (tid == 0)
-            for (int g2 = gc; g2 < issued; ++g2)
-                bar_wait(&S.rbar[g2 % kRecSlots], (uint32_t)((g2 / kRecSlots) & 1), p.stats + 2);
         // end of the stream for the MMA thread
         {
             const int fs = produced % kStages;
             bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
             if (tid == 0) S.stage_n[fs] = -1;
-            bar_arrive(&S.full[fs]);
+            __syncwarp();
+            if (lane == 0) bar_arrive(&S.full[fs]);
         }
         // ======================= epilogue ====================================
         bar_wait(&S.done, 0u, p.stats + 2);
@@ -452,13 +475,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                 for (int j = 0; j < 32; ++j) r[j] = c[j] = 0u;
             }
             const int f = cb < kTY / 32 ? (lowm ? 0 : 1) : 2;
+            const float scale = f == 0 ? 0.25f : 0.5f * sp.lam_half;
             const int y0 = ty0 + 32 * (cb & (kTY / 32 - 1));
             if (x >= sp.W) continue;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int y = y0 + j;
                 if (y < sp.H) {
-                    const float v = __uint_as_float(r[j]) + __uint_as_float(c[j]);
+                    const float v = (__uint_as_float(r[j]) + __uint_as_float(c[j])) * scale;
                     const size_t o = (size_t)y * sp.W + x;
                     if (G > 1) p.partial[((size_t)g * 3 + f) * plane + o] = v;
                     else p.out[(size_t)f * plane + o] = blend1(sp, x, y, f, v);
