@@ -265,6 +265,15 @@ SynthParams synth_params(scwp_ctx* ctx, const PatchHost& P) {
     sp.fsx = (float)(P.d.cell * N / L);
     sp.N = ctx->d.fft_n;
     sp.bg = ctx->bgout;
+    // every record amplitude is a table entry or the wake amplitude
+    double amax = std::fabs(P.d.wake_amp);
+    for (double a : P.T.amp) amax = std::max(amax, std::fabs(a));
+    int e = 0;
+    if (amax > 0) {
+        std::frexp(amax, &e);   // amax in [2^(e-1), 2^e)
+        e = std::min(std::max(13 - e, -60), 60);
+    }
+    sp.row_scale = (float)std::ldexp(1.0, e);
     return sp;
 }
 

@@ -100,6 +100,7 @@ struct SynthParams {
     float fx0, fy0, fsx;    // background coords: f = f0 + i * fs (grid units)
     int N;                  // background grid size
     const float* bg;        // [3][N][N]
+    float row_scale;        // power of two putting the patch's largest |A| near 2^13
 };
 
 // Every launcher reports how many kernels it enqueued (process-wide counter,

@@ -7,19 +7,20 @@
 // are one dense contraction over bumps,
 //   D[m][n] = sum_b Aop[m][b] Bop[n][b],
 //   Aop = [ 1 + cos(pi u_x/R) ; sin(pi u_x/R) ]              (128 x K: 64 columns x 2)
-//   Bop = [ A (1 + cos(pi v_y/R)) ; A sin(pi v_y/R) ]        (128 x K: 64 rows x 2)
-// whose quadrants are 4 h^T, (2/lam) Dx^T, (2/lam) Dy^T (the fourth is
-// unused; the constant factors are applied when the sums are read out),
-// computed by
-// tcgen05.mma (M = 128, N = 128, K = 8, kind::tf32) into FP32 accumulators in
-// tensor memory.  Each operand is split as hi + lo, hi = x truncated to TF32
-// and lo = x - hi (exact; the MMA takes its TF32 bits: 22 significant bits
-// together);
+//   Bop = S [ A (1 + cos(pi v_y/R)) ; A sin(pi v_y/R) ]      (128 x K: 64 rows x 2)
+// whose quadrants are 4 S h^T, (2 S/lam) Dx^T, (2 S/lam) Dy^T (the fourth is
+// unused; the constant factors are applied when the sums are read out; S is
+// a power of two that puts the largest |A| of the patch near 2^13), computed
+// by tcgen05.mma (M = 128, N = 128, K = 16, kind::f16) into FP32 accumulators
+// in tensor memory.  Each operand is split as hi + lo in FP16: hi = x
+// truncated to 10 mantissa bits (exact in FP16), lo = x - hi (exact in FP32,
+// then rounded to FP16): 22 significant bits together, the precision of a
+// TF32 pair at twice the tensor rate and half the shared-memory bytes.
 // hi*hi accumulates in one accumulator and the small corrections
 // hi*lo + lo*hi in a second one, so the large sum takes one rounding per step
 // and the two are added in FP32 when read out.
 //
-// Warps 0-7 produce the operands of each 16-bump chunk into a 3-stage ring in
+// Warps 0-7 produce the operands of each 32-bump chunk into a 3-stage ring in
 // shared memory (no-swizzle K-major canonical layout: 8-row x 16-byte core
 // matrices, 128 B apart along K, 512 B apart along rows) from bump records
 // that warp 9 stages in an eight-slot ring: it walks the bin ranges that
@@ -46,7 +47,7 @@ namespace {
 
 constexpr int kTX = 64;            // tile columns (x): the MMA's M = 2 * kTX
 constexpr int kTY = 64;            // tile rows (y):    the MMA's N = 2 * kTY
-constexpr int kKc = 16;            // bumps per stage (two K = 8 steps)
+constexpr int kKc = 32;            // bumps per stage (two K = 16 steps)
 constexpr int kStages = 3;
 constexpr int kRecSlots = 8;       // staged record chunks
 constexpr int kProdThreads = 256;  // warps 0-7: two halves of each chunk
@@ -59,13 +60,13 @@ constexpr int kTmemCols = 256;     // main accumulator at column 0, corrections 
 constexpr uint32_t kCorrCol = 2 * kTY;
 constexpr int32_t kQi = 65536, kHalfi = 32768;
 constexpr long long kWaitCycles = 4000000000ll;
-constexpr uint32_t kSBO = (kKc / 4) * 128;   // bytes between 8-row groups
+constexpr uint32_t kSBO = (kKc / 8) * 128;   // bytes between 8-row groups (16-bit elements)
 
-struct __align__(1024) TcStage {
-    float Ahi[2 * kTX * kKc];      // rows 0..63 k(u), 64..127 (lam/2) sin
-    float Alo[2 * kTX * kKc];
-    float Bhi[2 * kTY * kKc];      // rows 0..63 A k(v), 64..127 A (lam/2) sin
-    float Blo[2 * kTY * kKc];
+struct __align__(1024) TcStage {   // FP16 operands
+    uint16_t Ahi[2 * kTX * kKc];   // rows 0..63 1 + cos, 64..127 sin (tile columns)
+    uint16_t Alo[2 * kTX * kKc];
+    uint16_t Bhi[2 * kTY * kKc];   // rows 0..63 S A (1 + cos), 64..127 S A sin (tile rows)
+    uint16_t Blo[2 * kTY * kKc];
 };
 
 // what the loader tells the producers about a staged record chunk
@@ -140,64 +141,69 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint3
     return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 
-// TF32 part of x by truncation (sign, exponent and the top 10 mantissa
-// bits); x - tf32_hi(x) is exact in FP32 and smaller than 2^-10 |x|
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x truncated to 10 mantissa bits (exact in FP16 within its normal range);
+// x - hi10(x) is exact in FP32 and smaller than 2^-10 |x|
+__device__ __forceinline__ float hi10(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// two floats as FP16 (round to nearest), a in the low half (lower K index)
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
 
 // byte offset of element (row r, k) in a K-major canonical operand
 __device__ __forceinline__ int canon(int r, int kq) { return kq * 128 + (r >> 3) * (int)kSBO + (r & 7) * 16; }
 
-// Operand rows of one producer thread for its 8 bumps of a chunk.  ROW: the
-// tile row whose B rows are A (1 + cos(pi v/R)) and A sin(pi v/R); otherwise
-// the tile column whose A rows are 1 + cos(pi u/R) and sin(pi u/R); zero
-// outside the support |u| < R.  `rec` points at this role's 16-byte half of
-// each 32-byte record: {x, cx, sx, id} or {y, cy, sy, amp};
-// (ct, st) = e^{i pi (pos mod 2R)/R}.  The low part of the split is left in
-// FP32: the MMA reads only its TF32 bits.
+// one operand row, hi and lo parts, for 8 consecutive bumps (one 16-byte
+// core-matrix row each)
+__device__ __forceinline__ void store_split8(uint16_t* hi, uint16_t* lo, int off, const float (&f)[8]) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float a = hi10(f[2 * k]), b = hi10(f[2 * k + 1]);
+        h[k] = pack_f16(a, b);
+        l[k] = pack_f16(f[2 * k] - a, f[2 * k + 1] - b);
+    }
+    *reinterpret_cast<uint4*>((char*)hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>((char*)lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Operand rows of one producer thread for its 16 bumps of a chunk.  ROW: the
+// tile row whose B rows are S A (1 + cos(pi v/R)) and S A sin(pi v/R)
+// (`amul` = S); otherwise the tile column whose A rows are 1 + cos(pi u/R)
+// and sin(pi u/R) (`amul` = 1); zero outside the support |u| < R.  `rec`
+// points at this role's 16-byte half of each 32-byte record: {x, cx, sx, id}
+// or {y, cy, sy, amp}; (ct, st) = e^{i pi (pos mod 2R)/R}.
 template <bool ROW>
-__device__ __forceinline__ void gen_half_chunk(float* hi, float* lo, const float4* rec, int half, int idx,
-                                               int32_t pos, int32_t R, float ct, float st) {
+__device__ __forceinline__ void gen_half_chunk(uint16_t* hi, uint16_t* lo, const float4* rec, int half, int idx,
+                                               int32_t pos, int32_t R, float ct, float st, float amul) {
     const uint32_t span = (uint32_t)(2 * R - 1);
 #pragma unroll
-    for (int qq = 0; qq < kKc / 8; ++qq) {
-        const int q = 2 * half + qq;
-        float f0[4], f1[4];
+    for (int qq = 0; qq < kKc / 16; ++qq) {
+        const int q = 2 * half + qq;   // 16-byte K chunk: bumps 8q .. 8q + 7
+        float f0[8], f1[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float4 r = rec[2 * (4 * q + j)];
+        for (int j = 0; j < 8; ++j) {
+            const float4 r = rec[2 * (8 * q + j)];
             const int32_t u = pos - __float_as_int(r.x);
             const bool in = (uint32_t)(u + R - 1) < span;          // -R < u < R
             const float cs = ct * r.y - st * r.z;                  // cos pi u / R
             const float sn = st * r.y + ct * r.z;                  // sin pi u / R
-            const float m = in ? (ROW ? r.w : 1.f) : 0.f;          // A, or 1; 0 outside the support
+            const float m = in ? (ROW ? r.w * amul : amul) : 0.f;  // S A, or 1; 0 outside the support
             f0[j] = fmaf(m, cs, m);
             f1[j] = m * sn;
         }
-        float h4[4], l4[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            h4[j] = tf32_hi(f0[j]);
-            l4[j] = f0[j] - h4[j];
-        }
-        const int o0 = canon(idx, q);
-        *reinterpret_cast<float4*>((char*)hi + o0) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-        *reinterpret_cast<float4*>((char*)lo + o0) = make_float4(l4[0], l4[1], l4[2], l4[3]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            h4[j] = tf32_hi(f1[j]);
-            l4[j] = f1[j] - h4[j];
-        }
-        const int o1 = canon(kTX + idx, q);   // kTX == kTY: second half of either operand
-        *reinterpret_cast<float4*>((char*)hi + o1) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-        *reinterpret_cast<float4*>((char*)lo + o1) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+        store_split8(hi, lo, canon(idx, q), f0);
+        store_split8(hi, lo, canon(kTX + idx, q), f1);   // kTX == kTY: second half of either operand
     }
 }
 
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
         // ======================= MMA issuer ==================================
         if (lane == 0) {
             const uint32_t idesc =
-                (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);
+                (1u << 4) | ((uint32_t)(2 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);   // F32 += F16 x F16
             uint32_t acc = 0, acc2 = 0;
             for (int k = 0;; ++k) {
                 const int fs = k % kStages;
@@ -278,15 +284,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const TcStage& T = S.st[fs];
 #pragma unroll
-                for (int s = 0; s < kKc / 8; ++s) {
+                for (int s = 0; s < kKc / 16; ++s) {
                     const uint32_t off = (uint32_t)s * 256u;   // two 16-byte K chunks per step
                     const uint64_t ah = smem_desc((const char*)T.Ahi + off, 128, kSBO);
                     const uint64_t al = smem_desc((const char*)T.Alo + off, 128, kSBO);
                     const uint64_t bh = smem_desc((const char*)T.Bhi + off, 128, kSBO);
                     const uint64_t bl = smem_desc((const char*)T.Blo + off, 128, kSBO);
-                    mma_tf32(tmem, ah, bh, idesc, acc);
-                    mma_tf32(tmem + kCorrCol, ah, bl, idesc, acc2);
-                    mma_tf32(tmem + kCorrCol, al, bh, idesc, 1);
+                    mma_f16(tmem, ah, bh, idesc, acc);
+                    mma_f16(tmem + kCorrCol, ah, bl, idesc, acc2);
+                    mma_f16(tmem + kCorrCol, al, bh, idesc, 1);
                     acc = acc2 = 1;
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     } else {
         // ======================= producers ===================================
         const int32_t Xlo = tx0 * kQi + kHalfi, Ylo = ty0 * kQi + kHalfi;
-        // producer thread t builds bumps 8 (t >> 7) .. +7 of each chunk for
+        // producer thread t builds bumps 16 (t >> 7) .. +15 of each chunk for
         // row (t & 127) if (t & 127) < 64, else for column (t & 127) - 64
         const int half = tid >> 7, tq = tid & 127;
         const bool is_row = tq < kTY;
@@ -429,9 +435,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
             // slots past n hold sentinel records outside every support
             const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
             if (is_row)
-                gen_half_chunk<true>(T.Bhi, T.Blo, rc, half, idx, pos, R, ct, st);
+                gen_half_chunk<true>(T.Bhi, T.Blo, rc, half, idx, pos, R, ct, st, sp.row_scale);
             else
-                gen_half_chunk<false>(T.Ahi, T.Alo, rc, half, idx, pos, R, ct, st);
+                gen_half_chunk<false>(T.Ahi, T.Alo, rc, half, idx, pos, R, ct, st, 1.f);
             if (tid == 0) S.stage_n[fs] = m.n;
             // every lane's operand stores visible to the tensor core, then
             // one arrival for the warp on each barrier
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                 for (int j = 0; j < 32; ++j) r[j] = c[j] = 0u;
             }
             const int f = cb < kTY / 32 ? (lowm ? 0 : 1) : 2;
-            const float scale = f == 0 ? 0.25f : 0.5f * sp.lam_half;
+            const float scale = (f == 0 ? 0.25f : 0.5f * sp.lam_half) / sp.row_scale;
             const int y0 = ty0 + 32 * (cb & (kTY / 32 - 1));
             if (x >= sp.W) continue;
 #pragma unroll
