@@ -40,6 +40,18 @@ METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] \
 UNIT = "evals/s"
 # FP32 FMA issue-rate peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# tensor work of one operand stage of the tile gather: 6 MMAs of M = N = 128, K = 16
+FLOPS_PER_STAGE = 6 * 2 * 128 * 128 * 16
+
+
+def tensor_peak():
+    """Dense FP16 tensor peak: the measured bf16 GEMM rate (same nominal rate)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["bf16_tflops"])
+        return v, "measured: bf16 cuBLAS GEMM burst (FP16 dense has the same nominal rate)"
+    except Exception:
+        return 1900.0, "fallback: 1.9 PFLOP/s bf16 burst (FP16 dense has the same nominal rate)"
 FLOPS_PER_EVAL = 6          # 3 FMAs per bump-texel (h, Dx, Dy)
 
 
@@ -251,15 +263,27 @@ def run_ours(args):
         total_s_all, total_evals_all = total_s, float(total_evals)
     value = total_evals_all / total_s_all
 
-    # dominant kernel: tile-gather synthesis (+ blend epilogue), FP32 FMA bound
+    # dominant kernel: tensor-core tile gather (k_synth_tc, with its bucket-group
+    # blend epilogue), timed by the library's events around the synthesis
+    # stage on the stream it launches on.  Executed tensor work: operand stages
+    # x 6 MMAs of 128x128x16 (hi*hi, hi*lo, lo*hi over two K = 16 steps).
     synth_ms = stage_ms[2] / max(frames, 1)
     evals_per_step = total_evals / args.steps
-    achieved = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_synth_gather", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "flops_per_launch": evals_per_step * FLOPS_PER_EVAL, "avg_launch_ms": synth_ms,
+    stages = sum(sc.stats(p).mma_stages for p in range(len(cfg["patches"])))
+    mma_flops = stages * FLOPS_PER_STAGE
+    peak, peak_src = tensor_peak()
+    achieved = mma_flops / (synth_ms / 1000.0) / 1e12
+    fp32_eq = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_synth_tc", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_src,
+                "flops_per_launch": mma_flops, "operand_stages_per_launch": stages,
+                "avg_launch_ms": synth_ms,
+                "fp32_equivalent": {"flops_per_launch": evals_per_step * FLOPS_PER_EVAL,
+                                    "achieved": fp32_eq, "peak": FP32_PEAK_TFLOPS,
+                                    "frac": fp32_eq / FP32_PEAK_TFLOPS,
+                                    "note": "6 flop per bump-texel eval against the FP32 CUDA-core "
+                                            "FMA peak (152 SMs x 128 lanes x 2 flop x 2070 MHz)"},
                 "stage_ms": {"fft": stage_ms[0] / max(frames, 1),
                              "particles": stage_ms[1] / max(frames, 1),
                              "synth_blend": synth_ms, "frame": stage_ms[3] / max(frames, 1)}}
@@ -267,7 +291,7 @@ def run_ours(args):
     if os.path.exists(rfile):
         try:
             tr = json.load(open(rfile))
-            if tr.get("workload") == cfg["name"] and tr.get("kernel") == "k_synth_gather":
+            if tr.get("workload") == cfg["name"] and tr.get("kernel") == "k_synth_tc":
                 roofline["traffic"] = tr.get("dram_bytes_per_launch")
         except Exception:
             pass
@@ -311,7 +335,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * total_s_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": dict(describe(cfg), parallelism=f"replicas{world}"),
+            "data": "synthetic", "config": dict(describe(cfg), parallelism=f"replicas{world}",
+                                                synth_groups=[sc.info(p).synth_groups
+                                                              for p in range(len(cfg["patches"]))]),
             "p50_ms": p50, "p99_ms": p99, "evals_per_step": evals_per_step,
             "live_particles": sc.stats(0).live_particles,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -327,7 +353,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL))

@@ -136,6 +136,8 @@ typedef struct scwp_stats {
     int32_t error_flags;       /* bit 0: capacity, bit 1: timeout          */
     int64_t live_per_bucket[SCWP_MAX_BUCKETS];
     double injected_energy[SCWP_MAX_BUCKETS]; /* sum 1/8 A^2 pi r^2 (Eq. 12 / rho g) */
+    int64_t mma_stages;        /* operand stages (6 MMAs of 128x128x16 each) the last
+                                  tensor-core synthesis committed; 0 for the other modes */
 } scwp_stats;
 
 /* Scalar description of a patch's tables and bins. */
@@ -147,6 +149,9 @@ typedef struct scwp_patch_info {
     int32_t capacity;
     int32_t bin_cells[SCWP_MAX_BUCKETS];
     int32_t nbx[SCWP_MAX_BUCKETS], nby[SCWP_MAX_BUCKETS], bin_base[SCWP_MAX_BUCKETS];
+    int32_t synth_groups;      /* bucket groups of the tensor-core synthesis (planned at creation) */
+    int32_t synth_items;       /* its (tile, group) work items = CTAs per synthesis launch */
+    int32_t synth_slots;       /* resident CTA slots of the device the plan assumed */
 } scwp_patch_info;
 
 /* Table identifiers for scwp_get_table (element type, count). */

@@ -8,7 +8,10 @@
 #include <string.h>
 
 #include <atomic>
+#include <algorithm>
 #include <cmath>
+#include <functional>
+#include <queue>
 #include <new>
 #include <string>
 #include <vector>
@@ -43,6 +46,8 @@ struct PatchHost {
     int64_t injected = 0;
     std::vector<double> energy;       // [nb]
     double band = 0;
+    std::vector<int> tc_order;        // launch order of the tensor-core synthesis items
+    int tc_slots = 0;                 // resident CTA slots the plan assumed
 };
 
 struct FrameEvents {
@@ -242,6 +247,81 @@ scwp_status upload_dt_tables(scwp_ctx* ctx, PatchHost& P) {
     return SCWP_OK;
 }
 
+// Plan of the tensor-core synthesis of one patch: the bucket-group count G
+// and the launch order of its (tile, group) items.  Each item's work is
+// estimated in operand stages from the expected bump density of each bucket
+// (steady-state shares proportional to (W Q + 2 R_i) / R_i^2, the prefill
+// rule) times the part of the tile's reach (the tile grown by R_i) inside the
+// particle domain (the patch grown by R_i).  Items are ordered heaviest
+// first, so in-order block dispatch approximates longest-processing-time
+// scheduling; G minimises the simulated makespan of that dispatch over the
+// device's resident CTA slots plus the traffic of the group-sum blend.
+struct TcPlan {
+    int G = 1;
+    std::vector<int> order;
+};
+
+TcPlan plan_tc(const PatchHost& P, int slots) {
+    const PatchTablesHost& T = P.T;
+    const int ts = synth_tc_tile(), kc = synth_tc_stage_bumps();
+    const int ntx = (T.W + ts - 1) / ts, nty = (T.H + ts - 1) / ts, tiles = ntx * nty;
+    // bumps: two per live particle (crest and trough)
+    const double total = 2.0 * (P.d.prefill > 0 ? (double)P.d.prefill : 0.5 * (double)P.d.max_particles);
+    std::vector<double> w(T.nb);
+    double sw = 0.0;
+    for (int i = 0; i < T.nb; ++i) {
+        w[i] = ((double)T.W * kQ + 2.0 * T.R[i]) / ((double)T.R[i] * (double)T.R[i]);
+        sw += w[i];
+    }
+    std::vector<double> est((size_t)tiles * T.nb);   // stages per (tile, bucket)
+    for (int i = 0; i < T.nb; ++i) {
+        const double r = (double)T.R[i] / kQ;
+        const double dens = total * w[i] / sw / ((T.W + 2 * r) * (T.H + 2 * r));
+        for (int t = 0; t < tiles; ++t) {
+            const double x0 = (t % ntx) * ts - r, x1 = (t % ntx + 1) * ts + r;
+            const double y0 = (t / ntx) * ts - r, y1 = (t / ntx + 1) * ts + r;
+            const double ax = std::max(0.0, std::min(x1, T.W + r) - std::max(x0, -r));
+            const double ay = std::max(0.0, std::min(y1, T.H + r) - std::max(y0, -r));
+            est[(size_t)t * T.nb + i] = std::ceil(dens * ax * ay / kc);
+        }
+    }
+    constexpr double kItemStages = 2.0;   // set-up and read-out of one item, in stages
+    constexpr double kStageUs = 1.3;      // one stage on one CTA slot (two CTAs per SM)
+    constexpr double kHbmBytesPerUs = 6.8e6;
+    TcPlan best;
+    double best_cost = 0.0;
+    const int gmax = std::min(T.nb, 16);
+    for (int G = 1; G <= gmax; ++G) {
+        std::vector<double> work((size_t)tiles * G);
+        for (int t = 0; t < tiles; ++t)
+            for (int g = 0; g < G; ++g) {
+                double s = kItemStages;
+                for (int i = (g * T.nb) / G; i < ((g + 1) * T.nb) / G; ++i) s += est[(size_t)t * T.nb + i];
+                work[(size_t)t * G + g] = s;
+            }
+        std::vector<int> order(work.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+        std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+        for (int k = 0; k < std::max(slots, 1); ++k) q.push(0.0);
+        double makespan = 0.0;
+        for (int it : order) {
+            const double f = q.top() + work[it];
+            q.pop();
+            q.push(f);
+            makespan = std::max(makespan, f);
+        }
+        const double blend = G > 1 ? (G + 1) * 12.0 * T.W * T.H / kHbmBytesPerUs : 0.0;
+        const double cost = makespan * kStageUs + blend;
+        if (G == 1 || cost < best_cost) {
+            best_cost = cost;
+            best.G = G;
+            best.order = order;
+        }
+    }
+    return best;
+}
+
 scwp_status ready(scwp_ctx* ctx) {
     if (!ctx) return SCWP_E_INVALID;
     if (ctx->sticky != SCWP_OK) return ctx->sticky;
@@ -304,6 +384,7 @@ scwp_status synthesize(scwp_ctx* ctx, int mode) {
         } else if (mode == SCWP_SYNTH_GATHER_FP32) {
             CU(launch_synth_gather(P->dev, sp, ctx->st));
         } else {
+            CU(cudaMemsetAsync(P->dev.stats + 3 + P->T.nb, 0, sizeof(unsigned long long), ctx->st));
             CU(launch_synth_tc(P->dev, sp, ctx->st));
         }
     }
@@ -437,14 +518,23 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
             return G < 1 ? 1 : G;
         };
         D.groups = groups_for(((T.W + 63) / 64) * ((T.H + 63) / 64), 2);       // CUDA-core tiles
-        D.groups_tc = groups_for(((T.W + 63) / 64) * ((T.H + 63) / 64), 2);    // tensor-core tiles
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = synth_tc_ctas_per_sm();
+        P->tc_slots = sms * (per_sm > 0 ? per_sm : 1);
+        const TcPlan plan = plan_tc(*P, P->tc_slots);
+        D.groups_tc = plan.G;
+        P->tc_order = plan.order;
+        D.tc_order = (int*)dalloc(ctx, plan.order.size() * sizeof(int));
+        ok = ok && D.tc_order;
         const int G = D.groups > D.groups_tc ? D.groups : D.groups_tc;
         if (G > 1) {
             D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
             ok = ok && D.partial;
         }
     }
-    D.stats = (unsigned long long*)dalloc(ctx, (3 + (size_t)T.nb) * sizeof(unsigned long long));
+    D.stats = (unsigned long long*)dalloc(ctx, (4 + (size_t)T.nb) * sizeof(unsigned long long));
     ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.hist &&
          D.offsets && D.rec && D.out && D.stats;
     if (!ok) {
@@ -487,6 +577,8 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     int32_t counts[2] = {n0, n0};
     CU(cudaMemcpyAsync(D.amp, ampf.data(), ng * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(D.bk, P->bk.data(), T.nb * sizeof(BucketDev), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemcpyAsync(D.tc_order, P->tc_order.data(), P->tc_order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->st));
     // per-bucket phase steps of n texels: e^{i pi n Q / R_i}, n < kRotN
     std::vector<float2> rot((size_t)T.nb * kRotN);
     for (int i = 0; i < T.nb; ++i)
@@ -496,7 +588,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         }
     CU(cudaMemcpyAsync(D.rot, rot.data(), rot.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
-    CU(cudaMemsetAsync(D.stats, 0, (3 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
+    CU(cudaMemsetAsync(D.stats, 0, (4 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));
     CU(cudaMemsetAsync(D.out, 0, (size_t)3 * T.W * T.H * sizeof(float), ctx->st));
     if (n0 > 0) {
@@ -735,7 +827,7 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
     if (s != SCWP_OK) return s;
     if (!out || patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
     PatchHost* P = ctx->patches[patch_id];
-    std::vector<unsigned long long> st(3 + P->T.nb);
+    std::vector<unsigned long long> st(4 + P->T.nb);
     int32_t cnt[2];
     CU(cudaMemcpyAsync(st.data(), P->dev.stats, st.size() * 8, cudaMemcpyDeviceToHost, ctx->st));
     CU(cudaMemcpyAsync(cnt, P->dev.count, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
@@ -748,6 +840,7 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
     out->bumps_binned = (int64_t)st[1];
     out->error_flags = (int32_t)st[2];
     out->injected_total = P->injected;
+    out->mma_stages = (int64_t)st[3 + P->T.nb];
     out->n_buckets = P->T.nb;
     for (int i = 0; i < P->T.nb; ++i) {
         out->live_per_bucket[i] = (int64_t)st[3 + i];
@@ -771,6 +864,9 @@ scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info
     out->height = P->T.H;
     out->total_bins = P->dev.total_bins;
     out->capacity = P->dev.cap;
+    out->synth_groups = P->dev.groups_tc;
+    out->synth_items = (int32_t)P->tc_order.size();
+    out->synth_slots = P->tc_slots;
     for (int i = 0; i < P->T.nb; ++i) {
         out->bin_cells[i] = P->bin_cells[i];
         out->nbx[i] = P->bk[i].nbx;

@@ -63,7 +63,10 @@ struct PatchDev {
     float* partial = nullptr;             // [groups][3][H][W] per-bucket-group sums (groups > 1)
     int groups = 1;                       // bucket groups of the CUDA-core synthesis
     int groups_tc = 1;                    // bucket groups of the tensor-core synthesis
-    unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..] live per bucket
+    int* tc_order = nullptr;              // [groups_tc * tiles] launch order of (tile, group) items:
+                                          // item = tile * groups_tc + group, heaviest first
+    unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..3+nb) live per bucket,
+                                          // [3+nb] operand stages of the last tensor-core synthesis
     float* layers = nullptr;              // layered variant scratch (lazy)
     size_t layers_bytes = 0;
 };
@@ -115,6 +118,11 @@ cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
 cudaError_t launch_synth_tc(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
+// tensor-core synthesis geometry: tile side (texels), bumps per operand stage,
+// and resident CTAs per SM (0 on error)
+int synth_tc_tile();
+int synth_tc_stage_bumps();
+int synth_tc_ctas_per_sm();
 // sum `groups` partial [3][H][W] planes at src (in order), blend, store to p.out
 cudaError_t launch_blend(const PatchDev& p, const SynthParams& sp, const float* src, int groups,
                          cudaStream_t st);

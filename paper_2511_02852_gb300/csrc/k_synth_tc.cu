@@ -244,8 +244,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
-    const int G = gridDim.z, g = blockIdx.z;
+    // this CTA's (tile, bucket group) item, in the host-planned order
+    const int G = p.groups_tc;
+    const int item = p.tc_order[blockIdx.x];
+    const int tile = item / G, g = item - tile * G;
+    const int ntx = (p.W + kTX - 1) / kTX;
+    const int tx0 = (tile % ntx) * kTX, ty0 = (tile / ntx) * kTY;
     const int b_begin = (g * sp.nb) / G, b_end = ((g + 1) * sp.nb) / G;
 
     if (tid == 0) {
@@ -277,7 +281,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
             const uint32_t idesc =
                 (1u << 4) | ((uint32_t)(2 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);   // F32 += F16 x F16
             uint32_t acc = 0, acc2 = 0;
-            for (int k = 0;; ++k) {
+            int k = 0;   // stages consumed
+            for (;; ++k) {
                 const int fs = k % kStages;
                 if (!bar_wait(&S.full[fs], (k / kStages) & 1u, p.stats + 2)) break;
                 if (S.stage_n[fs] < 0) break;
@@ -299,6 +304,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                                  sa(&S.empty[fs]))
                              : "memory");
             }
+            // stages committed by this CTA (executed tensor work, for the roofline)
+            if (k > 0) atomicAdd(p.stats + 3 + p.nb, (unsigned long long)k);
             // arrives once every MMA issued above has completed
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              sa(&S.done))
@@ -504,15 +511,52 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
 
 }  // namespace
 
+int synth_tc_tile() { return kTX; }
+int synth_tc_stage_bumps() { return kKc; }
+
+namespace {
+// the largest shared-memory carveout, so that two CTAs fit on an SM
+cudaError_t tc_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+}  // namespace
+
+// Resident CTAs per SM from the SM's limits: shared memory (with the
+// per-block reservation), registers (allocated per warp in units of 256),
+// threads, and tensor-memory columns (512 per SM).  The runtime occupancy
+// query is not used: it reports one CTA for this 10-warp block although two
+// fit every one of these limits.
+int synth_tc_ctas_per_sm() {
+    if (tc_attributes() != cudaSuccess) return 0;
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
+    cudaFuncAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&a, k_synth_tc) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 0;
+    const int warps = kThreads / 32;
+    const int regs_warp = ((a.numRegs * 32 + 255) / 256) * 256;
+    int n = smem_sm / (int)(sizeof(TcSmem) + a.sharedSizeBytes + resv);
+    n = min(n, regs_sm / (regs_warp * warps));
+    n = min(n, thr_sm / kThreads);
+    n = min(n, 512 / kTmemCols);
+    return n;
+}
+
 cudaError_t launch_synth_tc(const PatchDev& p, const SynthParams& sp, cudaStream_t st) {
     const size_t sm = sizeof(TcSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = tc_attributes();
     if (e != cudaSuccess) return e;
-    const int G = p.groups_tc > 1 && p.partial ? p.groups_tc : 1;
-    dim3 grid((p.W + kTX - 1) / kTX, (p.H + kTY - 1) / kTY, G);
-    k_synth_tc<<<grid, kThreads, sm, st>>>(p, sp);
+    if (!p.tc_order || (p.groups_tc > 1 && !p.partial)) return cudaErrorInvalidValue;
+    const int tiles = ((p.W + kTX - 1) / kTX) * ((p.H + kTY - 1) / kTY);
+    k_synth_tc<<<tiles * p.groups_tc, kThreads, sm, st>>>(p, sp);
     count_launches(1);
-    if (G > 1) return launch_blend(p, sp, p.partial, G, st);
+    if (p.groups_tc > 1) return launch_blend(p, sp, p.partial, p.groups_tc, st);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ class scwp_stats(C.Structure):
                 ("bumps_binned", C.c_int64), ("eval_count", C.c_int64),
                 ("injected_total", C.c_int64), ("n_buckets", C.c_int32),
                 ("error_flags", C.c_int32), ("live_per_bucket", C.c_int64 * MAX_BUCKETS),
-                ("injected_energy", C.c_double * MAX_BUCKETS)]
+                ("injected_energy", C.c_double * MAX_BUCKETS), ("mma_stages", C.c_int64)]
 
 
 class scwp_patch_info(C.Structure):
@@ -68,7 +68,8 @@ class scwp_patch_info(C.Structure):
                 ("wake_bucket", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
                 ("total_bins", C.c_int32), ("capacity", C.c_int32),
                 ("bin_cells", C.c_int32 * MAX_BUCKETS), ("nbx", C.c_int32 * MAX_BUCKETS),
-                ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS)]
+                ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS),
+                ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32)]
 
 
 EXPORTS = {
