@@ -504,7 +504,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     D.amp = (float*)dalloc(ctx, ng * sizeof(float));
     D.bk = (BucketDev*)dalloc(ctx, T.nb * sizeof(BucketDev));
     D.rot = (float2*)dalloc(ctx, (size_t)T.nb * kRotN * sizeof(float2));
-    D.hist = (uint32_t*)dalloc(ctx, (size_t)256 * D.nblk_s * 4);
+    D.hist = (uint32_t*)dalloc(ctx, ((size_t)256 * D.nblk_s + 256) * 4);
     D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
     D.rec = (BumpRec*)dalloc(ctx, 2 * cap * sizeof(BumpRec));
     D.out = (float*)dalloc(ctx, (size_t)3 * T.W * T.H * sizeof(float));

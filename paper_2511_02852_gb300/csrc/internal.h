@@ -54,7 +54,7 @@ struct PatchDev {
     float2* rot = nullptr;                // [nb][kRotN] (cos, sin)(pi n Q / R_i)
     uint32_t* keys[2] = {nullptr, nullptr};  // [2 cap] bin keys (sort ping-pong)
     uint32_t* vals[2] = {nullptr, nullptr};  // [2 cap] bump ids
-    uint32_t* hist = nullptr;             // [256 * nblk_s]
+    uint32_t* hist = nullptr;             // [256 * nblk_s] per-block digit counts, then [256] digit totals
     int nblk_s = 0;
     int key_bits = 16;
     uint32_t* offsets = nullptr;          // [total_bins + 1]

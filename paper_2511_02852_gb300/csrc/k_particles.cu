@@ -314,51 +314,69 @@ __global__ void __launch_bounds__(kTpb) k_radix_hist(const uint32_t* keys, const
     hist[threadIdx.x * nblk + blockIdx.x] = s_h[threadIdx.x];
 }
 
-// exclusive scan of the digit-major histogram (one block)
-__global__ void __launch_bounds__(1024) k_scan_hist(uint32_t* h, int n) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
+// exclusive scan of one digit's row of the digit-major histogram (block d
+// scans hist[d * nblk .. + nblk)) and that digit's total into dtot[d]
+__global__ void __launch_bounds__(kTpb) k_scan_digits(uint32_t* hist, int nblk, uint32_t* dtot) {
+    __shared__ uint32_t s_warp[kTpb / 32];
+    uint32_t* row = hist + (size_t)blockIdx.x * nblk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int start = 0; start < n; start += 1024) {
+    uint32_t carry = 0;
+    for (int start = 0; start < nblk; start += kTpb) {
         const int i = start + threadIdx.x;
-        const uint32_t v = i < n ? h[i] : 0u;
+        const uint32_t v = i < nblk ? row[i] : 0u;
         uint32_t x = v;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) s_warp[warp] = x;
         __syncthreads();
-        if (warp == 0) {
-            uint32_t w = s_warp[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;
+        uint32_t before = 0, all = 0;
+#pragma unroll
+        for (int w = 0; w < kTpb / 32; ++w) {
+            const uint32_t t = s_warp[w];
+            if (w < warp) before += t;
+            all += t;
         }
-        __syncthreads();
-        const uint32_t carry = s_carry;
-        if (i < n) h[i] = carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
+        if (i < nblk) row[i] = carry + before + x - v;
+        carry += all;
         __syncthreads();
     }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
 }
 
-// stable scatter: items ranked in index order within the block, round by round
+// stable scatter of one sort block's keys by digit: base of digit d = keys
+// of smaller digits (exclusive scan of the 256 digit totals) + keys of
+// digit d in earlier blocks (the scanned row)
 __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, const uint32_t* vin,
                                                         uint32_t* kout, uint32_t* vout,
                                                         const int32_t* count, int shift,
-                                                        const uint32_t* hist, int nblk) {
+                                                        const uint32_t* hist, const uint32_t* dtot,
+                                                        int nblk) {
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_wc[kTpb / 32][256];
+    __shared__ uint32_t s_dw[kTpb / 32];
     const int n = 2 * count[0];
     const int base = blockIdx.x * kTileS;
-    s_base[threadIdx.x] = hist[threadIdx.x * nblk + blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        // exclusive scan of the digit totals (one digit per thread)
+        const uint32_t v = dtot[threadIdx.x];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_dw[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int w = 0; w < kTpb / 32; ++w)
+            if (w < warp) before += s_dw[w];
+        s_base[threadIdx.x] = before + x - v + hist[threadIdx.x * nblk + blockIdx.x];
+    }
     const uint32_t lt = (1u << lane) - 1u;
     for (int k = 0; k < kSortItems; ++k) {
         const int i = base + k * kTpb + threadIdx.x;
@@ -391,17 +409,16 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
     }
 }
 
-// offsets[k] = first sorted position with key >= k (k = 0..total_bins)
+// offsets[k] = first sorted position with key >= k (k = 0..total_bins),
+// from the sorted keys in one pass: position e is the answer for every k in
+// (key[e-1], key[e]] (for e = 0 from 0, for e = n up to total_bins)
 __global__ void k_bin_offsets(const uint32_t* keys, const int32_t* count, uint32_t* offsets,
                               int total_bins) {
     const int n = 2 * count[0];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= total_bins; k += gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (keys[mid] < (uint32_t)k) lo = mid + 1; else hi = mid;
-        }
-        offsets[k] = (uint32_t)lo;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n; e += gridDim.x * blockDim.x) {
+        const int lo = e == 0 ? 0 : (int)keys[e - 1] + 1;
+        const int hi = e == n ? total_bins : min((int)keys[e], total_bins);
+        for (int k = lo; k <= hi; ++k) offsets[k] = (uint32_t)e;
     }
 }
 
@@ -424,16 +441,18 @@ __global__ void k_records(PatchDev p, const uint32_t* vals) {
         r.y = trough ? Y[i] - vq.w : Y[i];
         r.amp = trough ? -A : A;
         r.id = id;
-        // e^{-i pi (x mod 2R)/R}: exact integer reduction, then sincospi
-        const int64_t R2 = 2 * (int64_t)R;
-        int64_t xm = (int64_t)r.x % R2, ym = (int64_t)r.y % R2;
+        // e^{-i pi (x mod 2R)/R}: exact integer reduction (2R < 2^31), then
+        // sincospi of the FP32 quotient (within a few ulp of the exact one)
+        const int32_t R2 = 2 * R;
+        int32_t xm = r.x % R2, ym = r.y % R2;
         if (xm < 0) xm += R2;
         if (ym < 0) ym += R2;
+        const float invR = p.bk[bd >> 16].invR;
         float s, c;
-        sincospif((float)((double)xm / (double)R), &s, &c);
+        sincospif((float)xm * invR, &s, &c);
         r.cx = c;
         r.sx = -s;
-        sincospif((float)((double)ym / (double)R), &s, &c);
+        sincospif((float)ym * invR, &s, &c);
         r.cy = c;
         r.sy = -s;
         p.rec[e] = r;
@@ -476,12 +495,14 @@ cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = 8 * ps;
         k_radix_hist<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.count, shift, p.hist, p.nblk_s);
-        k_scan_hist<<<1, 1024, 0, st>>>(p.hist, 256 * p.nblk_s);
+        uint32_t* dtot = p.hist + (size_t)256 * p.nblk_s;
+        k_scan_digits<<<256, kTpb, 0, st>>>(p.hist, p.nblk_s, dtot);
         k_radix_scatter<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.vals[src], p.keys[1 - src],
-                                                   p.vals[1 - src], p.count, shift, p.hist, p.nblk_s);
+                                                   p.vals[1 - src], p.count, shift, p.hist, dtot, p.nblk_s);
         src = 1 - src;
     }
-    int ob = (p.total_bins + 1 + kTpb - 1) / kTpb;
+    int ob = (2 * p.cap + 1 + kTpb - 1) / kTpb;
+    if (ob > 152 * 8) ob = 152 * 8;
     k_bin_offsets<<<ob, kTpb, 0, st>>>(p.keys[src], p.count, p.offsets, p.total_bins);
     int rb = (2 * p.cap + kTpb - 1) / kTpb;
     if (rb > 152 * 16) rb = 152 * 16;
