@@ -61,6 +61,21 @@ def workload_config(name, rank=0):
     return cfg
 
 
+def reduce_over_ranks(total_s, total_evals, world, device):
+    """Whole-job figures of a weak-scaled run: the slowest rank's timed
+    seconds and the evals of all ranks (one process per GPU, each with its
+    own scene replica; no exchange on the data path)."""
+    if world <= 1:
+        return total_s, float(total_evals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(total_evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def describe(cfg):
     s = cfg["spectrum"]
     p = cfg["patches"][0]
@@ -253,14 +268,7 @@ def run_ours(args):
     launches = sc.launch_count() - launches0
     total_s = sum(step_ms) / 1000.0
     total_evals = sum(evals)
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([float(total_evals)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        total_s_all, total_evals_all = float(t.item()), float(e.item())
-    else:
-        total_s_all, total_evals_all = total_s, float(total_evals)
+    total_s_all, total_evals_all = reduce_over_ranks(total_s, total_evals, world, "cuda")
     value = total_evals_all / total_s_all
 
     # dominant kernel: tensor-core tile gather (k_synth_tc, with its bucket-group
