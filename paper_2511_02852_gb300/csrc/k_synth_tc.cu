@@ -26,7 +26,7 @@
 // that warp 9 stages in an eight-slot ring: it walks the bin ranges that
 // reach the tile, bucket by bucket, and bulk-copies each chunk's records with
 // the chunk's size and kernel radius beside them.  Each producer thread owns
-// one tile row or column and one half of the chunk's bumps; the kernel phase
+// two tile rows or columns and a quarter of the chunk's bumps; the kernel phase
 // pi (X_n - x_b)/R of its sample is the product of its own
 // e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the bump's
 // e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half per
@@ -177,33 +177,40 @@ __device__ __forceinline__ void store_split8(uint16_t* hi, uint16_t* lo, int off
     *reinterpret_cast<uint4*>((char*)lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Operand rows of one producer thread for its 16 bumps of a chunk.  ROW: the
-// tile row whose B rows are S A (1 + cos(pi v/R)) and S A sin(pi v/R)
-// (`amul` = S); otherwise the tile column whose A rows are 1 + cos(pi u/R)
+// Operand rows of one producer thread: bumps 8q .. 8q + 7 of a chunk (one
+// 16-byte K chunk) for two tile rows or columns, idx and idx + 32.  ROW: the
+// tile rows whose B rows are S A (1 + cos(pi v/R)) and S A sin(pi v/R)
+// (`amul` = S); otherwise the tile columns whose A rows are 1 + cos(pi u/R)
 // and sin(pi u/R) (`amul` = 1); zero outside the support |u| < R.  `rec`
 // points at this role's 16-byte half of each 32-byte record: {x, cx, sx, id}
-// or {y, cy, sy, amp}; (ct, st) = e^{i pi (pos mod 2R)/R}.
+// or {y, cy, sy, amp}; (ct[e], st[e]) = e^{i pi (pos[e] mod 2R)/R}.
 template <bool ROW>
-__device__ __forceinline__ void gen_half_chunk(uint16_t* hi, uint16_t* lo, const float4* rec, int half, int idx,
-                                               int32_t pos, int32_t R, float ct, float st, float amul) {
+__device__ __forceinline__ void gen_quarter(uint16_t* hi, uint16_t* lo, const float4* rec, int q, int idx,
+                                            const int32_t (&pos)[2], int32_t R, const float (&ct)[2],
+                                            const float (&st)[2], float amul) {
     const uint32_t span = (uint32_t)(2 * R - 1);
+    float4 r[8];
 #pragma unroll
-    for (int qq = 0; qq < kKc / 16; ++qq) {
-        const int q = 2 * half + qq;   // 16-byte K chunk: bumps 8q .. 8q + 7
+    for (int j = 0; j < 8; ++j) {
+        r[j] = rec[2 * (8 * q + j)];
+        if (ROW) r[j].w *= amul;   // S A, shared by both rows
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
         float f0[8], f1[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const float4 r = rec[2 * (8 * q + j)];
-            const int32_t u = pos - __float_as_int(r.x);
-            const bool in = (uint32_t)(u + R - 1) < span;          // -R < u < R
-            const float cs = ct * r.y - st * r.z;                  // cos pi u / R
-            const float sn = st * r.y + ct * r.z;                  // sin pi u / R
-            const float m = in ? (ROW ? r.w * amul : amul) : 0.f;  // S A, or 1; 0 outside the support
+            const int32_t u = pos[e] - __float_as_int(r[j].x);
+            const bool in = (uint32_t)(u + R - 1) < span;              // -R < u < R
+            const float cs = ct[e] * r[j].y - st[e] * r[j].z;          // cos pi u / R
+            const float sn = st[e] * r[j].y + ct[e] * r[j].z;          // sin pi u / R
+            const float m = in ? (ROW ? r[j].w : amul) : 0.f;          // S A, or 1; 0 outside the support
             f0[j] = fmaf(m, cs, m);
             f1[j] = m * sn;
         }
-        store_split8(hi, lo, canon(idx, q), f0);
-        store_split8(hi, lo, canon(kTX + idx, q), f1);   // kTX == kTY: second half of either operand
+        const int ent = idx + 32 * e;
+        store_split8(hi, lo, canon(ent, q), f0);
+        store_split8(hi, lo, canon(kTX + ent, q), f1);   // kTX == kTY: second half of either operand
     }
 }
 
@@ -412,39 +419,45 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
     } else {
         // ======================= producers ===================================
         const int32_t Xlo = tx0 * kQi + kHalfi, Ylo = ty0 * kQi + kHalfi;
-        // producer thread t builds bumps 16 (t >> 7) .. +15 of each chunk for
-        // row (t & 127) if (t & 127) < 64, else for column (t & 127) - 64
-        const int half = tid >> 7, tq = tid & 127;
-        const bool is_row = tq < kTY;
-        const int idx = is_row ? tq : tq - kTY;
-        const int32_t pos = (is_row ? Ylo : Xlo) + idx * kQi;   // this thread's texel centre
+        // producer warp w builds bumps 8 (w & 3) .. +7 of each chunk for tile
+        // rows (w < 4) or columns (w >= 4); lane l for rows/columns l and l + 32
+        static_assert(kTX == 64 && kTY == 64 && kKc == 32 && kProdWarps == 8, "producer mapping");
+        const bool is_row = warp < 4;
+        const int kq = warp & 3, idx = lane;
+        const int32_t pos0 = (is_row ? Ylo : Xlo) + idx * kQi;   // this thread's texel centres
+        const int32_t pos[2] = {pos0, pos0 + 32 * kQi};
         int produced = 0;      // stages filled
+        int fs = 0;            // stage slot of the next stage, and its empty-barrier parity
+        uint32_t fpar = 1u;
+        int rs = 0;            // record slot of the next chunk, and its parity
+        uint32_t rpar = 0u;
         int32_t R = 0;         // radius of the current bucket
-        float st = 0.f, ct = 1.f;
-        for (int gc = 0;; ++gc) {
-            const int rs = gc % kRecSlots;
-            bool ok = bar_wait(&S.rbar[rs], (uint32_t)((gc / kRecSlots) & 1), p.stats + 2);
+        float st[2] = {0.f, 0.f}, ct[2] = {1.f, 1.f};
+        for (;;) {
+            bool ok = bar_wait(&S.rbar[rs], rpar, p.stats + 2);
             if (__any_sync(0xffffffffu, !ok)) break;   // this warp stops; the others time out in turn
             const ChunkMeta m = S.meta[rs];
             if (m.n < 0) break;
-            if (m.R != R) {   // new bucket: this thread's phase factor e^{i pi (pos mod 2R) / R}
+            if (m.R != R) {   // new bucket: this thread's phase factors e^{i pi (pos mod 2R) / R}
                 R = m.R;
                 const int64_t R2 = 2 * (int64_t)R;
-                int64_t pm = (int64_t)pos % R2;
-                if (pm < 0) pm += R2;
-                sincospif((float)((double)pm / (double)R), &st, &ct);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    int64_t pm = (int64_t)pos[e] % R2;
+                    if (pm < 0) pm += R2;
+                    sincospif((float)((double)pm / (double)R), &st[e], &ct[e]);
+                }
             }
-            const int fs = produced % kStages;
-            ok = bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
+            ok = bar_wait(&S.empty[fs], fpar, p.stats + 2);
             if (__any_sync(0xffffffffu, !ok)) break;
             TcStage& T = S.st[fs];
             // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp};
             // slots past n hold sentinel records outside every support
             const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
             if (is_row)
-                gen_half_chunk<true>(T.Bhi, T.Blo, rc, half, idx, pos, R, ct, st, sp.row_scale);
+                gen_quarter<true>(T.Bhi, T.Blo, rc, kq, idx, pos, R, ct, st, sp.row_scale);
             else
-                gen_half_chunk<false>(T.Ahi, T.Alo, rc, half, idx, pos, R, ct, st, 1.f);
+                gen_quarter<false>(T.Ahi, T.Alo, rc, kq, idx, pos, R, ct, st, 1.f);
             if (tid == 0) S.stage_n[fs] = m.n;
             // every lane's operand stores visible to the tensor core, then
             // one arrival for the warp on each barrier
@@ -455,11 +468,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParam
                 bar_arrive(&S.full[fs]);
             }
             ++produced;
+            if (++fs == kStages) {
+                fs = 0;
+                fpar ^= 1u;
+            }
+            if (++rs == kRecSlots) {
+                rs = 0;
+                rpar ^= 1u;
+            }
         }
         // end of the stream for the MMA thread
         {
-            const int fs = produced % kStages;
-            bar_wait(&S.empty[fs], ((produced / kStages) & 1u) ^ 1u, p.stats + 2);
+            bar_wait(&S.empty[fs], fpar, p.stats + 2);
             if (tid == 0) S.stage_n[fs] = -1;
             __syncwarp();
             if (lane == 0) bar_arrive(&S.full[fs]);
