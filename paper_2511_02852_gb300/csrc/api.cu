@@ -485,7 +485,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     bin_geometry(*P);
     const size_t cap = (size_t)D.cap;
     D.nblk_c = (int)((cap + 1023) / 1024);
-    D.nblk_s = (int)((2 * cap + 4095) / 4096);
+    D.nblk_s = (int)((2 * cap + kSortTile - 1) / kSortTile);
     bool ok = true;
     for (int k = 0; k < 2; ++k) {
         D.x[k] = (int32_t*)dalloc(ctx, cap * 4);

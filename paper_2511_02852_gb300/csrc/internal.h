@@ -8,6 +8,7 @@ namespace scwp {
 
 constexpr int kMaxBuckets = 64;
 constexpr int kRotN = 128;          // per-bucket phase-rotation table length
+constexpr int kSortTile = 1024;     // keys per block of the binning radix sort
 constexpr int kMaxSegments = 2 * kMaxBuckets + 2;
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;

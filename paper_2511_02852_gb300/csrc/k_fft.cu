@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(kThreads) k_spectrum_rows(BgDev bg, double t, 
     }
 }
 
-// Columns pass: inverse FFT along y of `cw` columns per CTA, one plane at a
-// time; writes h = Re, Dx = Im (plane 0) and Dy = Re (plane 1).
+// Columns pass: inverse FFT along y of `cw` columns of plane blockIdx.y per
+// CTA; writes h = Re, Dx = Im (plane 0) and Dy = Re (plane 1).
 __global__ void __launch_bounds__(kThreads) k_fft_cols(BgDev bg, int cw) {
     extern __shared__ float2 sm[];
     const int N = bg.N;
@@ -128,27 +128,24 @@ __global__ void __launch_bounds__(kThreads) k_fft_cols(BgDev bg, int cw) {
     float2* a = sm + N;
     float2* b = a + (size_t)N * cw;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = bg.tw[i];
-    const int c0 = blockIdx.x * cw;
+    const int c0 = blockIdx.x * cw, p = blockIdx.y;
     const size_t plane = (size_t)N * N;
-    for (int p = 0; p < 2; ++p) {
-        for (int w = threadIdx.x; w < N * cw; w += blockDim.x) {
-            const int m = w / cw, c = w - m * cw;
-            a[w] = bg.G[p * plane + (size_t)m * N + c0 + c];
+    for (int w = threadIdx.x; w < N * cw; w += blockDim.x) {
+        const int m = w / cw, c = w - m * cw;
+        a[w] = bg.G[p * plane + (size_t)m * N + c0 + c];
+    }
+    __syncthreads();
+    const float2* res = fft_inverse_smem(a, b, N, cw, tw);
+    for (int w = threadIdx.x; w < N * cw; w += blockDim.x) {
+        const int jy = w / cw, c = w - jy * cw;
+        const float2 v = res[w];
+        const size_t o = (size_t)jy * N + c0 + c;
+        if (p == 0) {
+            bg.out[o] = v.x;
+            bg.out[plane + o] = v.y;
+        } else {
+            bg.out[2 * plane + o] = v.x;
         }
-        __syncthreads();
-        const float2* res = fft_inverse_smem(a, b, N, cw, tw);
-        for (int w = threadIdx.x; w < N * cw; w += blockDim.x) {
-            const int jy = w / cw, c = w - jy * cw;
-            const float2 v = res[w];
-            const size_t o = (size_t)jy * N + c0 + c;
-            if (p == 0) {
-                bg.out[o] = v.x;
-                bg.out[plane + o] = v.y;
-            } else {
-                bg.out[2 * plane + o] = v.x;
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -163,14 +160,15 @@ cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st) {
                                          (int)smr);
     if (e != cudaSuccess) return e;
     k_spectrum_rows<<<N / rpc, kThreads, smr, st>>>(bg, t, rpc);
-    int cw = 8192 / N;
+    // enough column groups to fill the SMs (both planes: 2 N / cw CTAs)
+    int cw = 2048 / N;
     if (cw > 16) cw = 16;
     if (cw < 1) cw = 1;
     if (cw > N) cw = N;
     const size_t smc = sizeof(float2) * ((size_t)N + 2 * (size_t)N * cw);
     e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
     if (e != cudaSuccess) return e;
-    k_fft_cols<<<N / cw, kThreads, smc, st>>>(bg, cw);
+    k_fft_cols<<<dim3(N / cw, 2), kThreads, smc, st>>>(bg, cw);
     count_launches(2);
     return cudaGetLastError();
 }

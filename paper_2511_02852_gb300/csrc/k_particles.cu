@@ -19,8 +19,8 @@ namespace {
 constexpr int kTpb = 256;
 constexpr int kItems = 4;                 // per thread in the compaction tiles
 constexpr int kTileC = kTpb * kItems;     // 1024 particles per compaction block
-constexpr int kSortItems = 16;
-constexpr int kTileS = kTpb * kSortItems; // 4096 keys per sort block
+constexpr int kSortItems = kSortTile / kTpb;
+constexpr int kTileS = kSortTile;     // keys per sort block
 constexpr int32_t kQi = 65536, kHalfi = 32768;
 
 // Texel centres of [0, n) strictly inside (C - R, C + R) along one axis.
