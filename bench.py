@@ -230,6 +230,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cfg = workload_config(args.workload, rank)
     sc = scwp.Scene(cfg, device=local)
+    if args.batched:
+        sc.set_batched(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     dt = cfg["dt"]
@@ -307,21 +309,24 @@ def run_ours(args):
     # end to end through the C ABI: step + read of the blended maps to pinned host memory
     e2e = None
     if not args.no_e2e:
-        H, W = sc.patch_shape(0)
-        host = [torch.empty((H, W), dtype=torch.float32, pin_memory=True) for _ in range(3)]
+        npatch = len(cfg["patches"])
+        shapes = [sc.patch_shape(p) for p in range(npatch)]
+        host = [[torch.empty((H, W), dtype=torch.float32, pin_memory=True) for _ in range(3)]
+                for (H, W) in shapes]
         import ctypes as C
         barrier()
         t0 = time.perf_counter()
         e2e_evals = 0
         for k in range(args.steps):
             sc.step(dt)
-            for f in range(3):
-                scwp.scwp_height_map(sc.ctx, 0, f, C.c_void_p(host[f].data_ptr()), H * W, 0)
-            e2e_evals += sc.stats(0).eval_count
+            for p, (H, W) in enumerate(shapes):
+                for f in range(3):
+                    scwp.scwp_height_map(sc.ctx, p, f, C.c_void_p(host[p][f].data_ptr()), H * W, 0)
+                e2e_evals += sc.stats(p).eval_count
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8,
-               "d2h_bytes_per_step": 3 * H * W * 4,
+               "d2h_bytes_per_step": sum(3 * H * W * 4 for (H, W) in shapes),
                "note": "scwp_step + scwp_height_map of h, Dx, Dy into pinned host buffers; "
                        "the per-step host input is dt (the injection counts and wake state are "
                        "computed by the library on the host and passed as kernel arguments)"}
@@ -344,6 +349,7 @@ def run_ours(args):
             "ms_per_step": 1000.0 * total_s_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(describe(cfg), parallelism=f"replicas{world}",
+                                                mode="batched" if args.batched else "plain",
                                                 synth_groups=[sc.info(p).synth_groups
                                                               for p in range(len(cfg["patches"]))]),
             "p50_ms": p50, "p99_ms": p99, "evals_per_step": evals_per_step,
@@ -366,6 +372,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="one synthesis launch over all patches of the frame (scwp_set_batched)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0)

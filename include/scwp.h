@@ -238,6 +238,17 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode);
 /* Select the synthesis used by scwp_step (SCWP_SYNTH_*). */
 scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode);
 
+/* Batched frame step (on != 0): the tensor-core synthesis of all patches of
+ * the context runs as one launch over the (patch, tile, bucket group) items
+ * of every patch, heaviest first by a work estimate, followed by one
+ * group-sum blend launch; per-patch bucket-group counts are planned for the
+ * whole frame instead of for each patch alone.  The results are the same
+ * sums as the one-patch-per-launch path (with another grouping, the same
+ * values up to FP32 rounding order).  Applies to SCWP_SYNTH_GATHER; the
+ * paper has no counterpart (its frame is one scene on one GPU).  Returns
+ * SCWP_E_INVALID for a null context; takes effect at the next synthesis. */
+scwp_status scwp_set_batched(scwp_ctx* ctx, int32_t on);
+
 /* Stage timing with CUDA events on the context's stream: enable (1) or
  * disable (0).  scwp_timing_read sums, over the frames stepped since the
  * last read, the device time of [0] background FFT, [1] particle stages

@@ -46,7 +46,11 @@ struct PatchHost {
     int64_t injected = 0;
     std::vector<double> energy;       // [nb]
     double band = 0;
-    std::vector<int> tc_order;        // launch order of the tensor-core synthesis items
+    std::vector<TcItem> tc_items;     // tensor-core synthesis items of this patch, launch order
+    std::vector<BlendSpan> tc_spans;  // its group-sum blend spans (G > 1)
+    TcItem* d_items = nullptr;
+    BlendSpan* d_spans = nullptr;
+    int partial_planes = 1;           // bucket-group partial planes allocated
     int tc_slots = 0;                 // resident CTA slots the plan assumed
 };
 
@@ -62,6 +66,10 @@ struct scwp_ctx {
     cudaStream_t st = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // particle-stage streams of a multi-patch context: patch i runs on
+    // pst[i % pst.size()], all forked from and joined back into st
+    std::vector<cudaStream_t> pst;
+    std::vector<cudaEvent_t> pev;
     std::string err;
     scwp_status sticky = SCWP_OK;
     SpectrumModel sm;
@@ -84,6 +92,18 @@ struct scwp_ctx {
     double ms_sum[4] = {0, 0, 0, 0};
     int64_t timed_frames = 0;
     int64_t launches = 0;             // kernels enqueued by this context
+    // tensor-core synthesis: patch descriptors and parameters on the device,
+    // and the batched plan (all patches in one launch)
+    bool batched = false;
+    bool synth_dirty = true;
+    int slots = 0;
+    PatchDev* d_pdevs = nullptr;
+    SynthParams* d_sps = nullptr;
+    std::vector<TcItem> b_items;
+    std::vector<BlendSpan> b_spans;
+    TcItem* d_bitems = nullptr;
+    BlendSpan* d_bspans = nullptr;
+    double b_makespan = 0.0;
 };
 
 namespace {
@@ -247,24 +267,23 @@ scwp_status upload_dt_tables(scwp_ctx* ctx, PatchHost& P) {
     return SCWP_OK;
 }
 
-// Plan of the tensor-core synthesis of one patch: the bucket-group count G
-// and the launch order of its (tile, group) items.  Each item's work is
-// estimated in operand stages from the expected bump density of each bucket
-// (steady-state shares proportional to (W Q + 2 R_i) / R_i^2, the prefill
-// rule) times the part of the tile's reach (the tile grown by R_i) inside the
-// particle domain (the patch grown by R_i).  Items are ordered heaviest
-// first, so in-order block dispatch approximates longest-processing-time
-// scheduling; G minimises the simulated makespan of that dispatch over the
-// device's resident CTA slots plus the traffic of the group-sum blend.
-struct TcPlan {
-    int G = 1;
-    std::vector<int> order;
-};
+// Plans of the tensor-core synthesis.  Each (tile, bucket group) item's work
+// is estimated in operand stages from the expected bump density of each
+// bucket: steady-state shares proportional to (W Q + 2 R_i) / R_i^2 (the
+// prefill rule), two bumps per particle, times the part of the tile's reach
+// (the tile grown by R_i) that lies inside the particle domain (the patch
+// grown by R_i).  Items run heaviest first, so in-order block dispatch
+// approximates longest-processing-time scheduling.
+constexpr double kItemStages = 2.0;   // set-up and read-out of one item, in stages
+constexpr double kStageUs = 1.3;      // one stage on one CTA slot (two CTAs per SM)
+constexpr double kHbmBytesPerUs = 6.8e6;
 
-TcPlan plan_tc(const PatchHost& P, int slots) {
+// expected operand stages of every (tile, bucket) of a patch, [tiles][nb]
+std::vector<double> tile_bucket_stages(const PatchHost& P, int& tiles) {
     const PatchTablesHost& T = P.T;
     const int ts = synth_tc_tile(), kc = synth_tc_stage_bumps();
-    const int ntx = (T.W + ts - 1) / ts, nty = (T.H + ts - 1) / ts, tiles = ntx * nty;
+    const int ntx = (T.W + ts - 1) / ts, nty = (T.H + ts - 1) / ts;
+    tiles = ntx * nty;
     // bumps: two per live particle (crest and trough)
     const double total = 2.0 * (P.d.prefill > 0 ? (double)P.d.prefill : 0.5 * (double)P.d.max_particles);
     std::vector<double> w(T.nb);
@@ -273,7 +292,7 @@ TcPlan plan_tc(const PatchHost& P, int slots) {
         w[i] = ((double)T.W * kQ + 2.0 * T.R[i]) / ((double)T.R[i] * (double)T.R[i]);
         sw += w[i];
     }
-    std::vector<double> est((size_t)tiles * T.nb);   // stages per (tile, bucket)
+    std::vector<double> est((size_t)tiles * T.nb);
     for (int i = 0; i < T.nb; ++i) {
         const double r = (double)T.R[i] / kQ;
         const double dens = total * w[i] / sw / ((T.W + 2 * r) * (T.H + 2 * r));
@@ -285,41 +304,106 @@ TcPlan plan_tc(const PatchHost& P, int slots) {
             est[(size_t)t * T.nb + i] = std::ceil(dens * ax * ay / kc);
         }
     }
-    constexpr double kItemStages = 2.0;   // set-up and read-out of one item, in stages
-    constexpr double kStageUs = 1.3;      // one stage on one CTA slot (two CTAs per SM)
-    constexpr double kHbmBytesPerUs = 6.8e6;
-    TcPlan best;
+    return est;
+}
+
+double item_work(const std::vector<double>& est, int nb, int t, int g, int G) {
+    double s = kItemStages;
+    for (int i = (g * nb) / G; i < ((g + 1) * nb) / G; ++i) s += est[(size_t)t * nb + i];
+    return s;
+}
+
+// makespan of in-order dispatch of `work` (already in launch order) on `slots`
+double makespan(const std::vector<double>& work, const std::vector<int>& order, int slots) {
+    std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+    for (int k = 0; k < std::max(slots, 1); ++k) q.push(0.0);
+    double m = 0.0;
+    for (int it : order) {
+        const double f = q.top() + work[it];
+        q.pop();
+        q.push(f);
+        m = std::max(m, f);
+    }
+    return m;
+}
+
+std::vector<BlendSpan> blend_spans(const PatchHost& P, int G) {
+    std::vector<BlendSpan> out;
+    if (G <= 1) return out;
+    const int nq = ((P.T.W + 3) / 4) * P.T.H;
+    constexpr int kQuadsPerSpan = 2048;
+    for (int q0 = 0; q0 < nq; q0 += kQuadsPerSpan) out.push_back(BlendSpan{P.index, q0, std::min(nq, q0 + kQuadsPerSpan), G});
+    return out;
+}
+
+// Plan of one patch launched alone: G minimises the simulated makespan over
+// the device's resident CTA slots plus the traffic of the group-sum blend.
+void plan_patch(PatchHost& P, int slots) {
+    int tiles = 0;
+    const std::vector<double> est = tile_bucket_stages(P, tiles);
+    const int nb = P.T.nb;
     double best_cost = 0.0;
-    const int gmax = std::min(T.nb, 16);
-    for (int G = 1; G <= gmax; ++G) {
+    for (int G = 1; G <= std::min(nb, 16); ++G) {
         std::vector<double> work((size_t)tiles * G);
         for (int t = 0; t < tiles; ++t)
-            for (int g = 0; g < G; ++g) {
-                double s = kItemStages;
-                for (int i = (g * T.nb) / G; i < ((g + 1) * T.nb) / G; ++i) s += est[(size_t)t * T.nb + i];
-                work[(size_t)t * G + g] = s;
-            }
+            for (int g = 0; g < G; ++g) work[(size_t)t * G + g] = item_work(est, nb, t, g, G);
         std::vector<int> order(work.size());
         for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
-        std::priority_queue<double, std::vector<double>, std::greater<double>> q;
-        for (int k = 0; k < std::max(slots, 1); ++k) q.push(0.0);
-        double makespan = 0.0;
-        for (int it : order) {
-            const double f = q.top() + work[it];
-            q.pop();
-            q.push(f);
-            makespan = std::max(makespan, f);
-        }
-        const double blend = G > 1 ? (G + 1) * 12.0 * T.W * T.H / kHbmBytesPerUs : 0.0;
-        const double cost = makespan * kStageUs + blend;
+        const double blend = G > 1 ? (G + 1) * 12.0 * P.T.W * P.T.H / kHbmBytesPerUs : 0.0;
+        const double cost = makespan(work, order, slots) * kStageUs + blend;
         if (G == 1 || cost < best_cost) {
             best_cost = cost;
-            best.G = G;
-            best.order = order;
+            P.dev.groups_tc = G;
+            P.tc_items.clear();
+            for (int k : order) P.tc_items.push_back(TcItem{P.index, k / G, k % G, G});
         }
     }
-    return best;
+    P.tc_spans = blend_spans(P, P.dev.groups_tc);
+}
+
+// Plan of all patches in one launch: each patch's G is the smallest that
+// keeps its largest item under a quarter of the average per-slot load, and
+// all items of all patches run heaviest first.
+void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vector<BlendSpan>& spans,
+                  double& model_makespan) {
+    items.clear();
+    spans.clear();
+    std::vector<std::vector<double>> est(ctx->patches.size());
+    std::vector<int> tiles(ctx->patches.size());
+    double total = 0.0;
+    for (size_t k = 0; k < ctx->patches.size(); ++k) {
+        est[k] = tile_bucket_stages(*ctx->patches[k], tiles[k]);
+        for (double e : est[k]) total += e;
+        total += kItemStages * tiles[k];
+    }
+    const double cap = 0.25 * total / std::max(slots, 1);
+    std::vector<double> work;
+    for (size_t k = 0; k < ctx->patches.size(); ++k) {
+        const PatchHost& P = *ctx->patches[k];
+        const int nb = P.T.nb, gmax = std::min(std::min(nb, 16), P.partial_planes);
+        int G = 1;
+        for (;; ++G) {
+            double mx = 0.0;
+            for (int t = 0; t < tiles[k]; ++t)
+                for (int g = 0; g < G; ++g) mx = std::max(mx, item_work(est[k], nb, t, g, G));
+            if (mx <= cap || G >= gmax) break;
+        }
+        for (int t = 0; t < tiles[k]; ++t)
+            for (int g = 0; g < G; ++g) {
+                items.push_back(TcItem{P.index, t, g, G});
+                work.push_back(item_work(est[k], nb, t, g, G));
+            }
+        const std::vector<BlendSpan> sp = blend_spans(P, G);
+        spans.insert(spans.end(), sp.begin(), sp.end());
+    }
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    model_makespan = makespan(work, order, slots);
+    std::vector<TcItem> sorted;
+    for (int k : order) sorted.push_back(items[k]);
+    items.swap(sorted);
 }
 
 scwp_status ready(scwp_ctx* ctx) {
@@ -357,13 +441,74 @@ SynthParams synth_params(scwp_ctx* ctx, const PatchHost& P) {
     return sp;
 }
 
-scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P) {
-    CU(cudaMemsetAsync(P.dev.stats, 0, 2 * sizeof(unsigned long long), ctx->st));
-    CU(cudaMemsetAsync(P.dev.stats + 3, 0, (size_t)P.T.nb * sizeof(unsigned long long), ctx->st));
+scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P, cudaStream_t st) {
+    CU(cudaMemsetAsync(P.dev.stats, 0, 2 * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(P.dev.stats + 3, 0, ((size_t)P.T.nb + 1) * sizeof(unsigned long long), st));
+    return SCWP_OK;
+}
+
+// streams for the particle stages of up to kParticleStreams patches at once
+constexpr int kParticleStreams = 8;
+scwp_status particle_streams(scwp_ctx* ctx) {
+    const size_t want = std::min<size_t>(ctx->patches.size(), kParticleStreams);
+    while (ctx->pst.size() < want) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            if (s) cudaStreamDestroy(s);
+            cudaGetLastError();
+            return fail(ctx, SCWP_E_CUDA, "particle streams");
+        }
+        ctx->pst.push_back(s);
+        ctx->pev.push_back(e);
+    }
+    return SCWP_OK;
+}
+
+// device copies of the patch descriptors and synthesis parameters (and the
+// batched plan) after the set of patches or the batching mode changed
+scwp_status sync_synth(scwp_ctx* ctx) {
+    if (!ctx->synth_dirty) return SCWP_OK;
+    const size_t n = ctx->patches.size();
+    std::vector<PatchDev> pd(n);
+    std::vector<SynthParams> sp(n);
+    for (size_t k = 0; k < n; ++k) {
+        pd[k] = ctx->patches[k]->dev;
+        sp[k] = synth_params(ctx, *ctx->patches[k]);
+    }
+    ctx->d_pdevs = (PatchDev*)dalloc(ctx, std::max<size_t>(1, n) * sizeof(PatchDev));
+    ctx->d_sps = (SynthParams*)dalloc(ctx, std::max<size_t>(1, n) * sizeof(SynthParams));
+    if (!ctx->d_pdevs || !ctx->d_sps) return fail(ctx, SCWP_E_NOMEM, "synthesis descriptors");
+    CU(cudaMemcpyAsync(ctx->d_pdevs, pd.data(), n * sizeof(PatchDev), cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemcpyAsync(ctx->d_sps, sp.data(), n * sizeof(SynthParams), cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->batched) {
+        plan_batched(ctx, ctx->slots, ctx->b_items, ctx->b_spans, ctx->b_makespan);
+        ctx->d_bitems = (TcItem*)dalloc(ctx, std::max<size_t>(1, ctx->b_items.size()) * sizeof(TcItem));
+        ctx->d_bspans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, ctx->b_spans.size()) * sizeof(BlendSpan));
+        if (!ctx->d_bitems || !ctx->d_bspans) return fail(ctx, SCWP_E_NOMEM, "batched plan");
+        CU(cudaMemcpyAsync(ctx->d_bitems, ctx->b_items.data(), ctx->b_items.size() * sizeof(TcItem),
+                           cudaMemcpyHostToDevice, ctx->st));
+        if (!ctx->b_spans.empty())
+            CU(cudaMemcpyAsync(ctx->d_bspans, ctx->b_spans.data(), ctx->b_spans.size() * sizeof(BlendSpan),
+                               cudaMemcpyHostToDevice, ctx->st));
+    }
+    // the host vectors are copied before they go out of scope
+    CU(cudaStreamSynchronize(ctx->st));
+    ctx->synth_dirty = false;
     return SCWP_OK;
 }
 
 scwp_status synthesize(scwp_ctx* ctx, int mode) {
+    if (mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32) {
+        scwp_status s = sync_synth(ctx);
+        if (s != SCWP_OK) return s;
+        if (ctx->batched) {
+            CU(launch_synth_tc(ctx->d_bitems, (int)ctx->b_items.size(), ctx->d_pdevs, ctx->d_sps, ctx->d_bspans,
+                               (int)ctx->b_spans.size(), ctx->st));
+            return SCWP_OK;
+        }
+    }
     for (PatchHost* P : ctx->patches) {
         const SynthParams sp = synth_params(ctx, *P);
         if (mode == SCWP_SYNTH_LAYERED) {
@@ -384,8 +529,8 @@ scwp_status synthesize(scwp_ctx* ctx, int mode) {
         } else if (mode == SCWP_SYNTH_GATHER_FP32) {
             CU(launch_synth_gather(P->dev, sp, ctx->st));
         } else {
-            CU(cudaMemsetAsync(P->dev.stats + 3 + P->T.nb, 0, sizeof(unsigned long long), ctx->st));
-            CU(launch_synth_tc(P->dev, sp, ctx->st));
+            CU(launch_synth_tc(P->d_items, (int)P->tc_items.size(), ctx->d_pdevs, ctx->d_sps, P->d_spans,
+                               (int)P->tc_spans.size(), ctx->st));
         }
     }
     return SCWP_OK;
@@ -523,12 +668,14 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int per_sm = synth_tc_ctas_per_sm();
         P->tc_slots = sms * (per_sm > 0 ? per_sm : 1);
-        const TcPlan plan = plan_tc(*P, P->tc_slots);
-        D.groups_tc = plan.G;
-        P->tc_order = plan.order;
-        D.tc_order = (int*)dalloc(ctx, plan.order.size() * sizeof(int));
-        ok = ok && D.tc_order;
+        ctx->slots = P->tc_slots;
+        D.patch = P->index;
+        plan_patch(*P, P->tc_slots);
+        P->d_items = (TcItem*)dalloc(ctx, P->tc_items.size() * sizeof(TcItem));
+        P->d_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, P->tc_spans.size()) * sizeof(BlendSpan));
+        ok = ok && P->d_items && P->d_spans;
         const int G = D.groups > D.groups_tc ? D.groups : D.groups_tc;
+        P->partial_planes = G;
         if (G > 1) {
             D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
             ok = ok && D.partial;
@@ -577,8 +724,11 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     int32_t counts[2] = {n0, n0};
     CU(cudaMemcpyAsync(D.amp, ampf.data(), ng * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(D.bk, P->bk.data(), T.nb * sizeof(BucketDev), cudaMemcpyHostToDevice, ctx->st));
-    CU(cudaMemcpyAsync(D.tc_order, P->tc_order.data(), P->tc_order.size() * sizeof(int), cudaMemcpyHostToDevice,
+    CU(cudaMemcpyAsync(P->d_items, P->tc_items.data(), P->tc_items.size() * sizeof(TcItem), cudaMemcpyHostToDevice,
                        ctx->st));
+    if (!P->tc_spans.empty())
+        CU(cudaMemcpyAsync(P->d_spans, P->tc_spans.data(), P->tc_spans.size() * sizeof(BlendSpan),
+                           cudaMemcpyHostToDevice, ctx->st));
     // per-bucket phase steps of n texels: e^{i pi n Q / R_i}, n < kRotN
     std::vector<float2> rot((size_t)T.nb * kRotN);
     for (int i = 0; i < T.nb; ++i)
@@ -602,6 +752,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     P->carry.assign((size_t)T.nb * 2, 0.0);
     P->energy.assign(T.nb, 0.0);
     ctx->patches.push_back(P);
+    ctx->synth_dirty = true;
     if (patch_id) *patch_id = P->index;
     // velocity tables for the current dt (a provisional 1/60 s before the
     // first step, so the trough offsets are valid for scwp_resynthesize)
@@ -674,11 +825,19 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
     CU(cudaEventRecord(ctx->ev_join, ctx->side));
     ctx->bg_valid = true;
 
+    // one patch: the context stream; several: up to kParticleStreams
+    // streams, so that the small kernels of different patches overlap
+    const bool multi = ctx->patches.size() > 1;
+    if (multi) {
+        if ((s = particle_streams(ctx)) != SCWP_OK) return s;
+        for (cudaStream_t ps : ctx->pst) CU(cudaStreamWaitEvent(ps, ctx->ev_fork, 0));
+    }
     for (PatchHost* P : ctx->patches) {
         PatchDev& D = P->dev;
         const PatchTablesHost& T = P->T;
-        CU(launch_advect_flag(D, ctx->st));
-        CU(launch_compact(D, ctx->st));
+        cudaStream_t pst = multi ? ctx->pst[P->index % ctx->pst.size()] : ctx->st;
+        CU(launch_advect_flag(D, pst));
+        CU(launch_compact(D, pst));
         D.cur ^= 1;
         InjectParams ip{};
         ip.frame = (uint32_t)ctx->frame;
@@ -748,10 +907,15 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
         ip.nseg = nseg;
         ip.total = total;
         P->injected += total;
-        if (total > 0) CU(launch_inject(D, ip, ctx->st));
-        if ((s = reset_frame_stats(ctx, *P)) != SCWP_OK) return s;
-        CU(launch_bin(D, ctx->st));
+        if (total > 0) CU(launch_inject(D, ip, pst));
+        if ((s = reset_frame_stats(ctx, *P, pst)) != SCWP_OK) return s;
+        CU(launch_bin(D, pst));
     }
+    if (multi)
+        for (size_t k = 0; k < ctx->pst.size(); ++k) {
+            CU(cudaEventRecord(ctx->pev[k], ctx->pst[k]));
+            CU(cudaStreamWaitEvent(ctx->st, ctx->pev[k], 0));
+        }
     if (fe && (s = record(ctx, fe->e[1], ctx->st)) != SCWP_OK) return s;
     CU(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
     if (fe && (s = record(ctx, fe->e[2], ctx->st)) != SCWP_OK) return s;
@@ -778,12 +942,20 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
         ctx->bg_valid = true;
     }
     for (PatchHost* P : ctx->patches) {
-        if ((s = reset_frame_stats(ctx, *P)) != SCWP_OK) return s;
+        if ((s = reset_frame_stats(ctx, *P, ctx->st)) != SCWP_OK) return s;
         CU(launch_bin(P->dev, ctx->st));
     }
     if ((s = synthesize(ctx, mode)) != SCWP_OK) return s;
     ctx->launches += launches_total() - before;
     CU(cudaStreamSynchronize(ctx->st));
+    return SCWP_OK;
+}
+
+scwp_status scwp_set_batched(scwp_ctx* ctx, int32_t on) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    ctx->batched = on != 0;
+    ctx->synth_dirty = true;
     return SCWP_OK;
 }
 
@@ -865,7 +1037,7 @@ scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info
     out->total_bins = P->dev.total_bins;
     out->capacity = P->dev.cap;
     out->synth_groups = P->dev.groups_tc;
-    out->synth_items = (int32_t)P->tc_order.size();
+    out->synth_items = (int32_t)P->tc_items.size();
     out->synth_slots = P->tc_slots;
     for (int i = 0; i < P->T.nb; ++i) {
         out->bin_cells[i] = P->bin_cells[i];
@@ -1040,12 +1212,18 @@ void scwp_destroy(scwp_ctx* ctx) {
         cudaStreamSynchronize(ctx->st);
         if (ctx->side) cudaStreamSynchronize(ctx->side);
     }
+    for (cudaStream_t s : ctx->pst) cudaStreamSynchronize(s);
     cudaGetLastError();
     for (FrameEvents& f : ctx->ring)
         for (int k = 0; k < 6; ++k)
             if (f.e[k]) cudaEventDestroy(f.e[k]);
     for (PatchHost* P : ctx->patches) delete P;
     dfree_all(ctx);
+    for (cudaStream_t s : ctx->pst) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    for (cudaEvent_t e : ctx->pev) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->side) cudaStreamDestroy(ctx->side);

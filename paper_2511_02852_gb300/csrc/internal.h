@@ -64,12 +64,23 @@ struct PatchDev {
     float* partial = nullptr;             // [groups][3][H][W] per-bucket-group sums (groups > 1)
     int groups = 1;                       // bucket groups of the CUDA-core synthesis
     int groups_tc = 1;                    // bucket groups of the tensor-core synthesis
-    int* tc_order = nullptr;              // [groups_tc * tiles] launch order of (tile, group) items:
-                                          // item = tile * groups_tc + group, heaviest first
+    int patch = 0;                        // index of the patch in its context
     unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..3+nb) live per bucket,
                                           // [3+nb] operand stages of the last tensor-core synthesis
     float* layers = nullptr;              // layered variant scratch (lazy)
     size_t layers_bytes = 0;
+};
+
+// One work item of the tensor-core synthesis: bucket group `group` of
+// `groups` over tile `tile` of patch `patch`.
+struct TcItem {
+    int32_t patch, tile, group, groups;
+};
+
+// One span of the group-sum blend: quads [q0, q1) (4 texels of a row) of
+// patch `patch`, whose synthesis used `groups` bucket groups.
+struct BlendSpan {
+    int32_t patch, q0, q1, groups;
 };
 
 // One spawn segment of a frame's injection (Sec. 3.3 Eqs. 15-17 / Sec. 4.3).
@@ -118,12 +129,19 @@ cudaError_t launch_compact(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st);
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
-cudaError_t launch_synth_tc(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
+// Tensor-core synthesis of `n_items` items (any patches) in one launch, then
+// the group-sum blend of `n_spans` spans in one launch.  `pdevs` and `sps`
+// are device arrays indexed by patch.
+cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
+                            const BlendSpan* spans, int n_spans, cudaStream_t st);
 // tensor-core synthesis geometry: tile side (texels), bumps per operand stage,
 // and resident CTAs per SM (0 on error)
 int synth_tc_tile();
 int synth_tc_stage_bumps();
 int synth_tc_ctas_per_sm();
+// group sums and blend of `n_spans` spans of any patches, one launch
+cudaError_t launch_blend_spans(const BlendSpan* spans, int n_spans, const PatchDev* pdevs, const SynthParams* sps,
+                               cudaStream_t st);
 // sum `groups` partial [3][H][W] planes at src (in order), blend, store to p.out
 cudaError_t launch_blend(const PatchDev& p, const SynthParams& sp, const float* src, int groups,
                          cudaStream_t st);

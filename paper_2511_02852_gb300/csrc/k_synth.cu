@@ -207,48 +207,62 @@ __device__ __forceinline__ void store_row4(float* out, size_t plane, int W, int 
     }
 }
 
-// sum of the bucket-group partials (in group order) and the blend
-__global__ void __launch_bounds__(256) k_blend_groups(PatchDev p, SynthParams sp, const float* partial,
-                                                      int groups) {
+// sum of the bucket-group partials (in group order) and the blend of quad q
+// (texels 4 (q mod qw) .. + 3 of row q / qw)
+__device__ __forceinline__ void blend_quad(const PatchDev& p, const SynthParams& sp, const float* partial,
+                                           int groups, int q) {
     const size_t plane = (size_t)sp.W * sp.H;
     const int qw = (sp.W + 3) / 4;
-    const int nq = qw * sp.H;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-        const int iy = q / qw, ix0 = 4 * (q - iy * qw);
-        float acc[3][4];
+    const int iy = q / qw, ix0 = 4 * (q - iy * qw);
+    float acc[3][4];
 #pragma unroll
-        for (int f = 0; f < 3; ++f)
+    for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) acc[f][cc] = 0.f;
-        const size_t rowo = (size_t)iy * sp.W;
-        const bool vec = (sp.W & 3) == 0 && ix0 + 3 < sp.W;
-        for (int g = 0; g < groups; ++g) {
-            const float* src = partial + (size_t)g * 3 * plane;
+        for (int cc = 0; cc < 4; ++cc) acc[f][cc] = 0.f;
+    const size_t rowo = (size_t)iy * sp.W;
+    const bool vec = (sp.W & 3) == 0 && ix0 + 3 < sp.W;
+    for (int g = 0; g < groups; ++g) {
+        const float* src = partial + (size_t)g * 3 * plane;
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                if (vec) {
-                    const float4 v = *reinterpret_cast<const float4*>(src + f * plane + rowo + ix0);
-                    acc[f][0] += v.x;
-                    acc[f][1] += v.y;
-                    acc[f][2] += v.z;
-                    acc[f][3] += v.w;
-                } else {
+        for (int f = 0; f < 3; ++f) {
+            if (vec) {
+                const float4 v = *reinterpret_cast<const float4*>(src + f * plane + rowo + ix0);
+                acc[f][0] += v.x;
+                acc[f][1] += v.y;
+                acc[f][2] += v.z;
+                acc[f][3] += v.w;
+            } else {
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc)
-                        if (ix0 + cc < sp.W) acc[f][cc] += src[f * plane + rowo + ix0 + cc];
-                }
+                for (int cc = 0; cc < 4; ++cc)
+                    if (ix0 + cc < sp.W) acc[f][cc] += src[f * plane + rowo + ix0 + cc];
             }
         }
-        float o[3][4];
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            float bgv[3];
-            const float w = blend_at(sp, ix0 + cc, iy, bgv);
-#pragma unroll
-            for (int f = 0; f < 3; ++f) o[f][cc] = w * acc[f][cc] + (1.f - w) * bgv[f];
-        }
-        store_row4(p.out, plane, sp.W, iy, ix0, o);
     }
+    float o[3][4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        float bgv[3];
+        const float w = blend_at(sp, ix0 + cc, iy, bgv);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) o[f][cc] = w * acc[f][cc] + (1.f - w) * bgv[f];
+    }
+    store_row4(p.out, plane, sp.W, iy, ix0, o);
+}
+
+__global__ void __launch_bounds__(256) k_blend_groups(PatchDev p, SynthParams sp, const float* partial,
+                                                      int groups) {
+    const int nq = ((sp.W + 3) / 4) * sp.H;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
+        blend_quad(p, sp, partial, groups, q);
+}
+
+// the same over spans of any patches: one CTA per span
+__global__ void __launch_bounds__(256) k_blend_spans(const BlendSpan* spans, const PatchDev* pdevs,
+                                                     const SynthParams* sps) {
+    const BlendSpan sn = spans[blockIdx.x];
+    const PatchDev& p = pdevs[sn.patch];
+    const SynthParams& sp = sps[sn.patch];
+    for (int q = sn.q0 + threadIdx.x; q < sn.q1; q += blockDim.x) blend_quad(p, sp, p.partial, sn.groups, q);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_synth_gather(PatchDev p, SynthParams sp) {
@@ -504,6 +518,13 @@ cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaSt
     k_synth_gather<<<grid, kThreads, sm, st>>>(p, sp);
     count_launches(1);
     if (G > 1) return launch_blend(p, sp, p.partial, G, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_spans(const BlendSpan* spans, int n_spans, const PatchDev* pdevs, const SynthParams* sps,
+                               cudaStream_t st) {
+    k_blend_spans<<<n_spans, 256, 0, st>>>(spans, pdevs, sps);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,8 @@ struct TcSmem {
     unsigned long long done;             // final MMA commit -> epilogue
     int stage_n[kStages];                // bumps in the stage; -1 ends the stream
     uint32_t tmem;
+    alignas(16) unsigned char pd[sizeof(PatchDev)];     // this item's patch
+    alignas(16) unsigned char spd[sizeof(SynthParams)];
 };
 static_assert(sizeof(TcStage) % 1024 == 0, "stage alignment");
 static_assert(offsetof(TcSmem, rec) % 16 == 0, "record staging alignment");
@@ -247,17 +249,28 @@ __device__ __forceinline__ float blend1(const SynthParams& sp, int ix, int iy, i
     return w * wp + (1.f - w) * bg;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_synth_tc(PatchDev p, SynthParams sp) {
+__global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, const PatchDev* pdevs,
+                                                          const SynthParams* sps) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // this CTA's (tile, bucket group) item, in the host-planned order
-    const int G = p.groups_tc;
-    const int item = p.tc_order[blockIdx.x];
-    const int tile = item / G, g = item - tile * G;
-    const int ntx = (p.W + kTX - 1) / kTX;
+    // this CTA's (patch, tile, bucket group) item, in the host-planned order
+    const TcItem it = items[blockIdx.x];
+    {
+        static_assert(sizeof(PatchDev) % 4 == 0 && sizeof(SynthParams) % 4 == 0, "descriptor copy");
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(pdevs + it.patch);
+        const uint32_t* b = reinterpret_cast<const uint32_t*>(sps + it.patch);
+        for (int k = tid; k < (int)(sizeof(PatchDev) / 4); k += kThreads) reinterpret_cast<uint32_t*>(S.pd)[k] = a[k];
+        for (int k = tid; k < (int)(sizeof(SynthParams) / 4); k += kThreads)
+            reinterpret_cast<uint32_t*>(S.spd)[k] = b[k];
+    }
+    const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
+    const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
+    const int G = it.groups, g = it.group, tile = it.tile;
+    // (read from global memory: the shared copies are read after the first barrier)
+    const int ntx = (pdevs[it.patch].W + kTX - 1) / kTX, nb = sps[it.patch].nb;
     const int tx0 = (tile % ntx) * kTX, ty0 = (tile / ntx) * kTY;
-    const int b_begin = (g * sp.nb) / G, b_end = ((g + 1) * sp.nb) / G;
+    const int b_begin = (g * nb) / G, b_end = ((g + 1) * nb) / G;
 
     if (tid == 0) {
         for (int k = 0; k < kRecSlots; ++k) {
@@ -568,15 +581,16 @@ int synth_tc_ctas_per_sm() {
     return n;
 }
 
-cudaError_t launch_synth_tc(const PatchDev& p, const SynthParams& sp, cudaStream_t st) {
+cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
+                            const BlendSpan* spans, int n_spans, cudaStream_t st) {
     const size_t sm = sizeof(TcSmem);
     cudaError_t e = tc_attributes();
     if (e != cudaSuccess) return e;
-    if (!p.tc_order || (p.groups_tc > 1 && !p.partial)) return cudaErrorInvalidValue;
-    const int tiles = ((p.W + kTX - 1) / kTX) * ((p.H + kTY - 1) / kTY);
-    k_synth_tc<<<tiles * p.groups_tc, kThreads, sm, st>>>(p, sp);
-    count_launches(1);
-    if (p.groups_tc > 1) return launch_blend(p, sp, p.partial, p.groups_tc, st);
+    if (n_items > 0) {
+        k_synth_tc<<<n_items, kThreads, sm, st>>>(items, pdevs, sps);
+        count_launches(1);
+    }
+    if (n_spans > 0) return launch_blend_spans(spans, n_spans, pdevs, sps, st);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,7 @@ EXPORTS = {
                                 C.c_int64, C.POINTER(C.c_int64)]),
     "scwp_resynthesize": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_synth_mode": (C.c_int, [C.c_void_p, C.c_int32]),
+    "scwp_set_batched": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "scwp_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -351,6 +352,9 @@ class Scene:
 
     def set_synth_mode(self, mode):
         _check(lib().scwp_set_synth_mode(self.ctx, mode), self.ctx)
+
+    def set_batched(self, on):
+        _check(lib().scwp_set_batched(self.ctx, 1 if on else 0), self.ctx)
 
     def set_timing(self, on):
         _check(lib().scwp_set_timing(self.ctx, 1 if on else 0), self.ctx)

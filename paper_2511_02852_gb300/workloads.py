@@ -116,6 +116,29 @@ def small_two_patches(seed=5):
     return scene("small_two_patches", spec, [pa, pb], frames=8)
 
 
+# -- small_batch: a parity-sized batched frame: 5 patches of uneven sides
+#    (48..200 cells, ragged against the 64-texel tiles), 3-9 equal-energy
+#    buckets each, 300-3000 prefilled particles, three with wakes; one
+#    spectrum; patch draws from seed 7.
+def small_batch(n_patches=5, seed=7):
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(48, 201, size=(n_patches, 2))
+    counts = np.round(np.exp(rng.uniform(math.log(300), math.log(3000), n_patches))).astype(int)
+    nbs = rng.integers(3, 10, n_patches)
+    spec = spectrum(spectrum=JONSWAP, wind_speed=10.0, fetch=50e3, gamma=3.3,
+                    depth=40.0, n_buckets=6, n_theta=8, wind_dir=0.3,
+                    fft_n=128, fft_L=300.0, seed=seed)
+    ps = []
+    for i in range(n_patches):
+        ps.append(patch(origin_x=float(rng.uniform(-100, 100)), origin_y=float(rng.uniform(-100, 100)),
+                        cell=0.25 if i % 2 else 0.5, width=int(sides[i, 0]), height=int(sides[i, 1]),
+                        max_particles=int(4 * counts[i] + 2048), prefill=int(counts[i]),
+                        inject_scale=1.0, emitter=1 if i < 3 else 0, obj_radius=2.0,
+                        obj_speed=3.0 + i, obj_path_radius=4.0, wake_amp=0.03, wake_rate=1,
+                        n_buckets=int(nbs[i])))
+    return scene("small_batch", spec, ps, frames=6)
+
+
 # -- batched: 1024^2 FFT over 1 km; 32 patches, sides log-uniform in
 #    [64, 1024] cells at 0.25 m, 8-32 equal-energy buckets each (drawn per
 #    patch; all patches share one spectrum), 10k-500k particles
@@ -157,4 +180,4 @@ def scaled(sc, **patch_overrides):
 
 
 ALL = {"tiny": tiny, "realistic": realistic, "small_jonswap": small_jonswap,
-       "small_two_patches": small_two_patches, "batched": batched}
+       "small_two_patches": small_two_patches, "small_batch": small_batch, "batched": batched}

@@ -289,3 +289,33 @@ def test_both_gather_kernels_match_oracle(mode_name):
     ref, _ = orc.patch_maps(0)
     compare_maps(sc.maps(0), ref, orc.spec.Hs(), mode_name)
     sc.close()
+
+
+def test_batched_frame_matches_plain_and_oracle():
+    """One synthesis launch over all patches (scwp_set_batched): bit-exact
+    state and bins, maps within the contract of the oracle, and within
+    FP32 rounding of the one-patch-per-launch path, on a frame of five
+    uneven patches."""
+    cfg = wl.small_batch()
+    a = make(cfg)
+    b = make(cfg)
+    b.set_batched(True)
+    orc = OracleScene(cfg)
+    hs = orc.spec.Hs()
+    for f in range(1, 7):
+        a.step(cfg["dt"])
+        b.step(cfg["dt"])
+        orc.step(cfg["dt"])
+        if f in (2, 6):
+            bg = orc.background()
+            for p in range(len(cfg["patches"])):
+                compare_state(b, orc, p)
+                compare_bins(b, orc, p)
+                ref, ev = orc.patch_maps(p, bg)
+                assert b.stats(p).eval_count == ev
+                mb, ma = b.maps(p), a.maps(p)
+                compare_maps(mb, ref, hs, f"batched frame {f} patch {p}")
+                for x, y in zip(mb, ma):
+                    assert np.abs(x.astype(np.float64) - y).max() <= 1e-5 * hs
+    a.close()
+    b.close()
