@@ -104,6 +104,18 @@ struct scwp_ctx {
     TcItem* d_bitems = nullptr;
     BlendSpan* d_bspans = nullptr;
     double b_makespan = 0.0;
+    // captured batched frames (one per parity of the particle buffers)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool gvalid[2] = {false, false};
+    bool gpending[2] = {false, false};
+    uint64_t gmask[2] = {0, 0};
+    long long glaunches[2] = {0, 0};
+    cudaEvent_t gdone[2] = {nullptr, nullptr};
+    cudaStream_t gst = nullptr;       // capture origin (the caller's stream may be the legacy one)
+    void* hstage[2] = {nullptr, nullptr};
+    unsigned char* dparams = nullptr;
+    size_t params_bytes = 0;
+    std::vector<InjectParams> ips;    // this frame's injection plans
 };
 
 namespace {
@@ -447,6 +459,18 @@ scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P, cudaStream_t st) {
     return SCWP_OK;
 }
 
+// drop the captured frames (after a change that the captures baked in)
+void graph_reset(scwp_ctx* ctx) {
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->gpending[k] && ctx->gdone[k]) cudaEventSynchronize(ctx->gdone[k]);
+        ctx->gpending[k] = false;
+        if (ctx->gexec[k]) cudaGraphExecDestroy(ctx->gexec[k]);
+        ctx->gexec[k] = nullptr;
+        ctx->gvalid[k] = false;
+    }
+    cudaGetLastError();
+}
+
 // streams for the particle stages of up to kParticleStreams patches at once
 constexpr int kParticleStreams = 8;
 scwp_status particle_streams(scwp_ctx* ctx) {
@@ -564,7 +588,9 @@ scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
     };
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gdone[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gdone[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return bail(SCWP_E_CUDA);
     }
@@ -751,6 +777,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     CU(cudaStreamSynchronize(ctx->st));
     P->carry.assign((size_t)T.nb * 2, 0.0);
     P->energy.assign(T.nb, 0.0);
+    graph_reset(ctx);
     ctx->patches.push_back(P);
     ctx->synth_dirty = true;
     if (patch_id) *patch_id = P->index;
@@ -788,6 +815,85 @@ static scwp_status drain_ring(scwp_ctx* ctx) {
 
 static scwp_status step_impl(scwp_ctx* ctx, double dt);
 
+// Host side of one patch's frame: the injection plan (FP64 carries of
+// Eqs. 15-17 per bucket and edge pair, Sec. 3.3) and the wake segments of
+// the moving object (Sec. 4.3); updates the carries, injected counts and
+// energies.
+static void frame_injection(scwp_ctx* ctx, PatchHost* P, InjectParams& ip_out) {
+    const PatchTablesHost& T = P->T;
+    const PatchDev& D = P->dev;
+    InjectParams& ip = ip_out;
+    ip = InjectParams{};
+    ip.frame = (uint32_t)ctx->frame;
+    ip.patch = (uint32_t)P->index;
+    ip.seed = ctx->d.seed;
+    ip.W = T.W;
+    ip.H = T.H;
+    ip.nth = T.nth;
+    int total = 0, nseg = 0;
+    for (int i = 0; i < T.nb; ++i)
+        for (int sp = 0; sp < 2; ++sp) {
+            double& acc = P->carry[(size_t)i * 2 + sp];
+            acc += T.injection_rate(i, sp);
+            const double m = std::floor(acc);
+            acc -= m;
+            const int nv = P->nvalid[i * 2 + sp];
+            if (m <= 0 || nv == 0) continue;
+            const int mi = (int)m;
+            Segment& g = ip.seg[nseg++];
+            g.bucket = i;
+            g.s = sp;
+            g.count = mi * nv;
+            g.first = total;
+            g.ndir = nv;
+            total += g.count;
+            double e = 0.0;
+            for (int k = 0; k < nv; ++k) {
+                const int j = P->dirlist[((size_t)i * 2 + sp) * T.nth + k];
+                const double A = T.amp[(size_t)i * T.nth + j];
+                e += 0.125 * A * A * M_PI * T.r[i] * T.r[i];
+            }
+            P->energy[i] += mi * e;
+        }
+    if (D.emitter && P->d.wake_rate > 0) {
+        // reading of Sec. 4.3: object on a circle about the patch centre
+        const double dx = P->d.cell;
+        const double Rp = P->d.obj_path_radius / dx;
+        const double Om = P->d.obj_speed / P->d.obj_path_radius;
+        const double phi = Om * ctx->t;
+        ip.Px = T.W * 0.5 + Rp * std::cos(phi);
+        ip.Py = T.H * 0.5 + Rp * std::sin(phi);
+        const double psi = phi + M_PI / 2.0;
+        ip.rho = P->d.obj_radius / dx;
+        const double kelvin = M_PI / 2.0 - std::asin(1.0 / 3.0);
+        const double dpsi = 2.0 * M_PI / kWakeDirs;
+        for (int arm = 0; arm < 2; ++arm) {
+            const double sgn = arm == 0 ? 1.0 : -1.0;
+            const double psa = psi + sgn * kelvin;
+            int64_t a = (int64_t)std::floor(psa / dpsi + 0.5);
+            a = ((a % kWakeDirs) + kWakeDirs) % kWakeDirs;
+            ip.ca[arm] = T.wake_cos[a];
+            ip.sa[arm] = T.wake_sin[a];
+            Segment& g = ip.seg[nseg++];
+            g.bucket = T.wake_bucket;
+            g.s = 2;
+            g.count = P->d.wake_rate;
+            g.first = total;
+            g.ndir = P->d.wake_rate;
+            g.arm = arm;
+            g.wake_a = (int)a;
+            total += g.count;
+            const double rw = T.r[T.wake_bucket];
+            P->energy[T.wake_bucket] +=
+                P->d.wake_rate * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
+        }
+    }
+    ip.nseg = nseg;
+    ip.total = total;
+    P->injected += total;
+}
+
+
 scwp_status scwp_step(scwp_ctx* ctx, double dt) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
@@ -797,30 +903,17 @@ scwp_status scwp_step(scwp_ctx* ctx, double dt) {
     return s;
 }
 
-static scwp_status step_impl(scwp_ctx* ctx, double dt) {
+// Enqueue one frame's kernels.  ips: the host plans (eager launches pass
+// them by value); ip_dev / t_dev: their device copies (captured frames read
+// the frame's parameters from device memory).
+static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>& ips, const InjectParams* ip_dev,
+                          const double* t_dev, FrameEvents* fe) {
     scwp_status s = SCWP_OK;
-    if (!(dt > 0)) return fail(ctx, SCWP_E_INVALID, "dt must be > 0");
-    if (dt != ctx->dt) {
-        ctx->dt = dt;
-        for (PatchHost* P : ctx->patches) {
-            if (dt == P->T.dt) continue;
-            P->T.set_dt(dt);
-            if ((s = upload_dt_tables(ctx, *P)) != SCWP_OK) return s;
-        }
-    }
-    ctx->frame += 1;
-    ctx->t += dt;
-    FrameEvents* fe = nullptr;
-    if (ctx->timing) {
-        if (ctx->ring_n == kTimingRing && (s = drain_ring(ctx)) != SCWP_OK) return s;
-        fe = &ctx->ring[ctx->ring_n++];
-        if ((s = record(ctx, fe->e[0], ctx->st)) != SCWP_OK) return s;
-    }
     // background on the side stream, concurrent with the particle stages
     CU(cudaEventRecord(ctx->ev_fork, ctx->st));
     CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     if (fe && (s = record(ctx, fe->e[4], ctx->side)) != SCWP_OK) return s;
-    CU(launch_background(ctx->bg, ctx->t, ctx->side));
+    CU(launch_background(ctx->bg, ctx->t, ctx->side, t_dev));
     if (fe && (s = record(ctx, fe->e[5], ctx->side)) != SCWP_OK) return s;
     CU(cudaEventRecord(ctx->ev_join, ctx->side));
     ctx->bg_valid = true;
@@ -832,82 +925,17 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
         if ((s = particle_streams(ctx)) != SCWP_OK) return s;
         for (cudaStream_t ps : ctx->pst) CU(cudaStreamWaitEvent(ps, ctx->ev_fork, 0));
     }
-    for (PatchHost* P : ctx->patches) {
+    for (size_t k = 0; k < ctx->patches.size(); ++k) {
+        PatchHost* P = ctx->patches[k];
         PatchDev& D = P->dev;
-        const PatchTablesHost& T = P->T;
         cudaStream_t pst = multi ? ctx->pst[P->index % ctx->pst.size()] : ctx->st;
         CU(launch_advect_flag(D, pst));
         CU(launch_compact(D, pst));
         D.cur ^= 1;
-        InjectParams ip{};
-        ip.frame = (uint32_t)ctx->frame;
-        ip.patch = (uint32_t)P->index;
-        ip.seed = ctx->d.seed;
-        ip.W = T.W;
-        ip.H = T.H;
-        ip.nth = T.nth;
-        int total = 0, nseg = 0;
-        for (int i = 0; i < T.nb; ++i)
-            for (int sp = 0; sp < 2; ++sp) {
-                double& acc = P->carry[(size_t)i * 2 + sp];
-                acc += T.injection_rate(i, sp);
-                const double m = std::floor(acc);
-                acc -= m;
-                const int nv = P->nvalid[i * 2 + sp];
-                if (m <= 0 || nv == 0) continue;
-                const int mi = (int)m;
-                Segment& g = ip.seg[nseg++];
-                g.bucket = i;
-                g.s = sp;
-                g.count = mi * nv;
-                g.first = total;
-                g.ndir = nv;
-                total += g.count;
-                double e = 0.0;
-                for (int k = 0; k < nv; ++k) {
-                    const int j = P->dirlist[((size_t)i * 2 + sp) * T.nth + k];
-                    const double A = T.amp[(size_t)i * T.nth + j];
-                    e += 0.125 * A * A * M_PI * T.r[i] * T.r[i];
-                }
-                P->energy[i] += mi * e;
-            }
-        if (D.emitter && P->d.wake_rate > 0) {
-            // reading of Sec. 4.3: object on a circle about the patch centre
-            const double dx = P->d.cell;
-            const double Rp = P->d.obj_path_radius / dx;
-            const double Om = P->d.obj_speed / P->d.obj_path_radius;
-            const double phi = Om * ctx->t;
-            ip.Px = T.W * 0.5 + Rp * std::cos(phi);
-            ip.Py = T.H * 0.5 + Rp * std::sin(phi);
-            const double psi = phi + M_PI / 2.0;
-            ip.rho = P->d.obj_radius / dx;
-            const double kelvin = M_PI / 2.0 - std::asin(1.0 / 3.0);
-            const double dpsi = 2.0 * M_PI / kWakeDirs;
-            for (int arm = 0; arm < 2; ++arm) {
-                const double sgn = arm == 0 ? 1.0 : -1.0;
-                const double psa = psi + sgn * kelvin;
-                int64_t a = (int64_t)std::floor(psa / dpsi + 0.5);
-                a = ((a % kWakeDirs) + kWakeDirs) % kWakeDirs;
-                ip.ca[arm] = T.wake_cos[a];
-                ip.sa[arm] = T.wake_sin[a];
-                Segment& g = ip.seg[nseg++];
-                g.bucket = T.wake_bucket;
-                g.s = 2;
-                g.count = P->d.wake_rate;
-                g.first = total;
-                g.ndir = P->d.wake_rate;
-                g.arm = arm;
-                g.wake_a = (int)a;
-                total += g.count;
-                const double rw = T.r[T.wake_bucket];
-                P->energy[T.wake_bucket] +=
-                    P->d.wake_rate * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
-            }
-        }
-        ip.nseg = nseg;
-        ip.total = total;
-        P->injected += total;
-        if (total > 0) CU(launch_inject(D, ip, pst));
+        if (ip_dev)
+            CU(launch_inject_dev(D, ip_dev + k, pst));
+        else if (ips[k].total > 0)
+            CU(launch_inject(D, ips[k], pst));
         if ((s = reset_frame_stats(ctx, *P, pst)) != SCWP_OK) return s;
         CU(launch_bin(D, pst));
     }
@@ -923,6 +951,113 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
     if (fe && (s = record(ctx, fe->e[3], ctx->st)) != SCWP_OK) return s;
     CU(cudaGetLastError());
     return SCWP_OK;
+}
+
+// A batched frame as a CUDA graph: captured once for each parity of the
+// particle double buffers (every patch flips its live buffer each frame)
+// and replayed.  The frame's parameters (time, injection plans) reach the
+// graph through one copy from a pinned staging buffer per graph; a graph's
+// staging buffer is rewritten only after its previous replay completed.
+static scwp_status step_graph(scwp_ctx* ctx, const std::vector<InjectParams>& ips) {
+    scwp_status s = SCWP_OK;
+    uint64_t mask = 0;
+    for (size_t k = 0; k < ctx->patches.size(); ++k) mask |= (uint64_t)(ctx->patches[k]->dev.cur & 1) << k;
+    int g = -1;
+    for (int k = 0; k < 2; ++k)
+        if (ctx->gvalid[k] && ctx->gmask[k] == mask) g = k;
+    if (g < 0) g = !ctx->gvalid[0] ? 0 : 1;
+    const size_t bytes = 16 + ips.size() * sizeof(InjectParams);
+    if (!ctx->dparams || ctx->params_bytes < bytes) {
+        graph_reset(ctx);
+        ctx->dparams = (unsigned char*)dalloc(ctx, bytes);
+        if (!ctx->dparams) return fail(ctx, SCWP_E_NOMEM, "graph parameters");
+        for (int k = 0; k < 2; ++k) {
+            if (cudaMallocHost(&ctx->hstage[k], bytes) != cudaSuccess) {
+                ctx->hstage[k] = nullptr;
+                cudaGetLastError();
+                return fail(ctx, SCWP_E_NOMEM, "graph staging");
+            }
+        }
+        ctx->params_bytes = bytes;
+        g = 0;
+    }
+    if (ctx->gpending[g]) CU(cudaEventSynchronize(ctx->gdone[g]));
+    unsigned char* h = (unsigned char*)ctx->hstage[g];
+    memcpy(h, &ctx->t, sizeof(double));
+    memcpy(h + 16, ips.data(), ips.size() * sizeof(InjectParams));
+    if (!ctx->gvalid[g]) {
+        // everything that synchronises or allocates happens before the capture
+        if ((s = sync_synth(ctx)) != SCWP_OK) return s;
+        if (ctx->patches.size() > 1 && (s = particle_streams(ctx)) != SCWP_OK) return s;
+        if (!ctx->gst && cudaStreamCreateWithFlags(&ctx->gst, cudaStreamNonBlocking) != cudaSuccess) {
+            ctx->gst = nullptr;
+            return fail(ctx, SCWP_E_CUDA, "capture stream");
+        }
+        const long long before = launches_total();
+        // the frame is recorded as if enqueued on the context stream
+        cudaStream_t caller = ctx->st;
+        ctx->st = ctx->gst;
+        cudaError_t e = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeRelaxed);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaSuccess;
+        if (e == cudaSuccess) {
+            e = cudaMemcpyAsync(ctx->dparams, h, bytes, cudaMemcpyHostToDevice, ctx->st);
+            if (e == cudaSuccess)
+                s = enqueue_frame(ctx, ips, reinterpret_cast<const InjectParams*>(ctx->dparams + 16),
+                                  reinterpret_cast<const double*>(ctx->dparams), nullptr);
+            e2 = cudaStreamEndCapture(ctx->st, &graph);
+        }
+        ctx->st = caller;
+        if (e != cudaSuccess || s != SCWP_OK || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return s != SCWP_OK ? s : fail(ctx, SCWP_E_CUDA, "frame capture");
+        }
+        e = cudaGraphInstantiate(&ctx->gexec[g], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->gexec[g] = nullptr;
+            return fail(ctx, SCWP_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        ctx->gvalid[g] = true;
+        ctx->gmask[g] = mask;
+        ctx->glaunches[g] = launches_total() - before;
+    } else {
+        for (PatchHost* P : ctx->patches) P->dev.cur ^= 1;   // what the replay does on the device
+        count_launches((int)ctx->glaunches[g]);
+    }
+    CU(cudaGraphLaunch(ctx->gexec[g], ctx->st));
+    CU(cudaEventRecord(ctx->gdone[g], ctx->st));
+    ctx->gpending[g] = true;
+    return SCWP_OK;
+}
+
+static scwp_status step_impl(scwp_ctx* ctx, double dt) {
+    scwp_status s = SCWP_OK;
+    if (!(dt > 0)) return fail(ctx, SCWP_E_INVALID, "dt must be > 0");
+    if (dt != ctx->dt) {
+        ctx->dt = dt;
+        for (PatchHost* P : ctx->patches) {
+            if (dt == P->T.dt) continue;
+            P->T.set_dt(dt);
+            if ((s = upload_dt_tables(ctx, *P)) != SCWP_OK) return s;
+        }
+    }
+    ctx->frame += 1;
+    ctx->t += dt;
+    std::vector<InjectParams>& ips = ctx->ips;
+    ips.resize(ctx->patches.size());
+    for (size_t k = 0; k < ctx->patches.size(); ++k) frame_injection(ctx, ctx->patches[k], ips[k]);
+    // batched frames replay a captured graph unless stage timing is on
+    if (ctx->batched && !ctx->timing && ctx->synth_mode == SCWP_SYNTH_GATHER && ctx->patches.size() <= 64)
+        return step_graph(ctx, ips);
+    FrameEvents* fe = nullptr;
+    if (ctx->timing) {
+        if (ctx->ring_n == kTimingRing && (s = drain_ring(ctx)) != SCWP_OK) return s;
+        fe = &ctx->ring[ctx->ring_n++];
+        if ((s = record(ctx, fe->e[0], ctx->st)) != SCWP_OK) return s;
+    }
+    return enqueue_frame(ctx, ips, nullptr, nullptr, fe);
 }
 
 scwp_status scwp_launch_count(scwp_ctx* ctx, int64_t* n) {
@@ -954,6 +1089,7 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
 scwp_status scwp_set_batched(scwp_ctx* ctx, int32_t on) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
+    graph_reset(ctx);
     ctx->batched = on != 0;
     ctx->synth_dirty = true;
     return SCWP_OK;
@@ -964,6 +1100,7 @@ scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode) {
     if (s != SCWP_OK) return s;
     if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32)
         return fail(ctx, SCWP_E_INVALID, "mode");
+    graph_reset(ctx);
     ctx->synth_mode = mode;
     return SCWP_OK;
 }
@@ -1213,6 +1350,12 @@ void scwp_destroy(scwp_ctx* ctx) {
         if (ctx->side) cudaStreamSynchronize(ctx->side);
     }
     for (cudaStream_t s : ctx->pst) cudaStreamSynchronize(s);
+    graph_reset(ctx);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->hstage[k]) cudaFreeHost(ctx->hstage[k]);
+        if (ctx->gdone[k]) cudaEventDestroy(ctx->gdone[k]);
+    }
+    if (ctx->gst) cudaStreamDestroy(ctx->gst);
     cudaGetLastError();
     for (FrameEvents& f : ctx->ring)
         for (int k = 0; k < 6; ++k)

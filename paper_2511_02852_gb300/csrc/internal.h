@@ -127,6 +127,9 @@ long long launches_total();
 cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_compact(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st);
+// injection with the frame's parameters read from device memory (a fixed
+// grid, so that the launch can be replayed from a CUDA graph)
+cudaError_t launch_inject_dev(const PatchDev& p, const InjectParams* ip, cudaStream_t st);
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
 // Tensor-core synthesis of `n_items` items (any patches) in one launch, then
@@ -159,6 +162,7 @@ struct BgDev {
     float* out = nullptr;         // [3][N][N] h, Dx, Dy
     float lam = 1.f, dk = 0.f;
 };
-cudaError_t launch_background(const BgDev& b, double t, cudaStream_t st);
+// t_dev: if not null, the time is read from device memory (graph replay)
+cudaError_t launch_background(const BgDev& b, double t, cudaStream_t st, const double* t_dev = nullptr);
 
 }  // namespace scwp

@@ -70,7 +70,8 @@ __device__ float2* fft_inverse_smem(float2* a, float2* b, int N, int T, const fl
 
 // Rows pass: spectrum update (a1) + inverse FFT along x of h~ + i D~x and D~y.
 // One CTA handles `rpc` consecutive rows (2 rpc interleaved transforms).
-__global__ void __launch_bounds__(kThreads) k_spectrum_rows(BgDev bg, double t, int rpc) {
+__global__ void __launch_bounds__(kThreads) k_spectrum_rows(BgDev bg, double t_arg, const double* t_dev, int rpc) {
+    const double t = t_dev ? *t_dev : t_arg;
     extern __shared__ float2 sm[];
     const int N = bg.N;
     const int T = 2 * rpc;
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_cols(BgDev bg, int cw) {
 
 }  // namespace
 
-cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st) {
+cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st, const double* t_dev) {
     const int N = bg.N;
     int rpc = N >= 512 ? 1 : 512 / N;
     if (rpc > N) rpc = N;
@@ -159,7 +160,7 @@ cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_spectrum_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smr);
     if (e != cudaSuccess) return e;
-    k_spectrum_rows<<<N / rpc, kThreads, smr, st>>>(bg, t, rpc);
+    k_spectrum_rows<<<N / rpc, kThreads, smr, st>>>(bg, t, t_dev, rpc);
     // enough column groups to fill the SMs (both planes: 2 N / cw CTAs)
     int cw = 2048 / N;
     if (cw > 16) cw = 16;

@@ -183,7 +183,7 @@ __global__ void k_clear_flags(uint8_t* flags, int cap) {
 }
 
 // ---- a4 + a5: injection and wake emission -------------------------------------
-__global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) {
+__device__ __forceinline__ void inject_body(const PatchDev& p, const InjectParams& ip) {
     const int base = p.count[1];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t want = (int64_t)base + ip.total;
@@ -236,6 +236,11 @@ __global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) {
         BD[idx] = bd;
     }
 }
+
+__global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) { inject_body(p, ip); }
+
+// the same with the frame's parameters in device memory (CUDA-graph replay)
+__global__ void __launch_bounds__(kTpb) k_inject_dev(PatchDev p, const InjectParams* ip) { inject_body(p, *ip); }
 
 // ---- a6: binning ---------------------------------------------------------------
 __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, uint32_t* vals) {
@@ -481,6 +486,12 @@ cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_
     if (blocks < 1) blocks = 1;
     if (blocks > 1024) blocks = 1024;
     k_inject<<<blocks, kTpb, 0, st>>>(p, ip);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_dev(const PatchDev& p, const InjectParams* ip, cudaStream_t st) {
+    k_inject_dev<<<152 * 2, kTpb, 0, st>>>(p, ip);
     count_launches(1);
     return cudaGetLastError();
 }

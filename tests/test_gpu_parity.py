@@ -299,12 +299,16 @@ def test_batched_frame_matches_plain_and_oracle():
     cfg = wl.small_batch()
     a = make(cfg)
     b = make(cfg)
-    b.set_batched(True)
+    b.set_batched(True)          # captured frame graphs, replayed from frame 3
+    c = make(cfg)
+    c.set_batched(True)
+    c.set_timing(True)           # the same frames launched one kernel at a time
     orc = OracleScene(cfg)
     hs = orc.spec.Hs()
     for f in range(1, 7):
         a.step(cfg["dt"])
         b.step(cfg["dt"])
+        c.step(cfg["dt"])
         orc.step(cfg["dt"])
         if f in (2, 6):
             bg = orc.background()
@@ -317,5 +321,13 @@ def test_batched_frame_matches_plain_and_oracle():
                 compare_maps(mb, ref, hs, f"batched frame {f} patch {p}")
                 for x, y in zip(mb, ma):
                     assert np.abs(x.astype(np.float64) - y).max() <= 1e-5 * hs
+                for x, y in zip(mb, c.maps(p)):
+                    assert np.array_equal(x, y)     # graph replay == eager launches
+                assert b.stats(p).injected_total == c.stats(p).injected_total
+    # the captured frame launches the injection kernel even when a patch
+    # injects nothing this frame (the eager path skips it)
+    n_inj = len(cfg["patches"]) * 6
+    assert c.launch_count() <= b.launch_count() <= c.launch_count() + n_inj
     a.close()
     b.close()
+    c.close()
