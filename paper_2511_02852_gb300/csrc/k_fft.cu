@@ -161,10 +161,13 @@ cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st, const 
                                          (int)smr);
     if (e != cudaSuccess) return e;
     k_spectrum_rows<<<N / rpc, kThreads, smr, st>>>(bg, t, t_dev, rpc);
-    // enough column groups to fill the SMs (both planes: 2 N / cw CTAs)
+    // enough column groups to fill the SMs (both planes: 2 N / cw CTAs), at
+    // least 4 columns (one 32-byte sector of each row) where shared memory
+    // (twiddles + two buffers of N x cw) still leaves two CTAs per SM
     int cw = 2048 / N;
     if (cw > 16) cw = 16;
-    if (cw < 1) cw = 1;
+    if (cw < 4) cw = 4;
+    while (cw > 1 && sizeof(float2) * ((size_t)N + 2 * (size_t)N * cw) > 110 * 1024) cw >>= 1;   // two CTAs per SM
     if (cw > N) cw = N;
     const size_t smc = sizeof(float2) * ((size_t)N + 2 * (size_t)N * cw);
     e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
