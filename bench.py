@@ -215,6 +215,95 @@ def run_reference(args):
     return 0
 
 
+# ---- serving ---------------------------------------------------------------------------
+def run_serving(args):
+    """Open-loop serving run: Poisson frame-step requests over the serving
+    scenes through the frame-step server (continuous batching); latency =
+    completion seen by polling minus scheduled arrival."""
+    import numpy as np
+    import torch
+    from paper_2511_02852_gb300 import scwp
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    scenes = wl.serving()
+    sv = scwp.Server(hbm_budget_bytes=int(args.hbm_budget_gb * 1e9), max_inflight=args.inflight)
+    t_adm = time.perf_counter()
+    sid = [sv.add_scene(c) for c in scenes]
+    t_adm = time.perf_counter() - t_adm
+    admitted = [k for k, s in enumerate(sid) if s is not None]
+    dt = 1.0 / 60.0
+
+    def drain(n_req, first_id):
+        got = 0
+        while got < n_req:
+            sv.tick()
+            got += len(sv.poll())
+        return got
+
+    rid = 10 ** 9                       # warm-up: every scene twice (both graph-free paths warm)
+    for _ in range(2):
+        for k in admitted:
+            sv.submit(sid[k], dt, rid)
+            rid += 1
+        drain(len(admitted), 0)
+    torch.cuda.synchronize()
+
+    def eval_total():
+        tot = 0
+        for k in admitted:
+            v = sv.scene(sid[k])
+            tot += sum(v.stats(p).eval_total for p in range(len(scenes[k]["patches"])))
+        return tot
+
+    e0 = eval_total()
+    t_arr, s_arr = wl.serving_arrivals(rate=args.rate, seconds=args.serve_seconds, n_scenes=len(scenes))
+    keep = np.array([sid[s] is not None for s in s_arr], dtype=bool)
+    t_arr, s_arr = t_arr[keep], s_arr[keep]
+    n = len(t_arr)
+    lat = np.full(n, np.nan)
+    clk = ClockSampler(0)
+    clk.start()
+    i = done = 0
+    t0 = time.perf_counter()
+    while done < n:
+        now = time.perf_counter() - t0
+        while i < n and t_arr[i] <= now:
+            sv.submit(sid[s_arr[i]], dt, i)
+            i += 1
+        while sv.tick():
+            pass
+        fin = sv.poll()
+        if fin:
+            tnow = time.perf_counter() - t0
+            for r in fin:
+                lat[r] = tnow - t_arr[r]
+            done += len(fin)
+    elapsed = time.perf_counter() - t0
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    evals = eval_total() - e0
+    info = sv.info()
+    ms = np.sort(lat) * 1e3
+    line = {
+        "metric": METRIC + " (serving)", "value": evals / elapsed, "unit": UNIT, "n_gpus": 1,
+        "steps": n, "warmup": 2, "ms_per_step": 1e3 * elapsed / max(n, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {len(scenes)} scenes ({len(admitted)} admitted under "
+                               f"{args.hbm_budget_gb:g} GB), Poisson {args.rate:g} requests/s for "
+                               f"{args.serve_seconds:g} s, one frame step (dt 1/60) per request",
+                   "max_inflight_ticks": args.inflight, "admission_s": t_adm,
+                   "device_bytes": info.device_bytes},
+        "p50_ms": float(ms[len(ms) // 2]), "p99_ms": float(ms[min(len(ms) - 1, int(0.99 * len(ms)))]),
+        "max_ms": float(ms[-1]), "requests": n, "requests_per_s": n / elapsed,
+        "ticks": int(info.ticks_launched), "evals": int(evals), "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    sv.close()
+    return 0
+
+
 # ---- ours ----------------------------------------------------------------------------
 def run_ours(args):
     import numpy as np
@@ -387,8 +476,12 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL))
+    ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL) + ["serving"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--inflight", type=int, default=3, help="serving: ticks outstanding")
+    ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
     ap.add_argument("--batched", action="store_true",
                     help="one synthesis launch over all patches of the frame (scwp_set_batched)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -397,7 +490,13 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
+        if args.workload == "serving":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no request server; "
+                                                                  "serving is measured on the GPU path only"}))
+            return 0
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

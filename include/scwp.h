@@ -138,6 +138,7 @@ typedef struct scwp_stats {
     double injected_energy[SCWP_MAX_BUCKETS]; /* sum 1/8 A^2 pi r^2 (Eq. 12 / rho g) */
     int64_t mma_stages;        /* operand stages (6 MMAs of 128x128x16 each) the last
                                   tensor-core synthesis committed; 0 for the other modes */
+    int64_t eval_total;        /* eval_count summed over every frame stepped */
 } scwp_stats;
 
 /* Scalar description of a patch's tables and bins. */
@@ -299,6 +300,79 @@ const char* scwp_version(void);
 
 /* Free every device and host resource of the context (NULL is a no-op). */
 void scwp_destroy(scwp_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Frame-step server: continuous batching of frame-step requests over many
+ * device-resident scenes.  The paper has no counterpart (it runs one scene).
+ *
+ * Each scene is a context of its own (its spectrum, background and patches)
+ * created by the server on the server's stream and allocator, in batched
+ * mode.  scwp_server_tick takes every scene that has a pending request and
+ * no frame in flight, enqueues each one's background and particle stages
+ * (on eight internal streams) and runs the tensor-core synthesis of all of
+ * them as ONE launch over the union of their planned (patch, tile, bucket
+ * group) items, heaviest first, followed by one group-sum blend launch.
+ * Per scene the arithmetic is that of a batched scwp_step, so each result
+ * is the same whether the scene runs alone or in a mix.  At most
+ * max_inflight ticks are outstanding; the next tick's particle stages
+ * overlap the current tick's synthesis.  Requests of one scene run in
+ * submission order, one frame per tick.
+ * ------------------------------------------------------------------------- */
+typedef struct scwp_server scwp_server;
+
+typedef struct scwp_server_desc {
+    void* stream;                /* cudaStream_t for the synthesis; NULL: legacy stream */
+    int64_t hbm_budget_bytes;    /* device memory the scenes may hold; 0: no limit */
+    int32_t max_inflight;        /* ticks outstanding at once, 1..16 */
+    void* (*alloc)(size_t bytes, void* user);   /* as in scwp_spectrum_desc */
+    void (*free)(void* ptr, void* user);
+    void* alloc_user;
+} scwp_server_desc;
+
+typedef struct scwp_server_info {
+    int32_t scenes;              /* admitted scenes                          */
+    int32_t frames_in_flight;    /* scenes with a frame in an unfinished tick */
+    int32_t ticks_in_flight;
+    int32_t pad;
+    int64_t pending_requests;    /* submitted, not yet in a tick             */
+    int64_t device_bytes;        /* device memory held by admitted scenes    */
+    int64_t budget_bytes;
+    int64_t ticks_launched;
+    int64_t requests_done;
+} scwp_server_info;
+
+/* SCWP_E_INVALID: bad descriptor; SCWP_E_CUDA: stream/event creation failed. */
+scwp_status scwp_server_create(const scwp_server_desc* desc, scwp_server** out);
+
+/* Admit a scene: creates its context (spec->stream and allocator are replaced
+ * by the server's) with n_patches patches and plans its batched synthesis.
+ * SCWP_E_NOMEM if its device memory would exceed the budget (the scene is
+ * released again); any error of scwp_create / scwp_add_patch otherwise. */
+scwp_status scwp_server_add_scene(scwp_server* sv, const scwp_spectrum_desc* spec, const scwp_patch_desc* patches,
+                                  int32_t n_patches, int32_t* scene_id);
+
+/* Release a scene and its device memory (SCWP_E_INVALID while it has a
+ * frame in flight). */
+scwp_status scwp_server_remove_scene(scwp_server* sv, int32_t scene_id);
+
+/* Queue one frame step of dt seconds of a scene under a caller-chosen id. */
+scwp_status scwp_server_submit(scwp_server* sv, int32_t scene_id, double dt, int64_t request_id);
+
+/* Start one tick if a tick slot is free and any scene is ready; *started =
+ * the number of requests it carries (0: nothing started). */
+scwp_status scwp_server_tick(scwp_server* sv, int32_t* started);
+
+/* Ids of completed requests, in completion order (at most max_ids; the rest
+ * are reported by the next call).  Never blocks. */
+scwp_status scwp_server_poll(scwp_server* sv, int64_t* done_ids, int32_t max_ids, int32_t* n_done);
+
+/* The context of a scene, for scwp_height_map / scwp_stats_get of its last
+ * completed frame (those calls run on the server stream). */
+scwp_status scwp_server_scene(scwp_server* sv, int32_t scene_id, scwp_ctx** ctx);
+
+scwp_status scwp_server_info_get(scwp_server* sv, scwp_server_info* out);
+const char* scwp_server_last_error(scwp_server* sv);
+void scwp_server_destroy(scwp_server* sv);
 
 #ifdef __cplusplus
 }

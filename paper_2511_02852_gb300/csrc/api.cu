@@ -9,6 +9,7 @@
 
 #include <atomic>
 #include <algorithm>
+#include <deque>
 #include <cmath>
 #include <functional>
 #include <queue>
@@ -52,6 +53,21 @@ struct PatchHost {
     BlendSpan* d_spans = nullptr;
     int partial_planes = 1;           // bucket-group partial planes allocated
     int tc_slots = 0;                 // resident CTA slots the plan assumed
+};
+
+// A frame (or a scene's part of a frame) captured as CUDA graphs, one per
+// parity of the particle double buffers, with the pinned staging buffers
+// and the device block through which each replay gets its parameters.
+struct FrameGraph {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    bool valid[2] = {false, false};
+    bool pending[2] = {false, false};
+    uint64_t mask[2] = {0, 0};
+    long long launches[2] = {0, 0};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    void* hstage[2] = {nullptr, nullptr};
+    unsigned char* dparams = nullptr;
+    size_t bytes = 0;
 };
 
 struct FrameEvents {
@@ -105,17 +121,14 @@ struct scwp_ctx {
     BlendSpan* d_bspans = nullptr;
     double b_makespan = 0.0;
     // captured batched frames (one per parity of the particle buffers)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    bool gvalid[2] = {false, false};
-    bool gpending[2] = {false, false};
-    uint64_t gmask[2] = {0, 0};
-    long long glaunches[2] = {0, 0};
-    cudaEvent_t gdone[2] = {nullptr, nullptr};
+    FrameGraph gfull;                 // whole batched frames (scwp_step)
+    FrameGraph gprep;                 // background + particle stages (the server's ticks)
     cudaStream_t gst = nullptr;       // capture origin (the caller's stream may be the legacy one)
-    void* hstage[2] = {nullptr, nullptr};
-    unsigned char* dparams = nullptr;
-    size_t params_bytes = 0;
     std::vector<InjectParams> ips;    // this frame's injection plans
+    size_t alloc_bytes = 0;           // device memory held by the context
+    std::vector<double> b_work;       // estimated stages of each batched item
+    std::vector<PatchDev> h_pdevs;    // host copies of the device descriptor arrays
+    std::vector<SynthParams> h_sps;
 };
 
 namespace {
@@ -145,7 +158,10 @@ void* dalloc(scwp_ctx* c, size_t bytes) {
         cudaGetLastError();
         p = nullptr;
     }
-    if (p) c->allocs.push_back(p);
+    if (p) {
+        c->allocs.push_back(p);
+        c->alloc_bytes += bytes;
+    }
     return p;
 }
 
@@ -378,7 +394,7 @@ void plan_patch(PatchHost& P, int slots) {
 // keeps its largest item under a quarter of the average per-slot load, and
 // all items of all patches run heaviest first.
 void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vector<BlendSpan>& spans,
-                  double& model_makespan) {
+                  double& model_makespan, std::vector<double>& item_work_out) {
     items.clear();
     spans.clear();
     std::vector<std::vector<double>> est(ctx->patches.size());
@@ -414,7 +430,11 @@ void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vec
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
     model_makespan = makespan(work, order, slots);
     std::vector<TcItem> sorted;
-    for (int k : order) sorted.push_back(items[k]);
+    item_work_out.clear();
+    for (int k : order) {
+        sorted.push_back(items[k]);
+        item_work_out.push_back(work[k]);
+    }
     items.swap(sorted);
 }
 
@@ -460,15 +480,20 @@ scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P, cudaStream_t st) {
 }
 
 // drop the captured frames (after a change that the captures baked in)
-void graph_reset(scwp_ctx* ctx) {
+void graph_reset(FrameGraph& G) {
     for (int k = 0; k < 2; ++k) {
-        if (ctx->gpending[k] && ctx->gdone[k]) cudaEventSynchronize(ctx->gdone[k]);
-        ctx->gpending[k] = false;
-        if (ctx->gexec[k]) cudaGraphExecDestroy(ctx->gexec[k]);
-        ctx->gexec[k] = nullptr;
-        ctx->gvalid[k] = false;
+        if (G.pending[k] && G.done[k]) cudaEventSynchronize(G.done[k]);
+        G.pending[k] = false;
+        if (G.exec[k]) cudaGraphExecDestroy(G.exec[k]);
+        G.exec[k] = nullptr;
+        G.valid[k] = false;
     }
     cudaGetLastError();
+}
+
+void graph_reset(scwp_ctx* ctx) {
+    graph_reset(ctx->gfull);
+    graph_reset(ctx->gprep);
 }
 
 // streams for the particle stages of up to kParticleStreams patches at once
@@ -495,8 +520,10 @@ scwp_status particle_streams(scwp_ctx* ctx) {
 scwp_status sync_synth(scwp_ctx* ctx) {
     if (!ctx->synth_dirty) return SCWP_OK;
     const size_t n = ctx->patches.size();
-    std::vector<PatchDev> pd(n);
-    std::vector<SynthParams> sp(n);
+    std::vector<PatchDev>& pd = ctx->h_pdevs;
+    std::vector<SynthParams>& sp = ctx->h_sps;
+    pd.resize(n);
+    sp.resize(n);
     for (size_t k = 0; k < n; ++k) {
         pd[k] = ctx->patches[k]->dev;
         sp[k] = synth_params(ctx, *ctx->patches[k]);
@@ -507,7 +534,7 @@ scwp_status sync_synth(scwp_ctx* ctx) {
     CU(cudaMemcpyAsync(ctx->d_pdevs, pd.data(), n * sizeof(PatchDev), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(ctx->d_sps, sp.data(), n * sizeof(SynthParams), cudaMemcpyHostToDevice, ctx->st));
     if (ctx->batched) {
-        plan_batched(ctx, ctx->slots, ctx->b_items, ctx->b_spans, ctx->b_makespan);
+        plan_batched(ctx, ctx->slots, ctx->b_items, ctx->b_spans, ctx->b_makespan, ctx->b_work);
         ctx->d_bitems = (TcItem*)dalloc(ctx, std::max<size_t>(1, ctx->b_items.size()) * sizeof(TcItem));
         ctx->d_bspans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, ctx->b_spans.size()) * sizeof(BlendSpan));
         if (!ctx->d_bitems || !ctx->d_bspans) return fail(ctx, SCWP_E_NOMEM, "batched plan");
@@ -589,8 +616,10 @@ scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->gdone[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->gdone[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->gfull.done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gfull.done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gprep.done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gprep.done[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return bail(SCWP_E_CUDA);
     }
@@ -707,7 +736,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
             ok = ok && D.partial;
         }
     }
-    D.stats = (unsigned long long*)dalloc(ctx, (4 + (size_t)T.nb) * sizeof(unsigned long long));
+    D.stats = (unsigned long long*)dalloc(ctx, (5 + (size_t)T.nb) * sizeof(unsigned long long));
     ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.hist &&
          D.offsets && D.rec && D.out && D.stats;
     if (!ok) {
@@ -764,7 +793,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         }
     CU(cudaMemcpyAsync(D.rot, rot.data(), rot.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
-    CU(cudaMemsetAsync(D.stats, 0, (4 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
+    CU(cudaMemsetAsync(D.stats, 0, (5 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));
     CU(cudaMemsetAsync(D.out, 0, (size_t)3 * T.W * T.H * sizeof(float), ctx->st));
     if (n0 > 0) {
@@ -953,42 +982,73 @@ static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>&
     return SCWP_OK;
 }
 
-// A batched frame as a CUDA graph: captured once for each parity of the
-// particle double buffers (every patch flips its live buffer each frame)
-// and replayed.  The frame's parameters (time, injection plans) reach the
-// graph through one copy from a pinned staging buffer per graph; a graph's
-// staging buffer is rewritten only after its previous replay completed.
-static scwp_status step_graph(scwp_ctx* ctx, const std::vector<InjectParams>& ips) {
+// Background and particle stages of every patch of a scene, all on the
+// context stream (the server's ticks).  ips / ip_dev / t_dev as in
+// enqueue_frame.
+static scwp_status enqueue_prepare(scwp_ctx* ctx, const std::vector<InjectParams>& ips, const InjectParams* ip_dev,
+                                   const double* t_dev) {
+    scwp_status s = SCWP_OK;
+    CU(launch_background(ctx->bg, ctx->t, ctx->st, t_dev));
+    ctx->bg_valid = true;
+    for (size_t k = 0; k < ctx->patches.size(); ++k) {
+        PatchHost* P = ctx->patches[k];
+        PatchDev& D = P->dev;
+        CU(launch_advect_flag(D, ctx->st));
+        CU(launch_compact(D, ctx->st));
+        D.cur ^= 1;
+        if (ip_dev)
+            CU(launch_inject_dev(D, ip_dev + k, ctx->st));
+        else if (ips[k].total > 0)
+            CU(launch_inject(D, ips[k], ctx->st));
+        if ((s = reset_frame_stats(ctx, *P, ctx->st)) != SCWP_OK) return s;
+        CU(launch_bin(D, ctx->st));
+    }
+    CU(cudaGetLastError());
+    return SCWP_OK;
+}
+
+// Replay (capturing first if needed) graph set G with this frame's
+// parameters on `launch`.  A graph is captured once for each parity of the
+// particle double buffers (every patch flips its live buffer each frame);
+// the frame's varying inputs (time, injection plans) reach it through one
+// copy from a pinned staging buffer per graph, rewritten only after that
+// graph's previous replay completed.  full: the whole frame (enqueue_frame);
+// otherwise the background and particle stages (enqueue_prepare).
+static scwp_status run_graph(scwp_ctx* ctx, FrameGraph& G, const std::vector<InjectParams>& ips,
+                             cudaStream_t launch, bool full) {
     scwp_status s = SCWP_OK;
     uint64_t mask = 0;
     for (size_t k = 0; k < ctx->patches.size(); ++k) mask |= (uint64_t)(ctx->patches[k]->dev.cur & 1) << k;
     int g = -1;
     for (int k = 0; k < 2; ++k)
-        if (ctx->gvalid[k] && ctx->gmask[k] == mask) g = k;
-    if (g < 0) g = !ctx->gvalid[0] ? 0 : 1;
+        if (G.valid[k] && G.mask[k] == mask) g = k;
+    if (g < 0) g = !G.valid[0] ? 0 : 1;
     const size_t bytes = 16 + ips.size() * sizeof(InjectParams);
-    if (!ctx->dparams || ctx->params_bytes < bytes) {
-        graph_reset(ctx);
-        ctx->dparams = (unsigned char*)dalloc(ctx, bytes);
-        if (!ctx->dparams) return fail(ctx, SCWP_E_NOMEM, "graph parameters");
+    if (!G.dparams || G.bytes < bytes) {
+        graph_reset(G);
+        G.dparams = (unsigned char*)dalloc(ctx, bytes);
+        if (!G.dparams) return fail(ctx, SCWP_E_NOMEM, "graph parameters");
         for (int k = 0; k < 2; ++k) {
-            if (cudaMallocHost(&ctx->hstage[k], bytes) != cudaSuccess) {
-                ctx->hstage[k] = nullptr;
+            if (G.hstage[k]) cudaFreeHost(G.hstage[k]);
+            if (cudaMallocHost(&G.hstage[k], bytes) != cudaSuccess) {
+                G.hstage[k] = nullptr;
                 cudaGetLastError();
                 return fail(ctx, SCWP_E_NOMEM, "graph staging");
             }
         }
-        ctx->params_bytes = bytes;
+        G.bytes = bytes;
         g = 0;
     }
-    if (ctx->gpending[g]) CU(cudaEventSynchronize(ctx->gdone[g]));
-    unsigned char* h = (unsigned char*)ctx->hstage[g];
+    if (G.pending[g]) CU(cudaEventSynchronize(G.done[g]));
+    unsigned char* h = (unsigned char*)G.hstage[g];
     memcpy(h, &ctx->t, sizeof(double));
     memcpy(h + 16, ips.data(), ips.size() * sizeof(InjectParams));
-    if (!ctx->gvalid[g]) {
+    if (!G.valid[g]) {
         // everything that synchronises or allocates happens before the capture
-        if ((s = sync_synth(ctx)) != SCWP_OK) return s;
-        if (ctx->patches.size() > 1 && (s = particle_streams(ctx)) != SCWP_OK) return s;
+        if (full) {
+            if ((s = sync_synth(ctx)) != SCWP_OK) return s;
+            if (ctx->patches.size() > 1 && (s = particle_streams(ctx)) != SCWP_OK) return s;
+        }
         if (!ctx->gst && cudaStreamCreateWithFlags(&ctx->gst, cudaStreamNonBlocking) != cudaSuccess) {
             ctx->gst = nullptr;
             return fail(ctx, SCWP_E_CUDA, "capture stream");
@@ -1001,10 +1061,11 @@ static scwp_status step_graph(scwp_ctx* ctx, const std::vector<InjectParams>& ip
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaSuccess;
         if (e == cudaSuccess) {
-            e = cudaMemcpyAsync(ctx->dparams, h, bytes, cudaMemcpyHostToDevice, ctx->st);
+            e = cudaMemcpyAsync(G.dparams, h, bytes, cudaMemcpyHostToDevice, ctx->st);
+            const InjectParams* ipd = reinterpret_cast<const InjectParams*>(G.dparams + 16);
+            const double* td = reinterpret_cast<const double*>(G.dparams);
             if (e == cudaSuccess)
-                s = enqueue_frame(ctx, ips, reinterpret_cast<const InjectParams*>(ctx->dparams + 16),
-                                  reinterpret_cast<const double*>(ctx->dparams), nullptr);
+                s = full ? enqueue_frame(ctx, ips, ipd, td, nullptr) : enqueue_prepare(ctx, ips, ipd, td);
             e2 = cudaStreamEndCapture(ctx->st, &graph);
         }
         ctx->st = caller;
@@ -1013,26 +1074,28 @@ static scwp_status step_graph(scwp_ctx* ctx, const std::vector<InjectParams>& ip
             cudaGetLastError();
             return s != SCWP_OK ? s : fail(ctx, SCWP_E_CUDA, "frame capture");
         }
-        e = cudaGraphInstantiate(&ctx->gexec[g], graph, 0);
+        e = cudaGraphInstantiate(&G.exec[g], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            ctx->gexec[g] = nullptr;
+            G.exec[g] = nullptr;
             return fail(ctx, SCWP_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
         }
-        ctx->gvalid[g] = true;
-        ctx->gmask[g] = mask;
-        ctx->glaunches[g] = launches_total() - before;
+        G.valid[g] = true;
+        G.mask[g] = mask;
+        G.launches[g] = launches_total() - before;
     } else {
         for (PatchHost* P : ctx->patches) P->dev.cur ^= 1;   // what the replay does on the device
-        count_launches((int)ctx->glaunches[g]);
+        count_launches((int)G.launches[g]);
     }
-    CU(cudaGraphLaunch(ctx->gexec[g], ctx->st));
-    CU(cudaEventRecord(ctx->gdone[g], ctx->st));
-    ctx->gpending[g] = true;
+    CU(cudaGraphLaunch(G.exec[g], launch));
+    CU(cudaEventRecord(G.done[g], launch));
+    G.pending[g] = true;
     return SCWP_OK;
 }
 
-static scwp_status step_impl(scwp_ctx* ctx, double dt) {
+// Host part of a frame: dt tables (on the context stream), frame counter
+// and time, the injection plans.
+static scwp_status frame_begin(scwp_ctx* ctx, double dt) {
     scwp_status s = SCWP_OK;
     if (!(dt > 0)) return fail(ctx, SCWP_E_INVALID, "dt must be > 0");
     if (dt != ctx->dt) {
@@ -1045,19 +1108,35 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
     }
     ctx->frame += 1;
     ctx->t += dt;
-    std::vector<InjectParams>& ips = ctx->ips;
-    ips.resize(ctx->patches.size());
-    for (size_t k = 0; k < ctx->patches.size(); ++k) frame_injection(ctx, ctx->patches[k], ips[k]);
+    ctx->ips.resize(ctx->patches.size());
+    for (size_t k = 0; k < ctx->patches.size(); ++k) frame_injection(ctx, ctx->patches[k], ctx->ips[k]);
+    return SCWP_OK;
+}
+
+// A scene's frame up to the synthesis on `stream` (the server's ticks), as a
+// replayed graph.
+static scwp_status scene_prepare(scwp_ctx* ctx, double dt, cudaStream_t stream) {
+    cudaStream_t caller = ctx->st;
+    ctx->st = stream;
+    scwp_status s = frame_begin(ctx, dt);
+    ctx->st = caller;
+    if (s != SCWP_OK) return s;
+    return run_graph(ctx, ctx->gprep, ctx->ips, stream, false);
+}
+
+static scwp_status step_impl(scwp_ctx* ctx, double dt) {
+    scwp_status s = frame_begin(ctx, dt);
+    if (s != SCWP_OK) return s;
     // batched frames replay a captured graph unless stage timing is on
     if (ctx->batched && !ctx->timing && ctx->synth_mode == SCWP_SYNTH_GATHER && ctx->patches.size() <= 64)
-        return step_graph(ctx, ips);
+        return run_graph(ctx, ctx->gfull, ctx->ips, ctx->st, true);
     FrameEvents* fe = nullptr;
     if (ctx->timing) {
         if (ctx->ring_n == kTimingRing && (s = drain_ring(ctx)) != SCWP_OK) return s;
         fe = &ctx->ring[ctx->ring_n++];
         if ((s = record(ctx, fe->e[0], ctx->st)) != SCWP_OK) return s;
     }
-    return enqueue_frame(ctx, ips, nullptr, nullptr, fe);
+    return enqueue_frame(ctx, ctx->ips, nullptr, nullptr, fe);
 }
 
 scwp_status scwp_launch_count(scwp_ctx* ctx, int64_t* n) {
@@ -1136,7 +1215,7 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
     if (s != SCWP_OK) return s;
     if (!out || patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
     PatchHost* P = ctx->patches[patch_id];
-    std::vector<unsigned long long> st(4 + P->T.nb);
+    std::vector<unsigned long long> st(5 + P->T.nb);
     int32_t cnt[2];
     CU(cudaMemcpyAsync(st.data(), P->dev.stats, st.size() * 8, cudaMemcpyDeviceToHost, ctx->st));
     CU(cudaMemcpyAsync(cnt, P->dev.count, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
@@ -1150,6 +1229,7 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
     out->error_flags = (int32_t)st[2];
     out->injected_total = P->injected;
     out->mma_stages = (int64_t)st[3 + P->T.nb];
+    out->eval_total = (int64_t)st[4 + P->T.nb];
     out->n_buckets = P->T.nb;
     for (int i = 0; i < P->T.nb; ++i) {
         out->live_per_bucket[i] = (int64_t)st[3 + i];
@@ -1351,10 +1431,11 @@ void scwp_destroy(scwp_ctx* ctx) {
     }
     for (cudaStream_t s : ctx->pst) cudaStreamSynchronize(s);
     graph_reset(ctx);
-    for (int k = 0; k < 2; ++k) {
-        if (ctx->hstage[k]) cudaFreeHost(ctx->hstage[k]);
-        if (ctx->gdone[k]) cudaEventDestroy(ctx->gdone[k]);
-    }
+    for (FrameGraph* G : {&ctx->gfull, &ctx->gprep})
+        for (int k = 0; k < 2; ++k) {
+            if (G->hstage[k]) cudaFreeHost(G->hstage[k]);
+            if (G->done[k]) cudaEventDestroy(G->done[k]);
+        }
     if (ctx->gst) cudaStreamDestroy(ctx->gst);
     cudaGetLastError();
     for (FrameEvents& f : ctx->ring)
@@ -1372,6 +1453,352 @@ void scwp_destroy(scwp_ctx* ctx) {
     if (ctx->side) cudaStreamDestroy(ctx->side);
     cudaGetLastError();
     delete ctx;
+}
+
+
+// =============================================================================
+// Frame-step server: continuous batching of frame-step requests over many
+// device-resident scenes (one context each).  A tick takes every idle scene
+// with a pending request, enqueues each one's background and particle stages
+// on one of eight streams, and runs the tensor-core synthesis of all of them
+// as one launch over the union of their batched-plan items (heaviest first)
+// on the server stream.  A scene has at most one frame in flight; at most
+// `max_inflight` ticks are outstanding, so the next tick's particle stages
+// overlap the current tick's synthesis.  Scenes are admitted while their
+// device memory fits the budget.
+// =============================================================================
+}  // extern "C"
+
+namespace {
+
+struct ServerScene {
+    scwp_ctx* ctx = nullptr;
+    std::deque<std::pair<int64_t, double>> pending;   // request id, dt
+    bool in_flight = false;
+};
+
+struct ServerTick {
+    cudaEvent_t done = nullptr;
+    int slot = 0;
+    std::vector<std::pair<int, int64_t>> reqs;        // scene, request id
+    size_t next = 0;                                  // first request not yet reported
+};
+
+}  // namespace
+
+struct scwp_server {
+    scwp_server_desc d{};
+    cudaStream_t st = nullptr;
+    std::vector<cudaStream_t> pst;
+    std::vector<cudaEvent_t> pev;
+    std::vector<ServerScene> scenes;
+    std::deque<ServerTick> ticks;
+    std::vector<cudaEvent_t> tick_events;             // one per staging slot
+    std::vector<void*> hstage, dstage;
+    std::vector<size_t> stage_cap;
+    std::vector<bool> slot_busy;
+    size_t used = 0;
+    int rr = 0;
+    int64_t ticks_launched = 0, requests_done = 0;
+    std::string err;
+};
+
+namespace {
+
+scwp_status sfail(scwp_server* sv, scwp_status s, const std::string& m) {
+    if (sv) sv->err = m;
+    return s;
+}
+
+#define SCU(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return sfail(sv, SCWP_E_CUDA, std::string(#call) + ": " +  \
+                                                             cudaGetErrorString(e_));     \
+    } while (0)
+
+void* sv_alloc(scwp_server* sv, size_t bytes) {
+    void* p = nullptr;
+    if (sv->d.alloc) return sv->d.alloc(bytes, sv->d.alloc_user);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void sv_free(scwp_server* sv, void* p) {
+    if (!p) return;
+    if (sv->d.free) sv->d.free(p, sv->d.alloc_user);
+    else cudaFree(p);
+}
+
+size_t align16(size_t n) { return (n + 15) & ~(size_t)15; }
+
+}  // namespace
+
+extern "C" {
+
+scwp_status scwp_server_create(const scwp_server_desc* desc, scwp_server** out) {
+    if (!desc || !out || desc->max_inflight < 1 || desc->max_inflight > 16) return SCWP_E_INVALID;
+    *out = nullptr;
+    scwp_server* sv = new (std::nothrow) scwp_server();
+    if (!sv) return SCWP_E_NOMEM;
+    sv->d = *desc;
+    sv->st = (cudaStream_t)desc->stream;
+    const int slots = desc->max_inflight;
+    sv->tick_events.assign(slots, nullptr);
+    sv->hstage.assign(slots, nullptr);
+    sv->dstage.assign(slots, nullptr);
+    sv->stage_cap.assign(slots, 0);
+    sv->slot_busy.assign(slots, false);
+    bool ok = true;
+    for (int k = 0; k < slots; ++k)
+        ok = ok && cudaEventCreateWithFlags(&sv->tick_events[k], cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kParticleStreams && ok; ++k) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (s) sv->pst.push_back(s);
+        if (e) sv->pev.push_back(e);
+    }
+    if (!ok) {
+        cudaGetLastError();
+        scwp_server_destroy(sv);
+        return SCWP_E_CUDA;
+    }
+    *out = sv;
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_add_scene(scwp_server* sv, const scwp_spectrum_desc* spec, const scwp_patch_desc* patches,
+                                  int32_t n_patches, int32_t* scene_id) {
+    if (!sv || !spec || !scene_id || n_patches < 1 || !patches) return SCWP_E_INVALID;
+    scwp_spectrum_desc d = *spec;
+    d.stream = sv->st;
+    d.alloc = sv->d.alloc;
+    d.free = sv->d.free;
+    d.alloc_user = sv->d.alloc_user;
+    scwp_ctx* ctx = nullptr;
+    scwp_status s = scwp_create(&d, &ctx);
+    if (s != SCWP_OK) return sfail(sv, s, "scene: scwp_create failed");
+    for (int32_t k = 0; k < n_patches && s == SCWP_OK; ++k) {
+        int32_t pid = 0;
+        s = scwp_add_patch(ctx, patches + k, &pid);
+    }
+    if (s == SCWP_OK) s = scwp_set_batched(ctx, 1);
+    if (s == SCWP_OK) s = sync_synth(ctx);
+    if (s != SCWP_OK) {
+        sv->err = std::string("scene: ") + scwp_last_error(ctx);
+        scwp_destroy(ctx);
+        return s;
+    }
+    if (sv->d.hbm_budget_bytes > 0 && sv->used + ctx->alloc_bytes > (size_t)sv->d.hbm_budget_bytes) {
+        scwp_destroy(ctx);
+        return sfail(sv, SCWP_E_NOMEM, "scene refused: device memory budget");
+    }
+    sv->used += ctx->alloc_bytes;
+    int id = -1;
+    for (size_t k = 0; k < sv->scenes.size() && id < 0; ++k)
+        if (!sv->scenes[k].ctx) id = (int)k;
+    if (id < 0) {
+        id = (int)sv->scenes.size();
+        sv->scenes.emplace_back();
+    }
+    sv->scenes[id].ctx = ctx;
+    sv->scenes[id].pending.clear();
+    sv->scenes[id].in_flight = false;
+    *scene_id = id;
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_remove_scene(scwp_server* sv, int32_t scene_id) {
+    if (!sv || scene_id < 0 || scene_id >= (int)sv->scenes.size() || !sv->scenes[scene_id].ctx)
+        return SCWP_E_INVALID;
+    ServerScene& sc = sv->scenes[scene_id];
+    if (sc.in_flight) return sfail(sv, SCWP_E_INVALID, "scene has a frame in flight");
+    sv->used -= sc.ctx->alloc_bytes;
+    scwp_destroy(sc.ctx);
+    sc.ctx = nullptr;
+    sc.pending.clear();
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_submit(scwp_server* sv, int32_t scene_id, double dt, int64_t request_id) {
+    if (!sv || scene_id < 0 || scene_id >= (int)sv->scenes.size() || !sv->scenes[scene_id].ctx || !(dt > 0))
+        return SCWP_E_INVALID;
+    sv->scenes[scene_id].pending.emplace_back(request_id, dt);
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_tick(scwp_server* sv, int32_t* started) {
+    if (!sv || !started) return SCWP_E_INVALID;
+    *started = 0;
+    int slot = -1;
+    for (size_t k = 0; k < sv->slot_busy.size() && slot < 0; ++k)
+        if (!sv->slot_busy[k]) slot = (int)k;
+    if (slot < 0) return SCWP_OK;   // every tick slot is in flight
+    const int ns = (int)sv->scenes.size();
+    std::vector<int> take;
+    for (int k = 0; k < ns; ++k) {
+        const int i = (sv->rr + k) % ns;
+        const ServerScene& sc = sv->scenes[i];
+        if (sc.ctx && !sc.in_flight && !sc.pending.empty()) take.push_back(i);
+    }
+    if (take.empty()) return SCWP_OK;
+    sv->rr = (sv->rr + 1) % ns;
+    ServerTick tk;
+    tk.slot = slot;
+    tk.done = sv->tick_events[slot];
+    // background and particle stages, one scene per stream in turn
+    std::vector<bool> used(sv->pst.size(), false);
+    for (size_t k = 0; k < take.size(); ++k) {
+        ServerScene& sc = sv->scenes[take[k]];
+        const size_t q = k % sv->pst.size();
+        const std::pair<int64_t, double> rq = sc.pending.front();
+        const scwp_status s = scene_prepare(sc.ctx, rq.second, sv->pst[q]);
+        if (s != SCWP_OK) return sfail(sv, s, std::string("scene prepare: ") + sc.ctx->err);
+        used[q] = true;
+        sc.pending.pop_front();
+        sc.in_flight = true;
+        tk.reqs.emplace_back(take[k], rq.first);
+    }
+    for (size_t q = 0; q < sv->pst.size(); ++q)
+        if (used[q]) {
+            SCU(cudaEventRecord(sv->pev[q], sv->pst[q]));
+            SCU(cudaStreamWaitEvent(sv->st, sv->pev[q], 0));
+        }
+    // the union of the scenes' synthesis plans, heaviest first
+    std::vector<PatchDev> pd;
+    std::vector<SynthParams> sp;
+    std::vector<TcItem> items;
+    std::vector<double> work;
+    std::vector<BlendSpan> spans;
+    for (int i : take) {
+        scwp_ctx* c = sv->scenes[i].ctx;
+        const int base = (int)pd.size();
+        for (size_t p = 0; p < c->patches.size(); ++p) {
+            pd.push_back(c->patches[p]->dev);
+            sp.push_back(c->h_sps[p]);
+        }
+        for (size_t k = 0; k < c->b_items.size(); ++k) {
+            TcItem it = c->b_items[k];
+            it.patch += base;
+            items.push_back(it);
+            work.push_back(c->b_work[k]);
+        }
+        for (BlendSpan b : c->b_spans) {
+            b.patch += base;
+            spans.push_back(b);
+        }
+    }
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    const size_t o_sp = align16(pd.size() * sizeof(PatchDev));
+    const size_t o_it = o_sp + align16(sp.size() * sizeof(SynthParams));
+    const size_t o_bs = o_it + align16(items.size() * sizeof(TcItem));
+    const size_t bytes = o_bs + align16(std::max<size_t>(1, spans.size()) * sizeof(BlendSpan));
+    if (sv->stage_cap[slot] < bytes) {
+        if (sv->hstage[slot]) cudaFreeHost(sv->hstage[slot]);
+        sv_free(sv, sv->dstage[slot]);
+        sv->hstage[slot] = nullptr;
+        sv->dstage[slot] = nullptr;
+        sv->stage_cap[slot] = 0;
+        const size_t cap = bytes * 2;
+        if (cudaMallocHost(&sv->hstage[slot], cap) != cudaSuccess) {
+            sv->hstage[slot] = nullptr;
+            cudaGetLastError();
+            return sfail(sv, SCWP_E_NOMEM, "tick staging");
+        }
+        sv->dstage[slot] = sv_alloc(sv, cap);
+        if (!sv->dstage[slot]) return sfail(sv, SCWP_E_NOMEM, "tick staging");
+        sv->stage_cap[slot] = cap;
+    }
+    unsigned char* h = (unsigned char*)sv->hstage[slot];
+    memcpy(h, pd.data(), pd.size() * sizeof(PatchDev));
+    memcpy(h + o_sp, sp.data(), sp.size() * sizeof(SynthParams));
+    TcItem* hi = reinterpret_cast<TcItem*>(h + o_it);
+    for (size_t k = 0; k < order.size(); ++k) hi[k] = items[order[k]];
+    if (!spans.empty()) memcpy(h + o_bs, spans.data(), spans.size() * sizeof(BlendSpan));
+    unsigned char* dv = (unsigned char*)sv->dstage[slot];
+    SCU(cudaMemcpyAsync(dv, h, bytes, cudaMemcpyHostToDevice, sv->st));
+    SCU(launch_synth_tc(reinterpret_cast<const TcItem*>(dv + o_it), (int)items.size(),
+                        reinterpret_cast<const PatchDev*>(dv), reinterpret_cast<const SynthParams*>(dv + o_sp),
+                        reinterpret_cast<const BlendSpan*>(dv + o_bs), (int)spans.size(), sv->st));
+    SCU(cudaEventRecord(tk.done, sv->st));
+    sv->slot_busy[slot] = true;
+    *started = (int32_t)tk.reqs.size();
+    sv->ticks.push_back(std::move(tk));
+    sv->ticks_launched += 1;
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_poll(scwp_server* sv, int64_t* done_ids, int32_t max_ids, int32_t* n_done) {
+    if (!sv || !n_done || max_ids < 0 || (max_ids > 0 && !done_ids)) return SCWP_E_INVALID;
+    *n_done = 0;
+    while (!sv->ticks.empty()) {
+        ServerTick& tk = sv->ticks.front();
+        const cudaError_t q = cudaEventQuery(tk.done);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) return sfail(sv, SCWP_E_CUDA, std::string("tick: ") + cudaGetErrorString(q));
+        while (tk.next < tk.reqs.size() && *n_done < max_ids) {
+            const std::pair<int, int64_t>& r = tk.reqs[tk.next++];
+            sv->scenes[r.first].in_flight = false;
+            done_ids[(*n_done)++] = r.second;
+        }
+        if (tk.next < tk.reqs.size()) break;   // the caller's array is full
+        sv->slot_busy[tk.slot] = false;
+        sv->requests_done += (int64_t)tk.reqs.size();
+        sv->ticks.pop_front();
+    }
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_scene(scwp_server* sv, int32_t scene_id, scwp_ctx** ctx) {
+    if (!sv || !ctx || scene_id < 0 || scene_id >= (int)sv->scenes.size() || !sv->scenes[scene_id].ctx)
+        return SCWP_E_INVALID;
+    *ctx = sv->scenes[scene_id].ctx;
+    return SCWP_OK;
+}
+
+scwp_status scwp_server_info_get(scwp_server* sv, scwp_server_info* out) {
+    if (!sv || !out) return SCWP_E_INVALID;
+    memset(out, 0, sizeof(*out));
+    for (const ServerScene& sc : sv->scenes)
+        if (sc.ctx) {
+            out->scenes += 1;
+            out->pending_requests += (int64_t)sc.pending.size();
+            out->frames_in_flight += sc.in_flight ? 1 : 0;
+        }
+    out->device_bytes = (int64_t)sv->used;
+    out->budget_bytes = (int64_t)sv->d.hbm_budget_bytes;
+    out->ticks_in_flight = (int32_t)sv->ticks.size();
+    out->ticks_launched = sv->ticks_launched;
+    out->requests_done = sv->requests_done;
+    return SCWP_OK;
+}
+
+const char* scwp_server_last_error(scwp_server* sv) { return sv ? sv->err.c_str() : "null server"; }
+
+void scwp_server_destroy(scwp_server* sv) {
+    if (!sv) return;
+    if (sv->st) cudaStreamSynchronize(sv->st);
+    for (cudaStream_t s : sv->pst) cudaStreamSynchronize(s);
+    cudaGetLastError();
+    for (ServerScene& sc : sv->scenes)
+        if (sc.ctx) scwp_destroy(sc.ctx);
+    for (size_t k = 0; k < sv->hstage.size(); ++k) {
+        if (sv->hstage[k]) cudaFreeHost(sv->hstage[k]);
+        sv_free(sv, sv->dstage[k]);
+    }
+    for (cudaEvent_t e : sv->tick_events)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : sv->pst) cudaStreamDestroy(s);
+    for (cudaEvent_t e : sv->pev) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete sv;
 }
 
 }  // extern "C"

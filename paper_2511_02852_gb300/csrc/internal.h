@@ -66,7 +66,8 @@ struct PatchDev {
     int groups_tc = 1;                    // bucket groups of the tensor-core synthesis
     int patch = 0;                        // index of the patch in its context
     unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..3+nb) live per bucket,
-                                          // [3+nb] operand stages of the last tensor-core synthesis
+                                          // [3+nb] operand stages of the last tensor-core synthesis,
+                                          // [4+nb] evals summed over all frames
     float* layers = nullptr;              // layered variant scratch (lazy)
     size_t layers_bytes = 0;
 };

@@ -296,7 +296,10 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
             e += s_ev[w];
             bb += s_bin[w];
         }
-        if (e) atomicAdd(&p.stats[0], e);
+        if (e) {
+            atomicAdd(&p.stats[0], e);
+            atomicAdd(&p.stats[4 + p.nb], e);   // running total over frames
+        }
         if (bb) atomicAdd(&p.stats[1], bb);
     }
     for (int i = threadIdx.x; i < p.nb; i += blockDim.x)

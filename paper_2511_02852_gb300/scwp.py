@@ -60,7 +60,8 @@ class scwp_stats(C.Structure):
                 ("bumps_binned", C.c_int64), ("eval_count", C.c_int64),
                 ("injected_total", C.c_int64), ("n_buckets", C.c_int32),
                 ("error_flags", C.c_int32), ("live_per_bucket", C.c_int64 * MAX_BUCKETS),
-                ("injected_energy", C.c_double * MAX_BUCKETS), ("mma_stages", C.c_int64)]
+                ("injected_energy", C.c_double * MAX_BUCKETS), ("mma_stages", C.c_int64),
+                ("eval_total", C.c_int64)]
 
 
 class scwp_patch_info(C.Structure):
@@ -70,6 +71,17 @@ class scwp_patch_info(C.Structure):
                 ("bin_cells", C.c_int32 * MAX_BUCKETS), ("nbx", C.c_int32 * MAX_BUCKETS),
                 ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS),
                 ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32)]
+
+
+class scwp_server_desc(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("hbm_budget_bytes", C.c_int64), ("max_inflight", C.c_int32),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class scwp_server_info(C.Structure):
+    _fields_ = [("scenes", C.c_int32), ("frames_in_flight", C.c_int32), ("ticks_in_flight", C.c_int32),
+                ("pad", C.c_int32), ("pending_requests", C.c_int64), ("device_bytes", C.c_int64),
+                ("budget_bytes", C.c_int64), ("ticks_launched", C.c_int64), ("requests_done", C.c_int64)]
 
 
 EXPORTS = {
@@ -100,6 +112,17 @@ EXPORTS = {
     "scwp_last_error": (C.c_char_p, [C.c_void_p]),
     "scwp_version": (C.c_char_p, []),
     "scwp_destroy": (None, [C.c_void_p]),
+    "scwp_server_create": (C.c_int, [C.POINTER(scwp_server_desc), C.POINTER(C.c_void_p)]),
+    "scwp_server_add_scene": (C.c_int, [C.c_void_p, C.POINTER(scwp_spectrum_desc), C.c_void_p, C.c_int32,
+                                        C.POINTER(C.c_int32)]),
+    "scwp_server_remove_scene": (C.c_int, [C.c_void_p, C.c_int32]),
+    "scwp_server_submit": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int64]),
+    "scwp_server_tick": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "scwp_server_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "scwp_server_scene": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "scwp_server_info_get": (C.c_int, [C.c_void_p, C.POINTER(scwp_server_info)]),
+    "scwp_server_last_error": (C.c_char_p, [C.c_void_p]),
+    "scwp_server_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -369,3 +392,112 @@ class Scene:
         fr = C.c_int64()
         _check(lib().scwp_timing_read(self.ctx, ms, C.byref(fr)), self.ctx)
         return list(ms), fr.value
+
+
+class _ServerSceneView(Scene):
+    """A server scene's context, read like a Scene (maps, stats, info);
+    the server owns and releases it."""
+
+    def __init__(self, ctx, cfg, device):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.device = device
+        self.ctx = ctx
+        self.N = int(cfg["spectrum"]["fft_n"])
+
+    def close(self):
+        self.ctx = None
+
+
+class Server:
+    """The frame-step server of the C ABI (scwp_server_*): scenes admitted
+    against a device-memory budget, requests batched into ticks."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=3, device=0, stream=None, use_torch_alloc=True):
+        import torch
+        self.device = device
+        torch.cuda.set_device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self._alloc = self._free = None
+        if use_torch_alloc:
+            st = self.stream
+
+            def _a(nbytes, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, st))
+                except Exception:
+                    return None
+
+            def _f(ptr, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc = ALLOC_FN(_a)
+            self._free = FREE_FN(_f)
+        d = scwp_server_desc()
+        d.stream = C.c_void_p(self.stream.cuda_stream)
+        d.hbm_budget_bytes = int(hbm_budget_bytes)
+        d.max_inflight = int(max_inflight)
+        if self._alloc is not None:
+            d.alloc = self._alloc
+            d.free = self._free
+        self.sv = C.c_void_p()
+        self._check(lib().scwp_server_create(C.byref(d), C.byref(self.sv)))
+        self.cfgs = {}
+        self._ids = (C.c_int64 * 65536)()
+
+    def _check(self, status):
+        if status != 0:
+            msg = lib().scwp_server_last_error(self.sv).decode() if getattr(self, "sv", None) else ""
+            raise ScwpError(status, msg)
+
+    def close(self):
+        if getattr(self, "sv", None):
+            lib().scwp_server_destroy(self.sv)
+            self.sv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_scene(self, cfg):
+        """Admit a scene; its id, or None when the memory budget refuses it."""
+        sd = spectrum_desc(cfg["spectrum"])
+        arr = (scwp_patch_desc * len(cfg["patches"]))(*[patch_desc(p) for p in cfg["patches"]])
+        sid = C.c_int32()
+        rc = lib().scwp_server_add_scene(self.sv, C.byref(sd), C.cast(arr, C.c_void_p), len(cfg["patches"]),
+                                         C.byref(sid))
+        if rc == 2:
+            return None
+        self._check(rc)
+        self.cfgs[sid.value] = cfg
+        return sid.value
+
+    def remove_scene(self, sid):
+        self._check(lib().scwp_server_remove_scene(self.sv, int(sid)))
+        self.cfgs.pop(int(sid), None)
+
+    def submit(self, sid, dt, request_id):
+        self._check(lib().scwp_server_submit(self.sv, int(sid), float(dt), int(request_id)))
+
+    def tick(self):
+        n = C.c_int32()
+        self._check(lib().scwp_server_tick(self.sv, C.byref(n)))
+        return n.value
+
+    def poll(self):
+        n = C.c_int32()
+        self._check(lib().scwp_server_poll(self.sv, C.cast(self._ids, C.c_void_p), len(self._ids), C.byref(n)))
+        return [self._ids[k] for k in range(n.value)]
+
+    def scene(self, sid):
+        c = C.c_void_p()
+        self._check(lib().scwp_server_scene(self.sv, int(sid), C.byref(c)))
+        return _ServerSceneView(c, self.cfgs[int(sid)], self.device)
+
+    def info(self):
+        out = scwp_server_info()
+        self._check(lib().scwp_server_info_get(self.sv, C.byref(out)))
+        return out

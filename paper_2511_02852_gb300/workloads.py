@@ -171,6 +171,54 @@ def batched(n_patches=32, total_particles=4_000_000, seed=1):
     return scene("batched", spec, ps, frames=300)
 
 
+# -- serving: 64 independent scenes: FFT 256^2..1024^2 (log-uniform powers
+#    of two), JONSWAP U10 uniform in 5..20 m/s at a 100 km fetch, 1..16
+#    patches with sides log-uniform in 64..512 cells, 1e4..1e6 particles per
+#    scene (log-uniform, split over the patches by area), 8..16 buckets.
+#    Unstated by the scene list and chosen here: the cell is 1/48 of the
+#    peak wavelength (so kernel radii in cells stay alike across winds) and
+#    the FFT domain is N/32 peak wavelengths.  Scenes from seed 3.
+G = 9.81
+
+
+def serving(n_scenes=64, seed=3):
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_scenes):
+        U = float(rng.uniform(5.0, 20.0))
+        N = int(2 ** int(round(rng.uniform(8.0, 10.0))))
+        wp = 22.0 * (G * G / (U * 100e3)) ** (1.0 / 3.0)
+        lam_p = 2.0 * math.pi * G / (wp * wp)
+        cell = lam_p / 48.0
+        L = N * lam_p / 32.0
+        n_p = int(rng.integers(1, 17))
+        total = float(np.exp(rng.uniform(math.log(1e4), math.log(1e6))))
+        sides = np.clip(np.round(np.exp(rng.uniform(math.log(64), math.log(512), size=(n_p, 2)))), 64, 512)
+        area = sides[:, 0] * sides[:, 1]
+        nb = int(rng.integers(8, 17))
+        spec = spectrum(spectrum=JONSWAP, wind_speed=U, fetch=100e3, gamma=3.3, depth=0.0,
+                        n_buckets=nb, n_theta=16, fft_n=N, fft_L=L, seed=1000 + s)
+        ps = []
+        for k in range(n_p):
+            cnt = max(1, int(round(total * area[k] / area.sum())))
+            ps.append(patch(origin_x=float(rng.uniform(-0.25 * L, 0.25 * L)),
+                            origin_y=float(rng.uniform(-0.25 * L, 0.25 * L)),
+                            cell=cell, width=int(sides[k, 0]), height=int(sides[k, 1]),
+                            max_particles=int(2 * cnt + 4096), prefill=cnt, inject_scale=1.0,
+                            emitter=0))
+        out.append(scene(f"serving{s}", spec, ps, frames=1))
+    return out
+
+
+def serving_arrivals(rate=2000.0, seconds=60.0, n_scenes=64, seed=4):
+    """Poisson frame-step requests: (arrival time in s, scene index)."""
+    rng = np.random.default_rng(seed)
+    n = int(rate * seconds * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    t = t[t < seconds]
+    return t, rng.integers(0, n_scenes, len(t))
+
+
 def scaled(sc, **patch_overrides):
     """A copy of a scene with every patch's fields overridden."""
     out = copy.deepcopy(sc)
