@@ -359,7 +359,7 @@ std::vector<BlendSpan> blend_spans(const PatchHost& P, int G) {
     std::vector<BlendSpan> out;
     if (G <= 1) return out;
     const int nq = ((P.T.W + 3) / 4) * P.T.H;
-    constexpr int kQuadsPerSpan = 2048;
+    constexpr int kQuadsPerSpan = 256;   // one quad per thread of a 256-thread CTA
     for (int q0 = 0; q0 < nq; q0 += kQuadsPerSpan) out.push_back(BlendSpan{P.index, q0, std::min(nq, q0 + kQuadsPerSpan), G});
     return out;
 }

@@ -294,6 +294,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = S.tmem;
+    // descriptor fields used inside the loops, read once from shared memory
+    unsigned long long* const err = p.stats + 2;
+    const float row_scale = sp.row_scale;
 
     if (warp == kMmaWarp) {
         // ======================= MMA issuer ==================================
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             int k = 0;   // stages consumed
             for (;; ++k) {
                 const int fs = k % kStages;
-                if (!bar_wait(&S.full[fs], (k / kStages) & 1u, p.stats + 2)) break;
+                if (!bar_wait(&S.full[fs], (k / kStages) & 1u, err)) break;
                 if (S.stage_n[fs] < 0) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const TcStage& T = S.st[fs];
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             const int slot = gc % kRecSlots;
             bool got = true;
             if (gc >= kRecSlots && lane == 0)
-                got = bar_wait(&S.rfree[slot], (uint32_t)((gc / kRecSlots - 1) & 1), p.stats + 2);
+                got = bar_wait(&S.rfree[slot], (uint32_t)((gc / kRecSlots - 1) & 1), err);
             ok = ok && __shfl_sync(0xffffffffu, (int)got, 0) != 0;
             return slot;
         };
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
         // still be in flight)
         if (lane == 0)
             for (int g2 = max(0, gc - kRecSlots); g2 < gc; ++g2)
-                bar_wait(&S.rbar[g2 % kRecSlots], (uint32_t)((g2 / kRecSlots) & 1), p.stats + 2);
+                bar_wait(&S.rbar[g2 % kRecSlots], (uint32_t)((g2 / kRecSlots) & 1), err);
         __syncwarp();
     } else {
         // ======================= producers ===================================
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
         int32_t R = 0;         // radius of the current bucket
         float st[2] = {0.f, 0.f}, ct[2] = {1.f, 1.f};
         for (;;) {
-            bool ok = bar_wait(&S.rbar[rs], rpar, p.stats + 2);
+            bool ok = bar_wait(&S.rbar[rs], rpar, err);
             if (__any_sync(0xffffffffu, !ok)) break;   // this warp stops; the others time out in turn
             const ChunkMeta m = S.meta[rs];
             if (m.n < 0) break;
@@ -461,14 +464,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                     sincospif((float)((double)pm / (double)R), &st[e], &ct[e]);
                 }
             }
-            ok = bar_wait(&S.empty[fs], fpar, p.stats + 2);
+            ok = bar_wait(&S.empty[fs], fpar, err);
             if (__any_sync(0xffffffffu, !ok)) break;
             TcStage& T = S.st[fs];
             // this thread's half of each record: {x, cx, sx, id} or {y, cy, sy, amp};
             // slots past n hold sentinel records outside every support
             const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
             if (is_row)
-                gen_quarter<true>(T.Bhi, T.Blo, rc, kq, idx, pos, R, ct, st, sp.row_scale);
+                gen_quarter<true>(T.Bhi, T.Blo, rc, kq, idx, pos, R, ct, st, row_scale);
             else
                 gen_quarter<false>(T.Ahi, T.Alo, rc, kq, idx, pos, R, ct, st, 1.f);
             if (tid == 0) S.stage_n[fs] = m.n;
@@ -492,13 +495,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
         }
         // end of the stream for the MMA thread
         {
-            bar_wait(&S.empty[fs], fpar, p.stats + 2);
+            bar_wait(&S.empty[fs], fpar, err);
             if (tid == 0) S.stage_n[fs] = -1;
             __syncwarp();
             if (lane == 0) bar_arrive(&S.full[fs]);
         }
         // ======================= epilogue ====================================
-        bar_wait(&S.done, 0u, p.stats + 2);
+        bar_wait(&S.done, 0u, err);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool any = produced > 0;   // otherwise no MMA ever wrote the accumulator
         // warp w reads TMEM lane quarter w & 3 (accumulator rows); the two
@@ -521,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                 for (int j = 0; j < 32; ++j) r[j] = c[j] = 0u;
             }
             const int f = cb < kTY / 32 ? (lowm ? 0 : 1) : 2;
-            const float scale = (f == 0 ? 0.25f : 0.5f * sp.lam_half) / sp.row_scale;
+            const float scale = (f == 0 ? 0.25f : 0.5f * sp.lam_half) / row_scale;
             const int y0 = ty0 + 32 * (cb & (kTY / 32 - 1));
             if (x >= sp.W) continue;
 #pragma unroll
