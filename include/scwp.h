@@ -55,10 +55,17 @@ enum { SCWP_SPECTRUM_JONSWAP = 0, SCWP_SPECTRUM_PHILLIPS = 1 };
 enum { SCWP_SPREAD_COS2S_MITSUYASU = 0, SCWP_SPREAD_COS2 = 1 };
 enum { SCWP_AMP_NORMALIZED = 0, SCWP_AMP_LITERAL = 1 };
 enum { SCWP_FIELD_H = 0, SCWP_FIELD_DX = 1, SCWP_FIELD_DY = 2 };
-/* synthesis of the patch maps: the tile gather on the tensor cores (default;
- * tcgen05 TF32 MMAs with a hi/lo split, FP32-accurate), the same gather on
- * the FP32 CUDA cores, or the paper's layered-texture formulation */
-enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1, SCWP_SYNTH_GATHER_FP32 = 2 };
+/* Synthesis modes (Sec. 4.2):
+ *   SCWP_SYNTH_GATHER       tile gather on the tensor cores (default): tcgen05
+ *                           FP16 MMAs with a hi/lo operand split, FP32
+ *                           accumulation; the FP32 contract (1e-4 Hs);
+ *   SCWP_SYNTH_LAYERED      the paper's layered-texture formulation;
+ *   SCWP_SYNTH_GATHER_FP32  the same gather on the FP32 CUDA cores;
+ *   SCWP_SYNTH_GATHER_FP16  the tensor-core gather with single FP16 operands
+ *                           (one MMA per step instead of three), FP32
+ *                           accumulation; the reduced-precision contract
+ *                           (2e-3 Hs); positions and bins stay exact. */
+enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1, SCWP_SYNTH_GATHER_FP32 = 2, SCWP_SYNTH_GATHER_FP16 = 3 };
 
 #define SCWP_MAX_BUCKETS 64
 #define SCWP_MAX_THETA 256
@@ -238,6 +245,13 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode);
 
 /* Select the synthesis used by scwp_step (SCWP_SYNTH_*). */
 scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode);
+
+/* Diagnostic: the tensor-core synthesis modes sum only the buckets
+ * b_lo <= i < b_hi (clamped to each patch's count; default all), so that
+ * the error against the FP64 oracle can be stated per bucket.  The paper has
+ * no counterpart.  SCWP_E_INVALID if b_lo < 0 or b_hi <= b_lo.  The other
+ * synthesis modes ignore the range. */
+scwp_status scwp_set_bucket_range(scwp_ctx* ctx, int32_t b_lo, int32_t b_hi);
 
 /* Batched frame step (on != 0): the tensor-core synthesis of all patches of
  * the context runs as one launch over the (patch, tile, bucket group) items

@@ -50,10 +50,15 @@ class OracleScene:
         bm = ps.bumps()
         return synth_maps(ps.T.W, ps.T.H, bm, self.lam)
 
-    def patch_maps(self, p, bg=None, layered=False):
-        """Blended (h, Dx, Dy) of patch p and its eval count."""
+    def patch_maps(self, p, bg=None, layered=False, buckets=None):
+        """Blended (h, Dx, Dy) of patch p and its eval count.  buckets =
+        (lo, hi): only the bumps of buckets lo <= i < hi enter the WP sum (a
+        selection for per-bucket error statements; the sums are unchanged)."""
         ps = self.patches[p]
         bm = ps.bumps()
+        if buckets is not None:
+            sel = (bm["B"] >= buckets[0]) & (bm["B"] < buckets[1])
+            bm = {k: (v[sel] if isinstance(v, np.ndarray) and len(v) == len(sel) else v) for k, v in bm.items()}
         if layered:
             wp = layered_maps(ps.T.W, ps.T.H, bm, self.lam, ps.T.nb, ps.T.R)
             ev = int(bm["ec"].sum())

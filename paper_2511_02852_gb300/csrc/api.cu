@@ -112,6 +112,7 @@ struct scwp_ctx {
     // and the batched plan (all patches in one launch)
     bool batched = false;
     bool synth_dirty = true;
+    int b_lo = 0, b_hi = 1 << 30;     // buckets synthesised by the tensor-core modes
     int slots = 0;
     PatchDev* d_pdevs = nullptr;
     SynthParams* d_sps = nullptr;
@@ -470,6 +471,8 @@ SynthParams synth_params(scwp_ctx* ctx, const PatchHost& P) {
         e = std::min(std::max(13 - e, -60), 60);
     }
     sp.row_scale = (float)std::ldexp(1.0, e);
+    sp.b_lo = std::max(0, ctx->b_lo);
+    sp.b_hi = std::min(P.T.nb, ctx->b_hi);
     return sp;
 }
 
@@ -551,12 +554,13 @@ scwp_status sync_synth(scwp_ctx* ctx) {
 }
 
 scwp_status synthesize(scwp_ctx* ctx, int mode) {
-    if (mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32) {
+    const bool split = mode != SCWP_SYNTH_GATHER_FP16;
+    if (mode == SCWP_SYNTH_GATHER || mode == SCWP_SYNTH_GATHER_FP16) {
         scwp_status s = sync_synth(ctx);
         if (s != SCWP_OK) return s;
         if (ctx->batched) {
             CU(launch_synth_tc(ctx->d_bitems, (int)ctx->b_items.size(), ctx->d_pdevs, ctx->d_sps, ctx->d_bspans,
-                               (int)ctx->b_spans.size(), ctx->st));
+                               (int)ctx->b_spans.size(), ctx->st, split));
             return SCWP_OK;
         }
     }
@@ -581,7 +585,7 @@ scwp_status synthesize(scwp_ctx* ctx, int mode) {
             CU(launch_synth_gather(P->dev, sp, ctx->st));
         } else {
             CU(launch_synth_tc(P->d_items, (int)P->tc_items.size(), ctx->d_pdevs, ctx->d_sps, P->d_spans,
-                               (int)P->tc_spans.size(), ctx->st));
+                               (int)P->tc_spans.size(), ctx->st, split));
         }
     }
     return SCWP_OK;
@@ -1128,7 +1132,8 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
     scwp_status s = frame_begin(ctx, dt);
     if (s != SCWP_OK) return s;
     // batched frames replay a captured graph unless stage timing is on
-    if (ctx->batched && !ctx->timing && ctx->synth_mode == SCWP_SYNTH_GATHER && ctx->patches.size() <= 64)
+    if (ctx->batched && !ctx->timing && ctx->patches.size() <= 64 &&
+        (ctx->synth_mode == SCWP_SYNTH_GATHER || ctx->synth_mode == SCWP_SYNTH_GATHER_FP16))
         return run_graph(ctx, ctx->gfull, ctx->ips, ctx->st, true);
     FrameEvents* fe = nullptr;
     if (ctx->timing) {
@@ -1149,7 +1154,8 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
     const long long before = launches_total();
-    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32)
+    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32 &&
+        mode != SCWP_SYNTH_GATHER_FP16)
         return fail(ctx, SCWP_E_INVALID, "mode");
     if (!ctx->bg_valid) {
         CU(launch_background(ctx->bg, ctx->t, ctx->st));
@@ -1174,10 +1180,22 @@ scwp_status scwp_set_batched(scwp_ctx* ctx, int32_t on) {
     return SCWP_OK;
 }
 
+scwp_status scwp_set_bucket_range(scwp_ctx* ctx, int32_t b_lo, int32_t b_hi) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (b_lo < 0 || b_hi <= b_lo) return fail(ctx, SCWP_E_INVALID, "bucket range");
+    graph_reset(ctx);
+    ctx->b_lo = b_lo;
+    ctx->b_hi = b_hi;
+    ctx->synth_dirty = true;
+    return SCWP_OK;
+}
+
 scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
-    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32)
+    if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32 &&
+        mode != SCWP_SYNTH_GATHER_FP16)
         return fail(ctx, SCWP_E_INVALID, "mode");
     graph_reset(ctx);
     ctx->synth_mode = mode;

@@ -117,6 +117,7 @@ struct SynthParams {
     int N;                  // background grid size
     const float* bg;        // [3][N][N]
     float row_scale;        // power of two putting the patch's largest |A| near 2^13
+    int b_lo, b_hi;         // buckets synthesised: [b_lo, b_hi) (a diagnostic range; default all)
 };
 
 // Every launcher reports how many kernels it enqueued (process-wide counter,
@@ -136,8 +137,10 @@ cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaSt
 // Tensor-core synthesis of `n_items` items (any patches) in one launch, then
 // the group-sum blend of `n_spans` spans in one launch.  `pdevs` and `sps`
 // are device arrays indexed by patch.
+// split: FP16 hi/lo operands (3 MMAs per K step, the FP32 contract);
+// otherwise single FP16 operands (1 MMA per K step, the FP16 contract).
 cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
-                            const BlendSpan* spans, int n_spans, cudaStream_t st);
+                            const BlendSpan* spans, int n_spans, cudaStream_t st, bool split = true);
 // tensor-core synthesis geometry: tile side (texels), bumps per operand stage,
 // and resident CTAs per SM (0 on error)
 int synth_tc_tile();

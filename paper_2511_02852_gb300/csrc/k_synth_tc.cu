@@ -165,6 +165,14 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b) {
 // byte offset of element (row r, k) in a K-major canonical operand
 __device__ __forceinline__ int canon(int r, int kq) { return kq * 128 + (r >> 3) * (int)kSBO + (r & 7) * 16; }
 
+// one operand row, rounded to FP16 (no split), for 8 consecutive bumps
+__device__ __forceinline__ void store_half8(uint16_t* hi, int off, const float (&f)[8]) {
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = pack_f16(f[2 * k], f[2 * k + 1]);
+    *reinterpret_cast<uint4*>((char*)hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+}
+
 // one operand row, hi and lo parts, for 8 consecutive bumps (one 16-byte
 // core-matrix row each)
 __device__ __forceinline__ void store_split8(uint16_t* hi, uint16_t* lo, int off, const float (&f)[8]) {
@@ -186,7 +194,8 @@ __device__ __forceinline__ void store_split8(uint16_t* hi, uint16_t* lo, int off
 // and sin(pi u/R) (`amul` = 1); zero outside the support |u| < R.  `rec`
 // points at this role's 16-byte half of each 32-byte record: {x, cx, sx, id}
 // or {y, cy, sy, amp}; (ct[e], st[e]) = e^{i pi (pos[e] mod 2R)/R}.
-template <bool ROW>
+// SPLIT: hi + lo FP16 parts; otherwise one FP16 rounding (no lo part).
+template <bool ROW, bool SPLIT>
 __device__ __forceinline__ void gen_quarter(uint16_t* hi, uint16_t* lo, const float4* rec, int q, int idx,
                                             const int32_t (&pos)[2], int32_t R, const float (&ct)[2],
                                             const float (&st)[2], float amul) {
@@ -211,8 +220,13 @@ __device__ __forceinline__ void gen_quarter(uint16_t* hi, uint16_t* lo, const fl
             f1[j] = m * sn;
         }
         const int ent = idx + 32 * e;
-        store_split8(hi, lo, canon(ent, q), f0);
-        store_split8(hi, lo, canon(kTX + ent, q), f1);   // kTX == kTY: second half of either operand
+        if (SPLIT) {
+            store_split8(hi, lo, canon(ent, q), f0);
+            store_split8(hi, lo, canon(kTX + ent, q), f1);   // kTX == kTY: second half of either operand
+        } else {
+            store_half8(hi, canon(ent, q), f0);
+            store_half8(hi, canon(kTX + ent, q), f1);
+        }
     }
 }
 
@@ -249,6 +263,7 @@ __device__ __forceinline__ float blend1(const SynthParams& sp, int ix, int iy, i
     return w * wp + (1.f - w) * bg;
 }
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, const PatchDev* pdevs,
                                                           const SynthParams* sps) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -270,7 +285,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
     // (read from global memory: the shared copies are read after the first barrier)
     const int ntx = (pdevs[it.patch].W + kTX - 1) / kTX, nb = sps[it.patch].nb;
     const int tx0 = (tile % ntx) * kTX, ty0 = (tile / ntx) * kTY;
-    const int b_begin = (g * nb) / G, b_end = ((g + 1) * nb) / G;
+    const int b_begin = max((g * nb) / G, sps[it.patch].b_lo);
+    const int b_end = min(((g + 1) * nb) / G, sps[it.patch].b_hi);
 
     if (tid == 0) {
         for (int k = 0; k < kRecSlots; ++k) {
@@ -319,8 +335,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                     const uint64_t bh = smem_desc((const char*)T.Bhi + off, 128, kSBO);
                     const uint64_t bl = smem_desc((const char*)T.Blo + off, 128, kSBO);
                     mma_f16(tmem, ah, bh, idesc, acc);
-                    mma_f16(tmem + kCorrCol, ah, bl, idesc, acc2);
-                    mma_f16(tmem + kCorrCol, al, bh, idesc, 1);
+                    if (SPLIT) {
+                        mma_f16(tmem + kCorrCol, ah, bl, idesc, acc2);
+                        mma_f16(tmem + kCorrCol, al, bh, idesc, 1);
+                    }
                     acc = acc2 = 1;
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -471,9 +489,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             // slots past n hold sentinel records outside every support
             const float4* rc = reinterpret_cast<const float4*>(S.rec[rs]) + (is_row ? 1 : 0);
             if (is_row)
-                gen_quarter<true>(T.Bhi, T.Blo, rc, kq, idx, pos, R, ct, st, row_scale);
+                gen_quarter<true, SPLIT>(T.Bhi, T.Blo, rc, kq, idx, pos, R, ct, st, row_scale);
             else
-                gen_quarter<false>(T.Ahi, T.Alo, rc, kq, idx, pos, R, ct, st, 1.f);
+                gen_quarter<false, SPLIT>(T.Ahi, T.Alo, rc, kq, idx, pos, R, ct, st, 1.f);
             if (tid == 0) S.stage_n[fs] = m.n;
             // every lane's operand stores visible to the tensor core, then
             // one arrival for the warp on each barrier
@@ -518,7 +536,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             if (any) {
                 const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * cb);
                 tmem_ld32(lane_base, r);
-                tmem_ld32(lane_base + kCorrCol, c);
+                if (SPLIT) {
+                    tmem_ld32(lane_base + kCorrCol, c);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) c[j] = 0u;
+                }
             } else {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) r[j] = c[j] = 0u;
@@ -552,11 +575,17 @@ int synth_tc_stage_bumps() { return kKc; }
 
 namespace {
 // the largest shared-memory carveout, so that two CTAs fit on an SM
-cudaError_t tc_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+template <bool SPLIT>
+cudaError_t tc_attributes_one() {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_synth_tc<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_synth_tc<SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
+}
+cudaError_t tc_attributes() {
+    const cudaError_t e = tc_attributes_one<true>();
+    return e != cudaSuccess ? e : tc_attributes_one<false>();
 }
 }  // namespace
 
@@ -569,7 +598,7 @@ int synth_tc_ctas_per_sm() {
     if (tc_attributes() != cudaSuccess) return 0;
     int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
     cudaFuncAttributes a;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&a, k_synth_tc) != cudaSuccess ||
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&a, k_synth_tc<true>) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
@@ -585,12 +614,15 @@ int synth_tc_ctas_per_sm() {
 }
 
 cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
-                            const BlendSpan* spans, int n_spans, cudaStream_t st) {
+                            const BlendSpan* spans, int n_spans, cudaStream_t st, bool split) {
     const size_t sm = sizeof(TcSmem);
     cudaError_t e = tc_attributes();
     if (e != cudaSuccess) return e;
     if (n_items > 0) {
-        k_synth_tc<<<n_items, kThreads, sm, st>>>(items, pdevs, sps);
+        if (split)
+            k_synth_tc<true><<<n_items, kThreads, sm, st>>>(items, pdevs, sps);
+        else
+            k_synth_tc<false><<<n_items, kThreads, sm, st>>>(items, pdevs, sps);
         count_launches(1);
     }
     if (n_spans > 0) return launch_blend_spans(spans, n_spans, pdevs, sps, st);

@@ -22,7 +22,7 @@ from . import _build
 MAX_BUCKETS = 64
 WAKE_DIRS = 4096
 FIELD_H, FIELD_DX, FIELD_DY = 0, 1, 2
-SYNTH_GATHER, SYNTH_LAYERED, SYNTH_GATHER_FP32 = 0, 1, 2
+SYNTH_GATHER, SYNTH_LAYERED, SYNTH_GATHER_FP32, SYNTH_GATHER_FP16 = 0, 1, 2, 3
 (TAB_OMEGA, TAB_K, TAB_C, TAB_R, TAB_E, TAB_EDGES, TAB_AMP, TAB_RQ, TAB_VX, TAB_VY, TAB_QX,
  TAB_QY, TAB_WAKE_VX, TAB_WAKE_VY, TAB_WAKE_QX, TAB_WAKE_QY, TAB_CARRY) = range(17)
 STATUS = {0: "SCWP_OK", 1: "SCWP_E_INVALID", 2: "SCWP_E_NOMEM", 3: "SCWP_E_CAPACITY",
@@ -104,6 +104,7 @@ EXPORTS = {
     "scwp_resynthesize": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_synth_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_batched": (C.c_int, [C.c_void_p, C.c_int32]),
+    "scwp_set_bucket_range": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "scwp_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "scwp_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -378,6 +379,9 @@ class Scene:
 
     def set_batched(self, on):
         _check(lib().scwp_set_batched(self.ctx, 1 if on else 0), self.ctx)
+
+    def set_bucket_range(self, b_lo, b_hi):
+        _check(lib().scwp_set_bucket_range(self.ctx, int(b_lo), int(b_hi)), self.ctx)
 
     def set_timing(self, on):
         _check(lib().scwp_set_timing(self.ctx, 1 if on else 0), self.ctx)

@@ -171,6 +171,21 @@ def batched(n_patches=32, total_particles=4_000_000, seed=1):
     return scene("batched", spec, ps, frames=300)
 
 
+# -- mixed_large: 2048^2 FFT over 4 km; 8 patches of 1024^2 cells at 0.25 m,
+#    2M particles each, 32 equal-energy buckets; JONSWAP U10 = 15 m/s at a
+#    100 km fetch, gamma 3.3, depth 50 m (the realistic sea, which the scene
+#    list leaves open); no wakes; patch origins from seed 2.
+def mixed_large(n_patches=8, particles=2_000_000, seed=2):
+    rng = np.random.default_rng(seed)
+    spec = spectrum(spectrum=JONSWAP, wind_speed=15.0, fetch=100e3, gamma=3.3, depth=50.0,
+                    n_buckets=32, n_theta=16, fft_n=2048, fft_L=4000.0, seed=seed)
+    ps = [patch(origin_x=float(rng.uniform(-1500.0, 1200.0)), origin_y=float(rng.uniform(-1500.0, 1200.0)),
+                cell=0.25, width=1024, height=1024, max_particles=int(2 * particles + 4096),
+                prefill=int(particles), inject_scale=float(particles) / 200000.0 * 1.9)
+          for _ in range(n_patches)]
+    return scene("mixed_large", spec, ps, frames=300)
+
+
 # -- serving: 64 independent scenes: FFT 256^2..1024^2 (log-uniform powers
 #    of two), JONSWAP U10 uniform in 5..20 m/s at a 100 km fetch, 1..16
 #    patches with sides log-uniform in 64..512 cells, 1e4..1e6 particles per
@@ -228,4 +243,5 @@ def scaled(sc, **patch_overrides):
 
 
 ALL = {"tiny": tiny, "realistic": realistic, "small_jonswap": small_jonswap,
-       "small_two_patches": small_two_patches, "small_batch": small_batch, "batched": batched}
+       "small_two_patches": small_two_patches, "small_batch": small_batch, "batched": batched,
+       "mixed_large": mixed_large}

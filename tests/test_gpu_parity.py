@@ -331,3 +331,46 @@ def test_batched_frame_matches_plain_and_oracle():
     a.close()
     b.close()
     c.close()
+
+
+FP16_MAX_ABS = 2e-3    # times Hs: the contract of reduced-precision synthesis
+
+
+@pytest.mark.parametrize("make_cfg", [wl.small_jonswap, wl.small_batch])
+def test_fp16_synthesis_within_2e3_hs_per_bucket_and_patch(make_cfg):
+    """Single-FP16 tensor-core operands (SCWP_SYNTH_GATHER_FP16): state and
+    bins unchanged (bit-exact), and every patch's maps, and every bucket's
+    share of them, within 2e-3 Hs of the FP64 oracle.  The errors are
+    printed per patch and bucket."""
+    from paper_2511_02852_gb300 import scwp
+    cfg = make_cfg()
+    sc = make(cfg)
+    sc.set_batched(True)
+    sc.set_synth_mode(scwp.SYNTH_GATHER_FP16)
+    orc = OracleScene(cfg)
+    hs = orc.spec.Hs()
+    for _ in range(3):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    bg = orc.background()
+    worst = 0.0
+    for p in range(len(cfg["patches"])):
+        compare_state(sc, orc, p)
+        compare_bins(sc, orc, p)
+        ref, _ = orc.patch_maps(p, bg)
+        err = max(np.abs(g.astype(np.float64) - r).max() for g, r in zip(sc.maps(p), ref)) / hs
+        print(f"[fp16] {cfg['name']} patch {p}: max|d| = {err:.2e} Hs")
+        assert err <= FP16_MAX_ABS
+        worst = max(worst, err)
+    nbs = [sc.info(p).n_buckets for p in range(len(cfg["patches"]))]
+    for i in range(max(nbs)):
+        sc.set_bucket_range(i, i + 1)
+        sc.resynthesize(scwp.SYNTH_GATHER_FP16)
+        for p in range(len(cfg["patches"])):
+            if i >= nbs[p]:
+                continue
+            ref, _ = orc.patch_maps(p, bg, buckets=(i, i + 1))
+            err = max(np.abs(g.astype(np.float64) - r).max() for g, r in zip(sc.maps(p), ref)) / hs
+            print(f"[fp16] {cfg['name']} patch {p} bucket {i}: max|d| = {err:.2e} Hs")
+            assert err <= FP16_MAX_ABS
+    sc.close()
