@@ -19,7 +19,7 @@
 namespace scwp {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;    // upper bound of a launch's block
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -160,7 +160,10 @@ cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st, const 
     cudaError_t e = cudaFuncSetAttribute(k_spectrum_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smr);
     if (e != cudaSuccess) return e;
-    k_spectrum_rows<<<N / rpc, kThreads, smr, st>>>(bg, t, t_dev, rpc);
+    // 512 threads from N = 512 up (more warps to hide the shared-memory
+    // stages; measured best against 256 and 1024), 256 below
+    const int threads = N >= 512 ? 512 : 256;
+    k_spectrum_rows<<<N / rpc, threads, smr, st>>>(bg, t, t_dev, rpc);
     // enough column groups to fill the SMs (both planes: 2 N / cw CTAs), at
     // least 4 columns (one 32-byte sector of each row) where shared memory
     // (twiddles + two buffers of N x cw) still leaves two CTAs per SM
@@ -172,7 +175,7 @@ cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st, const 
     const size_t smc = sizeof(float2) * ((size_t)N + 2 * (size_t)N * cw);
     e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
     if (e != cudaSuccess) return e;
-    k_fft_cols<<<dim3(N / cw, 2), kThreads, smc, st>>>(bg, cw);
+    k_fft_cols<<<dim3(N / cw, 2), threads, smc, st>>>(bg, cw);
     count_launches(2);
     return cudaGetLastError();
 }
