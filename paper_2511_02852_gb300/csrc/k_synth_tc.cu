@@ -31,6 +31,13 @@
 // e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the bump's
 // e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half per
 // role), so a sample costs one complex multiply and an integer support test.
+// Bumps whose support covers the whole tile on both axes (whole bins of
+// them, by the bin geometry) skip the MMAs: for those the kernel factors are
+// rank 3 in (texel, bump), so the loader sums their 3 x 3 moments
+// M = sum_b A_b p_b q_b^T per bucket (p_b, q_b from the record's phase
+// factors) and the read-out adds u^T M v per texel (u, v the texel's own
+// phase factors) to the tensor-core sums: the same sums, a different
+// rounding order.
 // One thread of warp 8 issues the MMAs and commits each stage back to the
 // producers; after the last stage the producer warps read the accumulator
 // out of tensor memory (tcgen05.ld) and write the bucket group's partial
@@ -69,6 +76,14 @@ struct __align__(1024) TcStage {   // FP16 operands
     uint16_t Blo[2 * kTY * kKc];
 };
 
+// moments of one bucket's full-cover bumps over a tile: M[i][j] =
+// sum_b A_b p_i(b) q_j(b), p = (1, cos, -sin)(pi (x_b mod 2R)/R), q likewise
+// for y (the record's phase factors)
+struct MomRec {
+    int32_t R;
+    float m[9];
+};
+
 // what the loader tells the producers about a staged record chunk
 struct ChunkMeta {
     int n;          // bumps in the chunk (the rest of the slot holds sentinels); -1 ends the stream
@@ -85,6 +100,8 @@ struct TcSmem {
     unsigned long long empty[kStages];   // MMA commit -> producers (1 arrival)
     unsigned long long done;             // final MMA commit -> epilogue
     int stage_n[kStages];                // bumps in the stage; -1 ends the stream
+    MomRec mom[kMaxBuckets];             // full-cover moments, one per bucket that has any
+    int n_mom;
     uint32_t tmem;
     alignas(16) unsigned char pd[sizeof(PatchDev)];     // this item's patch
     alignas(16) unsigned char spd[sizeof(SynthParams)];
@@ -133,6 +150,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(sa(b))
                  : "memory");
 }
+
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory"); }
 
 // shared-memory matrix descriptor: no swizzle, K-major canonical layout
 __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
@@ -363,6 +382,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
         const int32_t Xlo = tx0 * kQi + kHalfi, Xhi = (tx0 + kTX - 1) * kQi + kHalfi;
         const int32_t Ylo = ty0 * kQi + kHalfi, Yhi = (ty0 + kTY - 1) * kQi + kHalfi;
         int gc = 0;        // chunks published
+        int n_mom = 0;     // buckets with full-cover moments
         bool ok = true;
         // slot of chunk gc once the producers are done with its previous chunk
         auto claim = [&]() -> int {
@@ -384,14 +404,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             if (bx_hi > bk.nbx - 1) bx_hi = bk.nbx - 1;
             if (by_hi > bk.nby - 1) by_hi = bk.nby - 1;
             if (bx_lo > bx_hi || by_lo > by_hi) continue;
+            // Bins whose every bump covers the whole tile (every texel centre
+            // strictly inside the support on both axes): bin bx holds
+            // x_b + R in [bx C, (bx + 1) C), so it is full-cover in x iff
+            // bx C > Xhi and (bx + 1) C <= Xlo + 2R.  Their bumps enter the
+            // sums through the tile's 3 x 3 moments instead of the MMAs.
+            const int fx_lo = max(bx_lo, (int)((int64_t)Xhi / bk.C) + 1);
+            const int fx_hi = min(bx_hi, (int)(((int64_t)Xlo + 2 * (int64_t)bk.R) / bk.C) - 1);
+            float mom[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) mom[q] = 0.f;
+            bool any_full = false;
             for (int byb = by_lo; byb <= by_hi && ok; byb += kBatchRows) {
                 const int nr = min(kBatchRows, by_hi - byb + 1);
-                int rs = 0, rl = 0;
+                // this lane's bin row: dense record ranges [rs, rs + rl) and
+                // [rs2, rs2 + rl2), full-cover range [fs, fs + fl)
+                int rs = 0, rl = 0, rs2 = 0, rl2 = 0, fs = 0, fl = 0;
                 if (lane < nr) {
-                    const int key0 = bk.base + (byb + lane) * bk.nbx;
+                    const int by = byb + lane;
+                    const int key0 = bk.base + by * bk.nbx;
+                    const bool fy = (int64_t)by * bk.C > (int64_t)Yhi &&
+                                    ((int64_t)by + 1) * bk.C <= (int64_t)Ylo + 2 * (int64_t)bk.R;
                     rs = (int)p.offsets[key0 + bx_lo];
-                    rl = (int)p.offsets[key0 + bx_hi + 1] - rs;
+                    const int e = (int)p.offsets[key0 + bx_hi + 1];
+                    if (fy && fx_lo <= fx_hi) {
+                        fs = (int)p.offsets[key0 + fx_lo];
+                        const int f1 = (int)p.offsets[key0 + fx_hi + 1];
+                        rl = fs - rs;
+                        fl = f1 - fs;
+                        rs2 = f1;
+                        rl2 = e - f1;
+                    } else {
+                        rl = e - rs;
+                    }
                 }
+                rl += rl2;      // dense length of this lane's row
                 int inc = rl;   // inclusive prefix of the range lengths over the lanes
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
@@ -422,15 +469,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                     __syncwarp();
                     if (lane == 0) bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
                     __syncwarp();
-                    // this lane's range covers [cum, cum + rl) of the batch
-                    const int a = max(lo, cum), b = min(lo + n, cum + rl);
+                    // this lane's row covers [cum, cum + rl) of the batch: its
+                    // first dense range, then its second
+                    const int l1 = rl - rl2;
+                    int a = max(lo, cum), b = min(lo + n, cum + l1);
                     if (a < b)
                         bulk_g2s(&S.rec[slot][a - lo], p.rec + rs + (a - cum), (uint32_t)((b - a) * sizeof(BumpRec)),
                                  &S.rbar[slot]);
+                    a = max(lo, cum + l1);
+                    b = min(lo + n, cum + rl);
+                    if (a < b)
+                        bulk_g2s(&S.rec[slot][a - lo], p.rec + rs2 + (a - cum - l1),
+                                 (uint32_t)((b - a) * sizeof(BumpRec)), &S.rbar[slot]);
                     ++gc;
                 }
+                // moments, after this batch's dense chunks are staged (the
+                // producers work through them meanwhile): lane l takes records
+                // l, l + 32, ... of each full-cover range, ranges in lane order
+                // (a fixed order)
+                if (__any_sync(0xffffffffu, fl > 0)) {
+                    any_full = true;
+                    for (int k = 0; k < nr; ++k) {
+                        const int s0 = __shfl_sync(0xffffffffu, fs, k), l0 = __shfl_sync(0xffffffffu, fl, k);
+                        for (int j = lane; j < l0; j += 32) {
+                            const float4 a4 = reinterpret_cast<const float4*>(p.rec + s0 + j)[0];   // x cx sx id
+                            const float4 b4 = reinterpret_cast<const float4*>(p.rec + s0 + j)[1];   // y cy sy A
+                            const float pv[3] = {b4.w, b4.w * a4.y, b4.w * a4.z};                  // A p
+                            const float qv[3] = {1.f, b4.y, b4.z};
+#pragma unroll
+                            for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+                                for (int j2 = 0; j2 < 3; ++j2) mom[3 * i2 + j2] = fmaf(pv[i2], qv[j2], mom[3 * i2 + j2]);
+                        }
+                    }
+                }
+            }
+            if (any_full) {   // this bucket's moments: a fixed reduction tree over the lanes
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) mom[q] += __shfl_xor_sync(0xffffffffu, mom[q], d);
+                if (lane == 0 && n_mom < kMaxBuckets) {
+                    S.mom[n_mom].R = bk.R;
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) S.mom[n_mom].m[q] = mom[q];
+                }
+                ++n_mom;
             }
         }
+        if (lane == 0) S.n_mom = min(n_mom, kMaxBuckets);   // published by the end-of-stream arrival
         if (ok) {   // end of the stream
             const int slot = claim();
             if (ok) {
@@ -522,6 +609,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
         bar_wait(&S.done, 0u, err);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool any = produced > 0;   // otherwise no MMA ever wrote the accumulator
+        // Full-cover moments: the operand stages are idle once every MMA has
+        // completed, so they hold the tile's phase factors per moment bucket,
+        // tab[b][e] = e^{i pi (X_e mod 2R_b)/R_b}, e < 64 the tile rows (y),
+        // e >= 64 the tile columns (x).
+        const int nm = S.n_mom;
+        const float2* tab = reinterpret_cast<const float2*>(S.st);
+        static_assert(sizeof(S.st) >= (size_t)kMaxBuckets * 128 * sizeof(float2), "phase tables fit the stages");
+        if (nm > 0) {
+            float2* wtab = reinterpret_cast<float2*>(S.st);
+            for (int k = tid; k < nm * 128; k += kProdThreads) {
+                const int b = k >> 7, e = k & 127;
+                const int32_t pe = e < 64 ? Ylo + e * kQi : Xlo + (e - 64) * kQi;
+                const int64_t R2 = 2 * (int64_t)S.mom[b].R;
+                int64_t pm = (int64_t)pe % R2;
+                if (pm < 0) pm += R2;
+                float sn, cs;
+                sincospif((float)((double)pm / (double)S.mom[b].R), &sn, &cs);
+                wtab[k] = make_float2(cs, sn);
+            }
+            prod_sync();
+        }
         // warp w reads TMEM lane quarter w & 3 (accumulator rows); the two
         // groups of four warps split the column blocks of those rows
         const int quarter = warp & 3, grp = warp >> 2;
@@ -549,12 +657,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             const int f = cb < kTY / 32 ? (lowm ? 0 : 1) : 2;
             const float scale = (f == 0 ? 0.25f : 0.5f * sp.lam_half) / row_scale;
             const int y0 = ty0 + 32 * (cb & (kTY / 32 - 1));
+            // the tensor-core sums, then the full-cover terms: h = 1/4 u M v,
+            // Dx = lam/4 u' M v, Dy = lam/4 u M v', u = (1, c, -s) and
+            // u' = (0, s, c) of the column, v and v' of the row
+            float val[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) val[j] = (__uint_as_float(r[j]) + __uint_as_float(c[j])) * scale;
+            for (int b = 0; b < nm; ++b) {
+                const float2 ux = tab[b * 128 + 64 + (m & (kTX - 1))];
+                const float u0 = f == 1 ? 0.f : 1.f, u1 = f == 1 ? ux.y : ux.x, u2 = f == 1 ? ux.x : -ux.y;
+                const float* M = S.mom[b].m;
+                const float w0 = u0 * M[0] + u1 * M[3] + u2 * M[6];   // (u^T M)_j
+                const float w1 = u0 * M[1] + u1 * M[4] + u2 * M[7];
+                const float w2 = u0 * M[2] + u1 * M[5] + u2 * M[8];
+                const float fs = f == 0 ? 0.25f : 0.5f * sp.lam_half;
+                const int e0 = 32 * (cb & (kTY / 32 - 1));
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float2 vy = tab[b * 128 + e0 + j];
+                    const float t = f == 2 ? fmaf(w1, vy.y, w2 * vy.x) : fmaf(w1, vy.x, fmaf(-w2, vy.y, w0));
+                    val[j] = fmaf(fs, t, val[j]);
+                }
+            }
             if (x >= sp.W) continue;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int y = y0 + j;
                 if (y < sp.H) {
-                    const float v = (__uint_as_float(r[j]) + __uint_as_float(c[j])) * scale;
+                    const float v = val[j];
                     const size_t o = (size_t)y * sp.W + x;
                     if (G > 1) p.partial[((size_t)g * 3 + f) * plane + o] = v;
                     else p.out[(size_t)f * plane + o] = blend1(sp, x, y, f, v);
