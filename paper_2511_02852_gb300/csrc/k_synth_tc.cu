@@ -491,15 +491,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                     any_full = true;
                     for (int k = 0; k < nr; ++k) {
                         const int s0 = __shfl_sync(0xffffffffu, fs, k), l0 = __shfl_sync(0xffffffffu, fl, k);
-                        for (int j = lane; j < l0; j += 32) {
-                            const float4 a4 = reinterpret_cast<const float4*>(p.rec + s0 + j)[0];   // x cx sx id
-                            const float4 b4 = reinterpret_cast<const float4*>(p.rec + s0 + j)[1];   // y cy sy A
-                            const float pv[3] = {b4.w, b4.w * a4.y, b4.w * a4.z};                  // A p
-                            const float qv[3] = {1.f, b4.y, b4.z};
+                        // four records in flight per lane, summed in index order
+                        for (int j0 = lane; j0 < l0; j0 += 128) {
+                            float4 a4[4], b4[4];
 #pragma unroll
-                            for (int i2 = 0; i2 < 3; ++i2)
+                            for (int u = 0; u < 4; ++u) {
+                                const int j = j0 + 32 * u;
+                                a4[u] = b4[u] = make_float4(0.f, 0.f, 0.f, 0.f);   // A = 0 past the range
+                                if (j < l0) {
+                                    a4[u] = reinterpret_cast<const float4*>(p.rec + s0 + j)[0];   // x cx sx id
+                                    b4[u] = reinterpret_cast<const float4*>(p.rec + s0 + j)[1];   // y cy sy A
+                                }
+                            }
 #pragma unroll
-                                for (int j2 = 0; j2 < 3; ++j2) mom[3 * i2 + j2] = fmaf(pv[i2], qv[j2], mom[3 * i2 + j2]);
+                            for (int u = 0; u < 4; ++u) {
+                                const float pv[3] = {b4[u].w, b4[u].w * a4[u].y, b4[u].w * a4[u].z};   // A p
+                                const float qv[3] = {1.f, b4[u].y, b4[u].z};
+#pragma unroll
+                                for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+                                    for (int j2 = 0; j2 < 3; ++j2)
+                                        mom[3 * i2 + j2] = fmaf(pv[i2], qv[j2], mom[3 * i2 + j2]);
+                            }
                         }
                     }
                 }
