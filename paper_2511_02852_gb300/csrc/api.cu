@@ -330,7 +330,14 @@ std::vector<double> tile_bucket_stages(const PatchHost& P, int& tiles) {
             const double y0 = (t / ntx) * ts - r, y1 = (t / ntx + 1) * ts + r;
             const double ax = std::max(0.0, std::min(x1, T.W + r) - std::max(x0, -r));
             const double ay = std::max(0.0, std::min(y1, T.H + r) - std::max(y0, -r));
-            est[(size_t)t * T.nb + i] = std::ceil(dens * ax * ay / kc);
+            // bump centres that cover the whole tile go through the 3 x 3
+            // moments, not the MMAs: the box (x_last - r, x_first + r),
+            // shrunk by half a bin on each side for the bin rounding
+            // (x0, x1 are the tile grown by r: the box is (x1 - 2r, x0 + 2r))
+            const double hc = 0.5 * P.bin_cells[i];
+            const double fx = std::max(0.0, std::min(x0 + 2 * r - hc, T.W + r) - std::max(x1 - 2 * r + hc, -r));
+            const double fy = std::max(0.0, std::min(y0 + 2 * r - hc, T.H + r) - std::max(y1 - 2 * r + hc, -r));
+            est[(size_t)t * T.nb + i] = std::ceil(dens * std::max(0.0, ax * ay - fx * fy) / kc);
         }
     }
     return est;
