@@ -205,6 +205,15 @@ scwp_status scwp_step(scwp_ctx* ctx, double dt);
  * least the map size.  dst_on_device = 1: device-to-device copy ordered on
  * the stream (asynchronous); 0: device-to-host copy, synchronises the
  * stream. */
+/* Unit normals of a patch's last blended maps, [3][height][width] (nx, ny,
+ * nz): the normal of the displaced surface p(i, j) = (i c + Dx, j c + Dy, h)
+ * (c = the patch's cell size) by finite differences, central inside the
+ * patch and one-sided at its edges, the normalised cross product of the
+ * two tangents (Sec. 4.2 derives normals from the maps by finite
+ * differences; the formula is this library's).  dst_elems >= 3 W H.
+ * dst_on_device as in scwp_height_map. */
+scwp_status scwp_normal_map(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t dst_elems, int32_t dst_on_device);
+
 scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field,
                             float* dst, size_t dst_elems, int32_t dst_on_device);
 

@@ -222,3 +222,29 @@ def layered_maps(W, H, bumps, lam, nb, Rb):
             dxm += 0.5 * lam * kk * b
             dym += 0.5 * lam * ss * a
     return h, dxm, dym
+
+
+def normal_map(h, dx, dy, cell):
+    """Unit normals (nx, ny, nz), float64 [3, H, W], of the displaced surface
+    p(i, j) = (i c + Dx, j c + Dy, h) by finite differences (the paper
+    derives normals from the height maps by finite differences, Sec. 4.2;
+    the formula is this reading's): tangents by central differences inside,
+    one-sided at the edges, normal = their normalised cross product."""
+    h = np.asarray(h, dtype=np.float64)
+    dx = np.asarray(dx, dtype=np.float64)
+    dy = np.asarray(dy, dtype=np.float64)
+    H, W = h.shape
+    i = np.arange(W)
+    il, ir = np.maximum(i - 1, 0), np.minimum(i + 1, W - 1)
+    j = np.arange(H)
+    jl, jr = np.maximum(j - 1, 0), np.minimum(j + 1, H - 1)
+    sx = ((ir - il) * cell)[None, :] * np.ones((H, 1))
+    sy = ((jr - jl) * cell)[:, None] * np.ones((1, W))
+    tx = np.stack([sx + dx[:, ir] - dx[:, il], dy[:, ir] - dy[:, il], h[:, ir] - h[:, il]])
+    ty = np.stack([dx[jr, :] - dx[jl, :], sy + dy[jr, :] - dy[jl, :], h[jr, :] - h[jl, :]])
+    if W == 1:
+        tx = np.stack([np.full((H, W), cell), np.zeros((H, W)), np.zeros((H, W))])
+    if H == 1:
+        ty = np.stack([np.zeros((H, W)), np.full((H, W), cell), np.zeros((H, W))])
+    n = np.cross(tx, ty, axis=0)
+    return n / np.linalg.norm(n, axis=0, keepdims=True)

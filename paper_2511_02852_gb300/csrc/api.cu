@@ -127,6 +127,8 @@ struct scwp_ctx {
     cudaStream_t gst = nullptr;       // capture origin (the caller's stream may be the legacy one)
     std::vector<InjectParams> ips;    // this frame's injection plans
     size_t alloc_bytes = 0;           // device memory held by the context
+    float* normal_scratch = nullptr;  // normals for host destinations
+    size_t normal_bytes = 0;
     std::vector<double> b_work;       // estimated stages of each batched item
     std::vector<PatchDev> h_pdevs;    // host copies of the device descriptor arrays
     std::vector<SynthParams> h_sps;
@@ -1230,6 +1232,30 @@ scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field, floa
         CU(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
     } else {
         CU(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    return SCWP_OK;
+}
+
+scwp_status scwp_normal_map(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t dst_elems, int32_t dst_on_device) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (!dst || patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
+    const PatchHost* P = ctx->patches[patch_id];
+    const size_t n = (size_t)P->T.W * P->T.H;
+    if (dst_elems < 3 * n) return fail(ctx, SCWP_E_INVALID, "dst too small");
+    float* out = dst;
+    if (!dst_on_device) {
+        if (ctx->normal_bytes < 3 * n * sizeof(float)) {
+            ctx->normal_scratch = (float*)dalloc(ctx, 3 * n * sizeof(float));
+            if (!ctx->normal_scratch) return fail(ctx, SCWP_E_NOMEM, "normal scratch");
+            ctx->normal_bytes = 3 * n * sizeof(float);
+        }
+        out = ctx->normal_scratch;
+    }
+    CU(launch_normals(P->dev.out, P->T.W, P->T.H, (float)P->d.cell, out, ctx->st));
+    if (!dst_on_device) {
+        CU(cudaMemcpyAsync(dst, out, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
         CU(cudaStreamSynchronize(ctx->st));
     }
     return SCWP_OK;

@@ -146,6 +146,9 @@ cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pd
 int synth_tc_tile();
 int synth_tc_stage_bumps();
 int synth_tc_ctas_per_sm();
+// unit normals [3][H][W] of the displaced surface of maps [3][H][W] (h, Dx, Dy)
+cudaError_t launch_normals(const float* maps, int W, int H, float cell, float* dst, cudaStream_t st);
+
 // group sums and blend of `n_spans` spans of any patches, one launch
 cudaError_t launch_blend_spans(const BlendSpan* spans, int n_spans, const PatchDev* pdevs, const SynthParams* sps,
                                cudaStream_t st);

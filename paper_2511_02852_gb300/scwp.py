@@ -105,6 +105,7 @@ EXPORTS = {
     "scwp_set_synth_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_batched": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_bucket_range": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "scwp_normal_map": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]),
     "scwp_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "scwp_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -379,6 +380,13 @@ class Scene:
 
     def set_batched(self, on):
         _check(lib().scwp_set_batched(self.ctx, 1 if on else 0), self.ctx)
+
+    def normals(self, p):
+        """Unit normals (nx, ny, nz) of patch p's last blended maps, float32 [3, H, W]."""
+        H, W = self.patch_shape(p)
+        a = np.empty((3, H, W), dtype=np.float32)
+        _check(lib().scwp_normal_map(self.ctx, int(p), a.ctypes.data_as(C.c_void_p), a.size, 0), self.ctx)
+        return a
 
     def set_bucket_range(self, b_lo, b_hi):
         _check(lib().scwp_set_bucket_range(self.ctx, int(b_lo), int(b_hi)), self.ctx)

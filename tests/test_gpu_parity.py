@@ -374,3 +374,32 @@ def test_fp16_synthesis_within_2e3_hs_per_bucket_and_patch(make_cfg):
             print(f"[fp16] {cfg['name']} patch {p} bucket {i}: max|d| = {err:.2e} Hs")
             assert err <= FP16_MAX_ABS
     sc.close()
+
+
+def test_normal_map_matches_oracle_formula():
+    """scwp_normal_map: the GPU normals of the GPU maps equal the oracle's
+    finite-difference normals of the same maps (1e-5), and stay within the
+    slope error the map contract allows of the normals of the oracle's own
+    maps (a one-sided difference of two texels each off by at most
+    max|d map|: |d slope| <= 2 max|d map| / cell)."""
+    from oracle.synth import normal_map
+    cfg = wl.small_jonswap()
+    sc = make(cfg)
+    orc = OracleScene(cfg)
+    for _ in range(3):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    hs = orc.spec.Hs()
+    cell = float(cfg["patches"][0]["cell"])
+    got = sc.normals(0)
+    maps = sc.maps(0)
+    mine = normal_map(*maps, cell)
+    assert np.abs(got - mine).max() <= 1e-5
+    ref, _ = orc.patch_maps(0)
+    theirs = normal_map(*ref, cell)
+    d_map = max(np.abs(g.astype(np.float64) - r).max() for g, r in zip(maps, ref))
+    err = np.abs(got - theirs).max()
+    print(f"[normals] max|d n| = {err:.2e} (map error {d_map / hs:.2e} Hs, bound {2 * d_map / cell:.2e})")
+    assert err <= 2 * d_map / cell + 1e-6
+    assert np.allclose(np.sum(got.astype(np.float64) ** 2, axis=0), 1.0, atol=1e-5)
+    sc.close()
