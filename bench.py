@@ -304,6 +304,45 @@ def run_serving(args):
     return 0
 
 
+# ---- sweeps ----------------------------------------------------------------------------
+def run_sweep(args):
+    """The paper's Table 2 axes as synthetic sweeps: per point the FFT stage
+    alone (FFT-only), the particle stages plus synthesis (WP-only) and the
+    whole frame (hybrid), from the library's stage events."""
+    import torch
+    from paper_2511_02852_gb300 import scwp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = []
+    for pt in wl.sweep_points():
+        cfg = wl.sweep_point(**pt)
+        sc = scwp.Scene(cfg)
+        for _ in range(args.warmup):
+            sc.step(cfg["dt"])
+        torch.cuda.synchronize()
+        sc.set_timing(True)
+        sc.timing_read()
+        evals = 0
+        for _ in range(args.steps):
+            sc.step(cfg["dt"])
+            evals += sc.stats(0).eval_count
+        torch.cuda.synchronize()
+        st, fr = sc.timing_read()
+        sc.set_timing(False)
+        fft, wp, frame = st[0] / fr, (st[1] + st[2]) / fr, st[3] / fr
+        out.append(dict(pt, fft_ms=fft, wp_ms=wp, frame_ms=frame, fps=1000.0 / frame,
+                        evals_per_s=evals / (st[2] / 1000.0) if st[2] > 0 else 0.0,
+                        live=sc.stats(0).live_particles))
+        sc.close()
+    line = {"metric": METRIC + " (sweep)", "value": max(o["evals_per_s"] for o in out), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "sweep: (n_omega, n_theta) in {8,12,16}^2 at U10 10 m/s, res 512; "
+                                   "U10 in {3,5,15}; res in {256,1024}; one 128 m patch, 100k particles"},
+            "sweep": out}
+    print(json.dumps(line))
+    return 0
+
+
 # ---- ours ----------------------------------------------------------------------------
 def run_ours(args):
     import numpy as np
@@ -479,7 +518,7 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL) + ["serving"])
+    ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL) + ["serving", "sweep"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -495,13 +534,15 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
-        if args.workload == "serving":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no request server; "
-                                                                  "serving is measured on the GPU path only"}))
+        if args.workload in ("serving", "sweep"):
+            print(json.dumps({"impl": "reference", "unavailable": f"no oracle counterpart of the {args.workload} "
+                                                                  "mode; it is measured on the GPU path only"}))
             return 0
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 

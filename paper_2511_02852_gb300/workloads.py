@@ -225,6 +225,26 @@ def serving(n_scenes=64, seed=3):
     return out
 
 
+# -- sweep points (the paper's Table 2 axes; its numbers are Unity frame
+#    rates, context only): one 128 m patch of res^2 texels (cell 128/res),
+#    an FFT of res^2 over 512 m, JONSWAP at a 100 km fetch, (n_omega,
+#    n_theta) buckets x directions; 100k prefilled particles, injection at
+#    the steady-state rate.
+def sweep_point(n_omega=16, n_theta=16, u10=10.0, res=512, seed=5):
+    spec = spectrum(spectrum=JONSWAP, wind_speed=float(u10), fetch=100e3, gamma=3.3, depth=0.0,
+                    n_buckets=int(n_omega), n_theta=int(n_theta), fft_n=int(res), fft_L=512.0, seed=seed)
+    p = patch(origin_x=-64.0, origin_y=-64.0, cell=128.0 / res, width=int(res), height=int(res),
+              max_particles=400000, prefill=100000, inject_scale=1.0)
+    return scene(f"sweep_{n_omega}x{n_theta}_u{u10:g}_r{res}", spec, [p], frames=25)
+
+
+def sweep_points():
+    pts = [dict(n_omega=a, n_theta=b, u10=10.0, res=512) for a in (8, 12, 16) for b in (8, 12, 16)]
+    pts += [dict(n_omega=16, n_theta=16, u10=u, res=512) for u in (3.0, 5.0, 15.0)]
+    pts += [dict(n_omega=16, n_theta=16, u10=10.0, res=r) for r in (256, 1024)]
+    return pts
+
+
 def serving_arrivals(rate=2000.0, seconds=60.0, n_scenes=64, seed=4):
     """Poisson frame-step requests: (arrival time in s, scene index)."""
     rng = np.random.default_rng(seed)
