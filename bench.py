@@ -150,9 +150,10 @@ class ClockSampler:
 
 
 # ---- CPU oracle ------------------------------------------------------------------
-def oracle_strip_rate(cfg, target_s=10.0, frames=1, state=None):
+def oracle_strip_rate(cfg, target_s=10.0, frames=1, state=None, rows=None):
     """Time the FP64 oracle's synthesis on a strip of rows of patch 0 (a
-    bounded sample of the frame).  Returns (evals/s, evals, seconds, rows, threads)."""
+    bounded sample of the frame; `rows` given: that many, else as many as
+    fit target_s).  Returns (evals/s, evals, seconds, rows, threads)."""
     import numpy as np
     from oracle.scene import OracleScene
     from oracle.synth import synth_maps
@@ -171,9 +172,10 @@ def oracle_strip_rate(cfg, target_s=10.0, frames=1, state=None):
         _, _, _, ev = synth_maps(ps.T.W, rows, b, orc.lam)
         return ev, time.perf_counter() - t0
 
-    ev, dt = run(8)
-    per_row = max(dt / 8, 1e-6)
-    rows = int(min(ps.T.H, max(8, target_s / per_row)))
+    if rows is None:
+        ev, dt = run(8)
+        per_row = max(dt / 8, 1e-6)
+        rows = int(min(ps.T.H, max(8, target_s / per_row)))
     y0 = max(0, (ps.T.H - rows) // 2)
     ev, dt = run(rows, y0)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -189,10 +191,13 @@ def run_reference(args):
     orc = OracleScene(cfg)
     rates, times, evs = [], [], []
     rows_used = None
+    # each step: the oracle's frame update plus a strip of the synthesis,
+    # the strip sized once so that the whole run stays within ref_total_seconds
+    per_step = min(args.ref_seconds, max(0.05, args.ref_total_seconds / (args.warmup + args.steps)))
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         orc.step(cfg["dt"])
-        rate, ev, dt, rows, threads = oracle_strip_rate(cfg, target_s=args.ref_seconds, state=orc)
+        rate, ev, dt, rows, threads = oracle_strip_rate(cfg, target_s=per_step, state=orc, rows=rows_used)
         rows_used = rows
         if k >= args.warmup:
             rates.append(rate)
@@ -530,7 +535,8 @@ def main():
                     help="one synthesis launch over all patches of the frame (scwp_set_batched)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-seconds", type=float, default=2.0)
+    ap.add_argument("--ref-seconds", type=float, default=2.0, help="reference: strip seconds per step at most")
+    ap.add_argument("--ref-total-seconds", type=float, default=60.0, help="reference: strip seconds in all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
