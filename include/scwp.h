@@ -129,6 +129,9 @@ typedef struct scwp_patch_desc {
     double obj_radius, obj_speed, obj_path_radius, wake_amp;
     int32_t wake_rate;         /* particles per arm per frame              */
     int32_t n_buckets;         /* <= 0: the spectrum's                     */
+    double heave_period;       /* s; > 0 (with emitter): the object heaves and emits
+                                  ring ripples (Sec. 4.3, vertical motion)  */
+    int32_t ring_rate;         /* ring particles per frame at full heave speed (>= 0) */
 } scwp_patch_desc;
 
 /* Per-patch statistics of the last completed frame (counts are exact). */

@@ -85,6 +85,8 @@ class PatchTables:
         self.wake_rate = int(pcfg["wake_rate"])
         self.obj_speed = float(pcfg["obj_speed"])
         self.obj_path_radius = float(pcfg["obj_path_radius"])
+        self.heave_period = float(pcfg.get("heave_period", 0.0))
+        self.ring_rate = int(pcfg.get("ring_rate", 0))
         ca = [math.cos(a * DPSI) for a in range(WAKE_DIRS)]
         sa = [math.sin(a * DPSI) for a in range(WAKE_DIRS)]
         rw = self.b.r[self.bw]
@@ -150,6 +152,8 @@ class PatchState:
         self.J = np.zeros(0, dtype=np.int64)
         self.injected = 0
         self.energy = np.zeros(self.T.nb)
+        self.ring_carry = 0.0
+        self.ring_total = 0
         self.overflow = False
         self.prefill(int(pcfg["prefill"]))
 
@@ -227,6 +231,7 @@ class PatchState:
         self.inject(f)
         if T.emitter:
             self.wake(f, t)
+            self.ring(t)
 
     def inject(self, f):
         """Boundary injection (Sec. 3.3 Eqs. 15-17, Sec. 4.2).
@@ -304,6 +309,41 @@ class PatchState:
                 Ys.append(rint((Py + rho * sa + tau * ca) * Q))
                 Js.append(T.nth + a)
         n = len(Xs)
+        if n:
+            self._append(np.array(Xs, dtype=np.int64), np.array(Ys, dtype=np.int64),
+                         np.full(n, T.bw, dtype=np.int64), np.array(Js, dtype=np.int64))
+
+    def ring(self, t):
+        """Ring ripples of the heaving object (reading of Sec. 4.3, vertical
+        motion): with heave period T_h the object emits, each frame,
+        ring_rate |cos(2 pi t / T_h)| particles (its heave speed relative to
+        the peak), through a float64 carry capped at 64 a frame (the excess
+        stays in the carry); the k-th ring particle since creation goes out
+        along wake-grid direction (2531 k) mod 4096 from the rim point in that
+        direction; amplitude wake_amp, the wake's bucket."""
+        T = self.T
+        if T.ring_rate <= 0 or T.heave_period <= 0:
+            return
+        dx = T.dx
+        Rp = T.obj_path_radius / dx
+        Om = T.obj_speed / T.obj_path_radius
+        phi = Om * t
+        Px = T.W * 0.5 + Rp * math.cos(phi)
+        Py = T.H * 0.5 + Rp * math.sin(phi)
+        rho = T.obj_radius / dx
+        c = abs(math.cos(2.0 * math.pi * t / T.heave_period))
+        self.ring_carry += T.ring_rate * c
+        m = math.floor(self.ring_carry)
+        self.ring_carry -= m
+        n = int(min(m, 64.0))
+        self.ring_carry += m - n
+        Xs, Ys, Js = [], [], []
+        for _ in range(n):
+            a = (self.ring_total * 2531) % WAKE_DIRS
+            self.ring_total += 1
+            Xs.append(rint((Px + rho * T._wca[a]) * Q))
+            Ys.append(rint((Py + rho * T._wsa[a]) * Q))
+            Js.append(T.nth + a)
         if n:
             self._append(np.array(Xs, dtype=np.int64), np.array(Ys, dtype=np.int64),
                          np.full(n, T.bw, dtype=np.int64), np.array(Js, dtype=np.int64))

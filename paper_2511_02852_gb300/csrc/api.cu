@@ -47,6 +47,8 @@ struct PatchHost {
     int64_t injected = 0;
     std::vector<double> energy;       // [nb]
     double band = 0;
+    double ring_carry = 0.0;          // ring-ripple emission carry
+    int64_t ring_total = 0;           // ring particles emitted so far
     std::vector<TcItem> tc_items;     // tensor-core synthesis items of this patch, launch order
     std::vector<BlendSpan> tc_spans;  // its group-sum blend spans (G > 1)
     TcItem* d_items = nullptr;
@@ -207,7 +209,8 @@ scwp_status check_patch_desc(const scwp_patch_desc* d, std::string& why) {
     if (d->prefill < 0) { why = "prefill < 0"; return SCWP_E_INVALID; }
     if (d->n_buckets > SCWP_MAX_BUCKETS) { why = "n_buckets out of range"; return SCWP_E_INVALID; }
     if (d->emitter) {
-        if (!(d->obj_path_radius > 0) || !(d->obj_radius > 0) || d->wake_rate < 0 || d->wake_rate > 1 << 20) {
+        if (!(d->obj_path_radius > 0) || !(d->obj_radius > 0) || d->wake_rate < 0 || d->wake_rate > 1 << 20 ||
+            d->ring_rate < 0 || d->ring_rate > 1 << 20 || d->heave_period < 0) {
             why = "emitter parameters";
             return SCWP_E_INVALID;
         }
@@ -928,6 +931,45 @@ static void frame_injection(scwp_ctx* ctx, PatchHost* P, InjectParams& ip_out) {
             const double rw = T.r[T.wake_bucket];
             P->energy[T.wake_bucket] +=
                 P->d.wake_rate * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
+        }
+    }
+    if (D.emitter && P->d.ring_rate > 0 && P->d.heave_period > 0) {
+        // reading of Sec. 4.3, vertical motion: the object heaves with
+        // period T_h; each frame it emits ring_rate |cos(2 pi t / T_h)|
+        // particles (its heave speed relative to the peak; an FP64 carry),
+        // outward on its rim at successive directions of the wake grid
+        // (stepping by 2531, odd, so every direction comes round), with the
+        // wake's amplitude and bucket
+        const double dx = P->d.cell;
+        const double Rp = P->d.obj_path_radius / dx;
+        const double Om = P->d.obj_speed / P->d.obj_path_radius;
+        const double phi = Om * ctx->t;
+        const double Px = T.W * 0.5 + Rp * std::cos(phi);
+        const double Py = T.H * 0.5 + Rp * std::sin(phi);
+        const double rho = P->d.obj_radius / dx;
+        const double c = std::fabs(std::cos(2.0 * M_PI * ctx->t / P->d.heave_period));
+        P->ring_carry += P->d.ring_rate * c;
+        const double m = std::floor(P->ring_carry);
+        P->ring_carry -= m;
+        const int n = (int)std::min(m, (double)kMaxRing);
+        P->ring_carry += m - n;
+        if (n > 0) {
+            Segment& g = ip.seg[nseg++];
+            g.bucket = T.wake_bucket;
+            g.s = 3;
+            g.count = n;
+            g.first = total;
+            g.ndir = n;
+            total += n;
+            for (int k = 0; k < n; ++k) {
+                const int a = (int)((P->ring_total * 2531) % kWakeDirs);
+                P->ring_total += 1;
+                ip.ring_x[k] = (int32_t)std::nearbyint((Px + rho * T.wake_cos[a]) * (double)kQ);
+                ip.ring_y[k] = (int32_t)std::nearbyint((Py + rho * T.wake_sin[a]) * (double)kQ);
+                ip.ring_a[k] = a;
+            }
+            const double rw = T.r[T.wake_bucket];
+            P->energy[T.wake_bucket] += n * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
         }
     }
     ip.nseg = nseg;

@@ -9,7 +9,8 @@ namespace scwp {
 constexpr int kMaxBuckets = 64;
 constexpr int kRotN = 128;          // per-bucket phase-rotation table length
 constexpr int kSortTile = 1024;     // keys per block of the binning radix sort
-constexpr int kMaxSegments = 2 * kMaxBuckets + 2;
+constexpr int kMaxSegments = 2 * kMaxBuckets + 3;
+constexpr int kMaxRing = 64;        // ring-ripple particles emitted per frame at most
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 
@@ -107,6 +108,9 @@ struct InjectParams {
     double Px, Py, rho;
     double ca[2], sa[2];
     Segment seg[kMaxSegments];
+    // ring ripples (s = 3): positions and wake-grid directions computed on
+    // the host in float64
+    int32_t ring_x[kMaxRing], ring_y[kMaxRing], ring_a[kMaxRing];
 };
 
 struct SynthParams {

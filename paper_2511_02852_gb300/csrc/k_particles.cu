@@ -219,6 +219,10 @@ __device__ __forceinline__ void inject_body(const PatchDev& p, const InjectParam
             x = sg.s == 0 ? across : along;
             y = sg.s == 0 ? along : across;
             bd = ((uint32_t)sg.bucket << 16) | (uint32_t)j;
+        } else if (sg.s == 3) {   // ring ripples: positions given
+            x = ip.ring_x[le];
+            y = ip.ring_y[le];
+            bd = ((uint32_t)sg.bucket << 16) | (uint32_t)(ip.nth + ip.ring_a[le]);
         } else {
             const uint32_t ord = (uint32_t)(sg.arm * sg.ndir + le);
             const U4 u = philox4x32_10(ip.frame, ip.patch, (uint32_t)sg.bucket | (2u << 16), ord, ip.seed);

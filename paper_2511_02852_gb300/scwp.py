@@ -52,7 +52,8 @@ class scwp_patch_desc(C.Structure):
                 ("inject_scale", C.c_double), ("bin_cells", C.c_int32), ("emitter", C.c_int32),
                 ("obj_radius", C.c_double), ("obj_speed", C.c_double),
                 ("obj_path_radius", C.c_double), ("wake_amp", C.c_double),
-                ("wake_rate", C.c_int32), ("n_buckets", C.c_int32)]
+                ("wake_rate", C.c_int32), ("n_buckets", C.c_int32),
+                ("heave_period", C.c_double), ("ring_rate", C.c_int32)]
 
 
 class scwp_stats(C.Structure):
@@ -224,11 +225,12 @@ def spectrum_desc(cfg, stream=None, alloc=None, free=None):
 def patch_desc(p):
     d = scwp_patch_desc()
     for k in ("width", "height", "max_particles", "prefill", "bin_cells", "emitter", "wake_rate",
-              "n_buckets"):
+              "n_buckets", "ring_rate"):
         setattr(d, k, int(p.get(k, 0)))
     for k in ("origin_x", "origin_y", "cell", "band", "inject_scale", "obj_radius", "obj_speed",
               "obj_path_radius", "wake_amp"):
         setattr(d, k, float(p[k]))
+    d.heave_period = float(p.get("heave_period", 0.0))
     return d
 
 

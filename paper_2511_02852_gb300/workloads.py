@@ -46,7 +46,7 @@ def patch(**kw):
         origin_x=0.0, origin_y=0.0, cell=0.25, width=128, height=128,
         band=0.0, max_particles=0, prefill=0, inject_scale=1.0, bin_cells=0,
         emitter=0, obj_radius=4.0, obj_speed=8.0, obj_path_radius=20.0,
-        wake_amp=0.05, wake_rate=2, n_buckets=0,
+        wake_amp=0.05, wake_rate=2, n_buckets=0, heave_period=0.0, ring_rate=0,
     )
     d.update(kw)
     return d

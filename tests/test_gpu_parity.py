@@ -403,3 +403,28 @@ def test_normal_map_matches_oracle_formula():
     assert err <= 2 * d_map / cell + 1e-6
     assert np.allclose(np.sum(got.astype(np.float64) ** 2, axis=0), 1.0, atol=1e-5)
     sc.close()
+
+
+def test_ring_ripples_state_bins_and_maps_match_oracle():
+    """A heaving object (ring ripples, Sec. 4.3 vertical motion) on top of
+    its Kelvin wake: particle state and bins bit-exact, injected energy and
+    counts equal, maps within the contract."""
+    cfg = wl.small_jonswap()
+    cfg["patches"][0].update(emitter=1, wake_rate=1, heave_period=20 * cfg["dt"], ring_rate=6,
+                             obj_radius=3.0, obj_speed=2.0, obj_path_radius=6.0)
+    sc = make(cfg)
+    orc = OracleScene(cfg)
+    for f in range(1, 31):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+        if f in (5, 17, 30):
+            compare_state(sc, orc, 0)
+            compare_bins(sc, orc, 0)
+    ps = orc.patches[0]
+    assert ps.ring_total > 0
+    st = sc.stats(0)
+    assert st.injected_total == ps.injected
+    assert np.allclose([st.injected_energy[i] for i in range(st.n_buckets)], ps.energy, rtol=1e-12, atol=0)
+    ref, _ = orc.patch_maps(0)
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), "ring ripples")
+    sc.close()

@@ -308,3 +308,52 @@ def test_layered_variant_close_to_gather_off_centre():
     lay = layered_maps(ps.T.W, ps.T.H, bm, 1.0, ps.T.nb, ps.T.R)
     rel = np.linalg.norm(g[0] - lay[0]) / np.linalg.norm(g[0])
     assert rel < 0.02
+
+
+def _ring_scene(frames_per_period=60, periods=4, rate=5):
+    from paper_2511_02852_gb300 import workloads as wl
+    cfg = wl.small_jonswap()
+    p = cfg["patches"][0]
+    p.update(emitter=1, wake_rate=0, heave_period=frames_per_period * cfg["dt"], ring_rate=rate,
+             obj_radius=3.0, obj_speed=2.0, obj_path_radius=6.0, max_particles=200000)
+    return cfg, frames_per_period * periods
+
+
+def test_ring_ripples_follow_the_heave_speed_and_start_on_the_rim():
+    """Ring ripples (vertical motion, Sec. 4.3): over whole heave periods the
+    particle count approaches rate x frames x 2/pi (the mean of |cos|);
+    every ring particle starts on the object's rim, moving outward."""
+    import math
+    from oracle.particles import Q, WAKE_DIRS
+    from oracle.scene import OracleScene
+    cfg, frames = _ring_scene()
+    orc = OracleScene(cfg)
+    ps = orc.patches[0]
+    T = ps.T
+    counts = []
+    for _ in range(frames):
+        n0 = len(ps.X)
+        before = set(zip(ps.X.tolist(), ps.Y.tolist()))
+        orc.step(cfg["dt"])
+        ring = ps.J >= T.nth
+        t = ps.t
+        Rp, Om, rho = T.obj_path_radius / T.dx, T.obj_speed / T.obj_path_radius, T.obj_radius / T.dx
+        Px, Py = T.W * 0.5 + Rp * math.cos(Om * t), T.H * 0.5 + Rp * math.sin(Om * t)
+        new = [k for k in np.nonzero(ring)[0] if (int(ps.X[k]), int(ps.Y[k])) not in before]
+        fresh = [k for k in new if abs(math.hypot(ps.X[k] / Q - Px, ps.Y[k] / Q - Py) - rho) < 1e-3]
+        counts.append(len(fresh))
+        for k in fresh:   # outward: the direction points away from the object centre
+            a = int(ps.J[k] - T.nth)
+            ux, uy = math.cos(2 * math.pi * a / WAKE_DIRS), math.sin(2 * math.pi * a / WAKE_DIRS)
+            assert (ps.X[k] / Q - Px) * ux + (ps.Y[k] / Q - Py) * uy > 0.99 * rho
+    total = sum(counts)
+    expect = T.ring_rate * frames * 2.0 / math.pi
+    assert abs(total - expect) <= 0.03 * expect + 2, (total, expect)
+    assert total == ps.ring_total
+
+
+def test_ring_directions_visit_the_whole_grid():
+    """Stepping the wake grid by 2531 (odd, coprime with 4096): 4096
+    successive ring particles take 4096 distinct directions."""
+    from oracle.particles import WAKE_DIRS
+    assert len({(k * 2531) % WAKE_DIRS for k in range(WAKE_DIRS)}) == WAKE_DIRS
