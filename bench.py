@@ -426,7 +426,8 @@ def run_ours(args):
     # dominant kernel: tensor-core tile gather (k_synth_tc, with its bucket-group
     # blend epilogue), timed by the library's events around the synthesis
     # stage on the stream it launches on.  Executed tensor work: operand stages
-    # x 6 MMAs of 128x128x16 (hi*hi, hi*lo, lo*hi over two K = 16 steps).
+    # x the work of 6 MMAs of 128x128x16 (hi*hi, hi*lo, lo*hi over two K = 16
+    # steps; issued as one N = 256 and one N = 128 MMA per step).
     synth_ms = stage_ms[2] / max(frames, 1)
     evals_per_step = total_evals / args.steps
     stages = sum(sc.stats(p).mma_stages for p in range(len(cfg["patches"])))

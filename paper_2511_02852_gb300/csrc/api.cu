@@ -720,6 +720,11 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     D.amp = (float*)dalloc(ctx, ng * sizeof(float));
     D.bk = (BucketDev*)dalloc(ctx, T.nb * sizeof(BucketDev));
     D.rot = (float2*)dalloc(ctx, (size_t)T.nb * kRotN * sizeof(float2));
+    {
+        const int ts = synth_tc_tile();
+        D.phase_len = std::max((T.W + ts - 1) / ts, (T.H + ts - 1) / ts) * ts;
+        D.phase = (float2*)dalloc(ctx, (size_t)T.nb * D.phase_len * sizeof(float2));
+    }
     D.hist = (uint32_t*)dalloc(ctx, ((size_t)256 * D.nblk_s + 256) * 4);
     D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
     D.rec = (BumpRec*)dalloc(ctx, 2 * cap * sizeof(BumpRec));
@@ -753,7 +758,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         }
     }
     D.stats = (unsigned long long*)dalloc(ctx, (5 + (size_t)T.nb) * sizeof(unsigned long long));
-    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.hist &&
+    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.phase && D.hist &&
          D.offsets && D.rec && D.out && D.stats;
     if (!ok) {
         delete P;
@@ -808,6 +813,19 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
             rot[(size_t)i * kRotN + n] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
     CU(cudaMemcpyAsync(D.rot, rot.data(), rot.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
+    // per-bucket kernel phase of every texel centre X_n = n Q + Q/2: the
+    // tensor-core synthesis reads its tile rows' and columns' factors here
+    // (reduced exactly modulo 2 R_i in integers, the angle in float64)
+    std::vector<float2> phase((size_t)T.nb * D.phase_len);
+    for (int i = 0; i < T.nb; ++i) {
+        const int64_t R2 = 2 * (int64_t)T.R[i];
+        for (int n = 0; n < D.phase_len; ++n) {
+            const int64_t pm = ((int64_t)n * kQ + kQ / 2) % R2;
+            const double a = M_PI * ((double)pm / (double)T.R[i]);
+            phase[(size_t)i * D.phase_len + n] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    }
+    CU(cudaMemcpyAsync(D.phase, phase.data(), phase.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
     CU(cudaMemsetAsync(D.stats, 0, (5 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));

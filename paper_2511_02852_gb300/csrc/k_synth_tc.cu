@@ -73,14 +73,17 @@ struct __align__(1024) TcStage {   // FP16 operands
     uint16_t Ahi[2 * kTX * kKc];   // rows 0..63 1 + cos, 64..127 sin (tile columns)
     uint16_t Alo[2 * kTX * kKc];
     uint16_t Bhi[2 * kTY * kKc];   // rows 0..63 S A (1 + cos), 64..127 S A sin (tile rows)
-    uint16_t Blo[2 * kTY * kKc];
+    uint16_t Blo[2 * kTY * kKc];   // directly after Bhi: rows 128..255 of one N = 256 operand
 };
+static_assert(offsetof(TcStage, Blo) == offsetof(TcStage, Bhi) + sizeof(TcStage::Bhi),
+              "Bhi and Blo form one 256-row operand");
+static_assert(kCorrCol == 2 * kTY, "the corrections sit in the columns after the main sums");
 
 // moments of one bucket's full-cover bumps over a tile: M[i][j] =
 // sum_b A_b p_i(b) q_j(b), p = (1, cos, -sin)(pi (x_b mod 2R)/R), q likewise
 // for y (the record's phase factors)
 struct MomRec {
-    int32_t R;
+    int32_t b;      // bucket
     float m[9];
 };
 
@@ -88,6 +91,8 @@ struct MomRec {
 struct ChunkMeta {
     int n;          // bumps in the chunk (the rest of the slot holds sentinels); -1 ends the stream
     int32_t R;      // kernel radius of the chunk's bucket (Q16.16)
+    int32_t b;      // the chunk's bucket
+    int32_t pad;
 };
 
 struct TcSmem {
@@ -336,9 +341,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
     if (warp == kMmaWarp) {
         // ======================= MMA issuer ==================================
         if (lane == 0) {
+            // F32 += F16 x F16, M = 128; N = 128, or N = 256 for [Bhi; Blo]
             const uint32_t idesc =
-                (1u << 4) | ((uint32_t)(2 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);   // F32 += F16 x F16
-            uint32_t acc = 0, acc2 = 0;
+                (1u << 4) | ((uint32_t)(2 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);
+            const uint32_t idesc2 =
+                (1u << 4) | ((uint32_t)(4 * kTY >> 3) << 17) | ((uint32_t)(2 * kTX >> 4) << 24);
+            uint32_t acc = 0;
             int k = 0;   // stages consumed
             for (;; ++k) {
                 const int fs = k % kStages;
@@ -350,15 +358,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                 for (int s = 0; s < kKc / 16; ++s) {
                     const uint32_t off = (uint32_t)s * 256u;   // two 16-byte K chunks per step
                     const uint64_t ah = smem_desc((const char*)T.Ahi + off, 128, kSBO);
-                    const uint64_t al = smem_desc((const char*)T.Alo + off, 128, kSBO);
                     const uint64_t bh = smem_desc((const char*)T.Bhi + off, 128, kSBO);
-                    const uint64_t bl = smem_desc((const char*)T.Blo + off, 128, kSBO);
-                    mma_f16(tmem, ah, bh, idesc, acc);
                     if (SPLIT) {
-                        mma_f16(tmem + kCorrCol, ah, bl, idesc, acc2);
+                        // [main | corrections] (+)= Ahi [Bhi; Blo]^T in one N = 256 MMA
+                        // (Ahi read once for both), then corrections += Alo Bhi^T
+                        const uint64_t al = smem_desc((const char*)T.Alo + off, 128, kSBO);
+                        mma_f16(tmem, ah, bh, idesc2, acc);
                         mma_f16(tmem + kCorrCol, al, bh, idesc, 1);
+                    } else {
+                        mma_f16(tmem, ah, bh, idesc, acc);
                     }
-                    acc = acc2 = 1;
+                    acc = 1;
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  sa(&S.empty[fs]))
@@ -465,6 +475,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                     if (lane == 0) {
                         S.meta[slot].n = n;
                         S.meta[slot].R = bk.R;
+                        S.meta[slot].b = bi;
                     }
                     __syncwarp();
                     if (lane == 0) bar_arrive_tx(&S.rbar[slot], (uint32_t)(n * sizeof(BumpRec)));
@@ -523,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
 #pragma unroll
                     for (int d = 16; d > 0; d >>= 1) mom[q] += __shfl_xor_sync(0xffffffffu, mom[q], d);
                 if (lane == 0 && n_mom < kMaxBuckets) {
-                    S.mom[n_mom].R = bk.R;
+                    S.mom[n_mom].b = bi;
 #pragma unroll
                     for (int q = 0; q < 9; ++q) S.mom[n_mom].m[q] = mom[q];
                 }
@@ -537,6 +548,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                 if (lane == 0) {
                     S.meta[slot].n = -1;
                     S.meta[slot].R = 0;
+                    S.meta[slot].b = -1;
                 }
                 __syncwarp();
                 if (lane == 0) bar_arrive(&S.rbar[slot]);
@@ -566,21 +578,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
         int rs = 0;            // record slot of the next chunk, and its parity
         uint32_t rpar = 0u;
         int32_t R = 0;         // radius of the current bucket
+        int32_t B = -1;        // the current bucket
         float st[2] = {0.f, 0.f}, ct[2] = {1.f, 1.f};
         for (;;) {
             bool ok = bar_wait(&S.rbar[rs], rpar, err);
             if (__any_sync(0xffffffffu, !ok)) break;   // this warp stops; the others time out in turn
             const ChunkMeta m = S.meta[rs];
             if (m.n < 0) break;
-            if (m.R != R) {   // new bucket: this thread's phase factors e^{i pi (pos mod 2R) / R}
+            if (m.b != B) {   // new bucket: this thread's phase factors e^{i pi (pos mod 2R) / R}
+                B = m.b;
                 R = m.R;
-                const int64_t R2 = 2 * (int64_t)R;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    int64_t pm = (int64_t)pos[e] % R2;
-                    if (pm < 0) pm += R2;
-                    sincospif((float)((double)pm / (double)R), &st[e], &ct[e]);
-                }
+                // this thread's texels in the patch's phase table
+                const float2* ph = p.phase + (size_t)B * p.phase_len + (is_row ? ty0 : tx0) + idx;
+                const float2 a0 = ph[0], a1 = ph[32];
+                ct[0] = a0.x;
+                st[0] = a0.y;
+                ct[1] = a1.x;
+                st[1] = a1.y;
             }
             ok = bar_wait(&S.empty[fs], fpar, err);
             if (__any_sync(0xffffffffu, !ok)) break;
@@ -633,13 +647,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
             float2* wtab = reinterpret_cast<float2*>(S.st);
             for (int k = tid; k < nm * 128; k += kProdThreads) {
                 const int b = k >> 7, e = k & 127;
-                const int32_t pe = e < 64 ? Ylo + e * kQi : Xlo + (e - 64) * kQi;
-                const int64_t R2 = 2 * (int64_t)S.mom[b].R;
-                int64_t pm = (int64_t)pe % R2;
-                if (pm < 0) pm += R2;
-                float sn, cs;
-                sincospif((float)((double)pm / (double)S.mom[b].R), &sn, &cs);
-                wtab[k] = make_float2(cs, sn);
+                const int t = e < 64 ? ty0 + e : tx0 + (e - 64);   // texel row or column
+                wtab[k] = p.phase[(size_t)S.mom[b].b * p.phase_len + t];
             }
             prod_sync();
         }
@@ -692,16 +701,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
                     val[j] = fmaf(fs, t, val[j]);
                 }
             }
-            if (x >= sp.W) continue;
+            // read once per block: the global stores below may alias shared
+            // memory as far as the compiler knows
+            const int Wd = sp.W, Hd = sp.H;
+            if (x >= Wd) continue;
+            // bucket groups: this group's partial plane; one group: the blended map
+            float* const dst = (G > 1 ? p.partial + ((size_t)g * 3 + f) * plane : p.out + (size_t)f * plane) + x;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int y = y0 + j;
-                if (y < sp.H) {
-                    const float v = val[j];
-                    const size_t o = (size_t)y * sp.W + x;
-                    if (G > 1) p.partial[((size_t)g * 3 + f) * plane + o] = v;
-                    else p.out[(size_t)f * plane + o] = blend1(sp, x, y, f, v);
-                }
+                if (y < Hd) dst[(size_t)y * Wd] = G > 1 ? val[j] : blend1(sp, x, y, f, val[j]);
             }
         }
     }
