@@ -64,8 +64,18 @@ enum { SCWP_FIELD_H = 0, SCWP_FIELD_DX = 1, SCWP_FIELD_DY = 2 };
  *   SCWP_SYNTH_GATHER_FP16  the tensor-core gather with single FP16 operands
  *                           (one MMA per step instead of three), FP32
  *                           accumulation; the reduced-precision contract
- *                           (2e-3 Hs); positions and bins stay exact. */
-enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1, SCWP_SYNTH_GATHER_FP32 = 2, SCWP_SYNTH_GATHER_FP16 = 3 };
+ *                           (2e-3 Hs); positions and bins stay exact.
+ *   SCWP_SYNTH_SAT          the same per-bucket sums (Sec. 4.2, kernel
+ *                           reading O11/O12) through summed-area tables: on
+ *                           its support a bump's raised-cosine factors are
+ *                           rank 3 in (texel, bump), so per (tile, bucket)
+ *                           the maps are a 3 x 3 contraction of 2-D prefix
+ *                           sums of the bumps' support-box corners (integer
+ *                           events, exact prefix sums, FP32 contraction);
+ *                           the FP32 contract; the cost no longer grows with
+ *                           the bumps that cover a texel. */
+enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1, SCWP_SYNTH_GATHER_FP32 = 2, SCWP_SYNTH_GATHER_FP16 = 3,
+       SCWP_SYNTH_SAT = 4 };
 
 #define SCWP_MAX_BUCKETS 64
 #define SCWP_MAX_THETA 256

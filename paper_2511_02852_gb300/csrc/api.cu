@@ -55,6 +55,12 @@ struct PatchHost {
     BlendSpan* d_spans = nullptr;
     int partial_planes = 1;           // bucket-group partial planes allocated
     int tc_slots = 0;                 // resident CTA slots the plan assumed
+    std::vector<TcItem> sat_items;    // summed-area synthesis items of this patch, launch order
+    std::vector<BlendSpan> sat_spans;
+    TcItem* d_sat_items = nullptr;
+    BlendSpan* d_sat_spans = nullptr;
+    int sat_groups = 1;
+    int sat_slots = 0;
 };
 
 // A frame (or a scene's part of a frame) captured as CUDA graphs, one per
@@ -122,6 +128,14 @@ struct scwp_ctx {
     std::vector<BlendSpan> b_spans;
     TcItem* d_bitems = nullptr;
     BlendSpan* d_bspans = nullptr;
+    // the batched plan of the summed-area synthesis
+    int sat_slots = 0;
+    std::vector<TcItem> s_items;
+    std::vector<BlendSpan> s_spans;
+    TcItem* d_sitems = nullptr;
+    BlendSpan* d_sspans = nullptr;
+    double s_makespan = 0.0;
+    std::vector<double> s_work;
     double b_makespan = 0.0;
     // captured batched frames (one per parity of the particle buffers)
     FrameGraph gfull;                 // whole batched frames (scwp_step)
@@ -348,6 +362,40 @@ std::vector<double> tile_bucket_stages(const PatchHost& P, int& tiles) {
     return est;
 }
 
+// Work of the summed-area synthesis per (tile, bucket), in the same stage
+// units: a fixed part (three rounds of clearing, two prefix passes and the
+// 3 x 3 contraction over the tile's texels) plus one part per candidate bump
+// of the bins that reach the tile (its corner events).
+constexpr double kSatBucketUs = 2.0;
+constexpr double kSatBumpUs = 0.0008;
+
+std::vector<double> tile_bucket_sat(const PatchHost& P, int& tiles) {
+    const PatchTablesHost& T = P.T;
+    const int ts = synth_sat_tile();
+    const int ntx = (T.W + ts - 1) / ts, nty = (T.H + ts - 1) / ts;
+    tiles = ntx * nty;
+    const double total = 2.0 * (P.d.prefill > 0 ? (double)P.d.prefill : 0.5 * (double)P.d.max_particles);
+    std::vector<double> w(T.nb);
+    double sw = 0.0;
+    for (int i = 0; i < T.nb; ++i) {
+        w[i] = ((double)T.W * kQ + 2.0 * T.R[i]) / ((double)T.R[i] * (double)T.R[i]);
+        sw += w[i];
+    }
+    std::vector<double> est((size_t)tiles * T.nb);
+    for (int i = 0; i < T.nb; ++i) {
+        const double r = (double)T.R[i] / kQ, c = (double)P.bin_cells[i];
+        const double dens = total * w[i] / sw / ((T.W + 2 * r) * (T.H + 2 * r));
+        for (int t = 0; t < tiles; ++t) {
+            const double x0 = (t % ntx) * ts - r, x1 = (t % ntx + 1) * ts + r;
+            const double y0 = (t / ntx) * ts - r, y1 = (t / ntx + 1) * ts + r;
+            const double ax = std::max(0.0, std::min(x1 + c, T.W + r) - std::max(x0, -r));
+            const double ay = std::max(0.0, std::min(y1 + c, T.H + r) - std::max(y0, -r));
+            est[(size_t)t * T.nb + i] = (kSatBucketUs + dens * ax * ay * kSatBumpUs) / kStageUs;
+        }
+    }
+    return est;
+}
+
 double item_work(const std::vector<double>& est, int nb, int t, int g, int G) {
     double s = kItemStages;
     for (int i = (g * nb) / G; i < ((g + 1) * nb) / G; ++i) s += est[(size_t)t * nb + i];
@@ -379,11 +427,13 @@ std::vector<BlendSpan> blend_spans(const PatchHost& P, int G) {
 
 // Plan of one patch launched alone: G minimises the simulated makespan over
 // the device's resident CTA slots plus the traffic of the group-sum blend.
-void plan_patch(PatchHost& P, int slots) {
+void plan_patch(PatchHost& P, int slots, bool sat = false) {
     int tiles = 0;
-    const std::vector<double> est = tile_bucket_stages(P, tiles);
+    const std::vector<double> est = sat ? tile_bucket_sat(P, tiles) : tile_bucket_stages(P, tiles);
     const int nb = P.T.nb;
     double best_cost = 0.0;
+    int& groups = sat ? P.sat_groups : P.dev.groups_tc;
+    std::vector<TcItem>& plan = sat ? P.sat_items : P.tc_items;
     for (int G = 1; G <= std::min(nb, 16); ++G) {
         std::vector<double> work((size_t)tiles * G);
         for (int t = 0; t < tiles; ++t)
@@ -395,26 +445,26 @@ void plan_patch(PatchHost& P, int slots) {
         const double cost = makespan(work, order, slots) * kStageUs + blend;
         if (G == 1 || cost < best_cost) {
             best_cost = cost;
-            P.dev.groups_tc = G;
-            P.tc_items.clear();
-            for (int k : order) P.tc_items.push_back(TcItem{P.index, k / G, k % G, G});
+            groups = G;
+            plan.clear();
+            for (int k : order) plan.push_back(TcItem{P.index, k / G, k % G, G});
         }
     }
-    P.tc_spans = blend_spans(P, P.dev.groups_tc);
+    (sat ? P.sat_spans : P.tc_spans) = blend_spans(P, groups);
 }
 
 // Plan of all patches in one launch: each patch's G is the smallest that
 // keeps its largest item under a quarter of the average per-slot load, and
 // all items of all patches run heaviest first.
 void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vector<BlendSpan>& spans,
-                  double& model_makespan, std::vector<double>& item_work_out) {
+                  double& model_makespan, std::vector<double>& item_work_out, bool sat = false) {
     items.clear();
     spans.clear();
     std::vector<std::vector<double>> est(ctx->patches.size());
     std::vector<int> tiles(ctx->patches.size());
     double total = 0.0;
     for (size_t k = 0; k < ctx->patches.size(); ++k) {
-        est[k] = tile_bucket_stages(*ctx->patches[k], tiles[k]);
+        est[k] = sat ? tile_bucket_sat(*ctx->patches[k], tiles[k]) : tile_bucket_stages(*ctx->patches[k], tiles[k]);
         for (double e : est[k]) total += e;
         total += kItemStages * tiles[k];
     }
@@ -558,6 +608,15 @@ scwp_status sync_synth(scwp_ctx* ctx) {
         if (!ctx->b_spans.empty())
             CU(cudaMemcpyAsync(ctx->d_bspans, ctx->b_spans.data(), ctx->b_spans.size() * sizeof(BlendSpan),
                                cudaMemcpyHostToDevice, ctx->st));
+        plan_batched(ctx, ctx->sat_slots, ctx->s_items, ctx->s_spans, ctx->s_makespan, ctx->s_work, true);
+        ctx->d_sitems = (TcItem*)dalloc(ctx, std::max<size_t>(1, ctx->s_items.size()) * sizeof(TcItem));
+        ctx->d_sspans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, ctx->s_spans.size()) * sizeof(BlendSpan));
+        if (!ctx->d_sitems || !ctx->d_sspans) return fail(ctx, SCWP_E_NOMEM, "batched plan");
+        CU(cudaMemcpyAsync(ctx->d_sitems, ctx->s_items.data(), ctx->s_items.size() * sizeof(TcItem),
+                           cudaMemcpyHostToDevice, ctx->st));
+        if (!ctx->s_spans.empty())
+            CU(cudaMemcpyAsync(ctx->d_sspans, ctx->s_spans.data(), ctx->s_spans.size() * sizeof(BlendSpan),
+                               cudaMemcpyHostToDevice, ctx->st));
     }
     // the host vectors are copied before they go out of scope
     CU(cudaStreamSynchronize(ctx->st));
@@ -567,6 +626,19 @@ scwp_status sync_synth(scwp_ctx* ctx) {
 
 scwp_status synthesize(scwp_ctx* ctx, int mode) {
     const bool split = mode != SCWP_SYNTH_GATHER_FP16;
+    if (mode == SCWP_SYNTH_SAT) {
+        scwp_status s = sync_synth(ctx);
+        if (s != SCWP_OK) return s;
+        if (ctx->batched) {
+            CU(launch_synth_sat(ctx->d_sitems, (int)ctx->s_items.size(), ctx->d_pdevs, ctx->d_sps, ctx->d_sspans,
+                                (int)ctx->s_spans.size(), ctx->st));
+        } else {
+            for (PatchHost* P : ctx->patches)
+                CU(launch_synth_sat(P->d_sat_items, (int)P->sat_items.size(), ctx->d_pdevs, ctx->d_sps,
+                                    P->d_sat_spans, (int)P->sat_spans.size(), ctx->st));
+        }
+        return SCWP_OK;
+    }
     if (mode == SCWP_SYNTH_GATHER || mode == SCWP_SYNTH_GATHER_FP16) {
         scwp_status s = sync_synth(ctx);
         if (s != SCWP_OK) return s;
@@ -747,10 +819,16 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         ctx->slots = P->tc_slots;
         D.patch = P->index;
         plan_patch(*P, P->tc_slots);
+        const int sat_per_sm = synth_sat_ctas_per_sm();
+        P->sat_slots = sms * (sat_per_sm > 0 ? sat_per_sm : 1);
+        ctx->sat_slots = P->sat_slots;
+        plan_patch(*P, P->sat_slots, true);
         P->d_items = (TcItem*)dalloc(ctx, P->tc_items.size() * sizeof(TcItem));
         P->d_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, P->tc_spans.size()) * sizeof(BlendSpan));
-        ok = ok && P->d_items && P->d_spans;
-        const int G = D.groups > D.groups_tc ? D.groups : D.groups_tc;
+        P->d_sat_items = (TcItem*)dalloc(ctx, P->sat_items.size() * sizeof(TcItem));
+        P->d_sat_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, P->sat_spans.size()) * sizeof(BlendSpan));
+        ok = ok && P->d_items && P->d_spans && P->d_sat_items && P->d_sat_spans;
+        const int G = std::max(std::max(D.groups, D.groups_tc), P->sat_groups);
         P->partial_planes = G;
         if (G > 1) {
             D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
@@ -804,6 +882,11 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
                        ctx->st));
     if (!P->tc_spans.empty())
         CU(cudaMemcpyAsync(P->d_spans, P->tc_spans.data(), P->tc_spans.size() * sizeof(BlendSpan),
+                           cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemcpyAsync(P->d_sat_items, P->sat_items.data(), P->sat_items.size() * sizeof(TcItem),
+                       cudaMemcpyHostToDevice, ctx->st));
+    if (!P->sat_spans.empty())
+        CU(cudaMemcpyAsync(P->d_sat_spans, P->sat_spans.data(), P->sat_spans.size() * sizeof(BlendSpan),
                            cudaMemcpyHostToDevice, ctx->st));
     // per-bucket phase steps of n texels: e^{i pi n Q / R_i}, n < kRotN
     std::vector<float2> rot((size_t)T.nb * kRotN);
@@ -1202,7 +1285,8 @@ static scwp_status step_impl(scwp_ctx* ctx, double dt) {
     if (s != SCWP_OK) return s;
     // batched frames replay a captured graph unless stage timing is on
     if (ctx->batched && !ctx->timing && ctx->patches.size() <= 64 &&
-        (ctx->synth_mode == SCWP_SYNTH_GATHER || ctx->synth_mode == SCWP_SYNTH_GATHER_FP16))
+        (ctx->synth_mode == SCWP_SYNTH_GATHER || ctx->synth_mode == SCWP_SYNTH_GATHER_FP16 ||
+         ctx->synth_mode == SCWP_SYNTH_SAT))
         return run_graph(ctx, ctx->gfull, ctx->ips, ctx->st, true);
     FrameEvents* fe = nullptr;
     if (ctx->timing) {
@@ -1224,7 +1308,7 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode) {
     if (s != SCWP_OK) return s;
     const long long before = launches_total();
     if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32 &&
-        mode != SCWP_SYNTH_GATHER_FP16)
+        mode != SCWP_SYNTH_GATHER_FP16 && mode != SCWP_SYNTH_SAT)
         return fail(ctx, SCWP_E_INVALID, "mode");
     if (!ctx->bg_valid) {
         CU(launch_background(ctx->bg, ctx->t, ctx->st));
@@ -1264,7 +1348,7 @@ scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
     if (mode != SCWP_SYNTH_GATHER && mode != SCWP_SYNTH_LAYERED && mode != SCWP_SYNTH_GATHER_FP32 &&
-        mode != SCWP_SYNTH_GATHER_FP16)
+        mode != SCWP_SYNTH_GATHER_FP16 && mode != SCWP_SYNTH_SAT)
         return fail(ctx, SCWP_E_INVALID, "mode");
     graph_reset(ctx);
     ctx->synth_mode = mode;

@@ -148,6 +148,13 @@ cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaSt
 // otherwise single FP16 operands (1 MMA per K step, the FP16 contract).
 cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
                             const BlendSpan* spans, int n_spans, cudaStream_t st, bool split = true);
+// Summed-area synthesis (the same sums through 2-D difference arrays of the
+// kernel's rank-3 factors) of `n_items` items in one launch, then the
+// group-sum blend, like launch_synth_tc.
+cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
+                             const BlendSpan* spans, int n_spans, cudaStream_t st);
+int synth_sat_tile();
+int synth_sat_ctas_per_sm();
 // tensor-core synthesis geometry: tile side (texels), bumps per operand stage,
 // and resident CTAs per SM (0 on error)
 int synth_tc_tile();

@@ -1,0 +1,319 @@
+// Summed-area synthesis of the wave-particle maps: the per-bucket kernel
+// sums of Sec. 4.2 (kernel reading O11, analytic displacement O12) computed
+// from the structure of the raised-cosine kernel instead of one evaluation
+// per (bump, texel) pair.
+//
+// On its support |X - x_b| < R a bump's x factor is
+//     1 + cos(pi (X - x_b)/R) = u(X) . p_b,   sin(pi (X - x_b)/R) = u'(X) . p_b,
+// with u(X) = (1, cos a_X, -sin a_X), u'(X) = (0, sin a_X, cos a_X),
+// a_X = pi (X mod 2R)/R and p_b = (1, c_b, s_b) = (1, e^{-i pi (x_b mod 2R)/R})
+// (the bump record's phase pair); likewise v(Y), v'(Y), q_b for y.  Within a
+// tile the support is a box [alpha_b, beta_b) x [gamma_b, delta_b) of texel
+// indices, so
+//     h(X, Y)  = 1/4     sum_ij u_i(X)  v_j(Y)  S_ij(X, Y),
+//     Dx(X, Y) = lam/4   sum_ij u'_i(X) v_j(Y)  S_ij(X, Y),
+//     Dy(X, Y) = lam/4   sum_ij u_i(X)  v'_j(Y) S_ij(X, Y),
+//     S_ij(X, Y) = sum_b A_b p_i(b) q_j(b) [alpha_b <= X < beta_b][gamma_b <= Y < delta_b],
+// and S_ij is the 2-D inclusive prefix sum of a difference array that holds
+// +-A_b p_i q_j at the four corners of each box (corners at index 64 fall
+// outside the tile and are dropped).  These are the same sums as the direct
+// gather in another association.  Per (tile, bucket) the work is four corner
+// events per bump, two prefix passes and a 3 x 3 contraction per texel: it
+// no longer grows with the number of bumps covering a texel.
+//
+// Exactness of the prefix sums: the corner weights are rounded once to
+// 32-bit integers with a per-(tile, bucket) scale 2^30 / (1.001 sum_b |A_b|)
+// over the tile's candidate bumps.  Every S_ij then fits in 31 bits, the
+// events accumulate exactly in any order (integer shared-memory atomics:
+// deterministic results), and the prefix sums are exact modulo 2^32 (their
+// intermediate values may wrap; the final ones do not).  The contraction is
+// FP32.  The rounding error of a weight is at most 2^-31 sum |A|, far below
+// the FP32 map tolerance.
+//
+// One CTA per (tile, bucket group) item, 512 threads, two CTAs per SM.  The
+// nine S components are processed in three groups of three (fixed p_i), so
+// the difference array takes 48 KB of shared memory.
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "blend_dev.cuh"
+#include "internal.h"
+
+namespace scwp {
+namespace {
+
+constexpr int kT = 64;                       // tile side in texels
+constexpr int kSatThreads = 512;
+constexpr int kSatWarps = kSatThreads / 32;
+constexpr int kSegs = kSatThreads / kT;      // row segments of the column pass
+constexpr int kSegRows = kT / kSegs;         // rows per segment
+constexpr int kSatMaxRows = 512;             // bin rows of one bucket that reach a tile
+constexpr int32_t kQs = 65536, kHalfs = 32768;
+static_assert(kSegs * kSegRows == kT && kSegs == 8, "column-pass mapping");
+
+struct SatSmem {
+    uint32_t E[3][kT * kT];               // difference array, then prefix sums (one component group)
+    uint32_t seg[kSegs][3][kT];           // column sums of each row segment
+    float2 ph[2 * kT];                    // the bucket's texel phases (cos, sin) a: rows, then columns
+    int32_t rs[kSatMaxRows], rl[kSatMaxRows];   // candidate record range of each bin row
+    float red[kSatWarps];                 // per-warp sums of |A|
+    alignas(16) unsigned char pd[sizeof(PatchDev)];
+    alignas(16) unsigned char spd[sizeof(SynthParams)];
+};
+
+// element (row y, column x) of a 64 x 64 plane: columns XOR-swizzled by the
+// row so that a warp walking a row (one row per lane) or a column (one
+// column per lane) touches 32 different banks
+__device__ __forceinline__ int sw(int y, int x) { return y * kT + (x ^ (y & 31)); }
+
+__device__ __forceinline__ int clamp_t(int t) { return min(max(t, 0), kT); }
+
+// the three components of one corner event
+__device__ __forceinline__ void event3(SatSmem& S, int x, int y, uint32_t w0, uint32_t w1, uint32_t w2) {
+    const int o = sw(y, x);
+    atomicAdd(&S.E[0][o], w0);
+    atomicAdd(&S.E[1][o], w1);
+    atomicAdd(&S.E[2][o], w2);
+}
+
+__global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* items, const PatchDev* pdevs,
+                                                            const SynthParams* sps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SatSmem& S = *reinterpret_cast<SatSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcItem it = items[blockIdx.x];
+    {
+        static_assert(sizeof(PatchDev) % 4 == 0 && sizeof(SynthParams) % 4 == 0, "descriptor copy");
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(pdevs + it.patch);
+        const uint32_t* b = reinterpret_cast<const uint32_t*>(sps + it.patch);
+        for (int k = tid; k < (int)(sizeof(PatchDev) / 4); k += kSatThreads) reinterpret_cast<uint32_t*>(S.pd)[k] = a[k];
+        for (int k = tid; k < (int)(sizeof(SynthParams) / 4); k += kSatThreads)
+            reinterpret_cast<uint32_t*>(S.spd)[k] = b[k];
+    }
+    __syncthreads();
+    const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
+    const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
+    const int G = it.groups, g = it.group;
+    const int ntx = (sp.W + kT - 1) / kT;
+    const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
+    const int b_begin = max((g * sp.nb) / G, sp.b_lo);
+    const int b_end = min(((g + 1) * sp.nb) / G, sp.b_hi);
+    // Q16.16 centres of the tile's first and last texel columns and rows
+    const int32_t X0 = tx0 * kQs + kHalfs, X1 = X0 + (kT - 1) * kQs;
+    const int32_t Y0 = ty0 * kQs + kHalfs, Y1 = Y0 + (kT - 1) * kQs;
+    const float lamq = 0.5f * sp.lam_half;   // lam / 4
+
+    // column pass: this thread owns texel column cx of rows sg*8 .. sg*8 + 7
+    const int cx = tid & (kT - 1), sg = tid / kT;
+    float ah[kSegRows], adx[kSegRows], ady[kSegRows];
+#pragma unroll
+    for (int r = 0; r < kSegRows; ++r) ah[r] = adx[r] = ady[r] = 0.f;
+
+    for (int bi = b_begin; bi < b_end; ++bi) {
+        const BucketDev bk = p.bk[bi];
+        // bins whose bumps can reach the tile (x_b + R in [bx C, (bx + 1) C))
+        int bx_lo = (int)((int64_t)X0 / bk.C);
+        int bx_hi = (int)(((int64_t)X1 + 2 * (int64_t)bk.R - 1) / bk.C);
+        int by_lo = (int)((int64_t)Y0 / bk.C);
+        int by_hi = (int)(((int64_t)Y1 + 2 * (int64_t)bk.R - 1) / bk.C);
+        bx_hi = min(bx_hi, bk.nbx - 1);
+        by_hi = min(by_hi, bk.nby - 1);
+        if (bx_lo > bx_hi || by_lo > by_hi) continue;
+        const int nrows = by_hi - by_lo + 1;
+        if (nrows > kSatMaxRows) {
+            if (tid == 0) atomicOr(p.stats + 2, (unsigned long long)kErrCapacity);
+            continue;
+        }
+        __syncthreads();   // the previous bucket is done with rs, rl, ph and E
+        for (int r = tid; r < nrows; r += kSatThreads) {
+            const int key0 = bk.base + (by_lo + r) * bk.nbx;
+            const int s0 = (int)p.offsets[key0 + bx_lo];
+            S.rs[r] = s0;
+            S.rl[r] = (int)p.offsets[key0 + bx_hi + 1] - s0;
+        }
+        for (int k = tid; k < 2 * kT; k += kSatThreads)
+            S.ph[k] = p.phase[(size_t)bi * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
+        __syncthreads();
+        // sum of |A| over the candidates: warp w takes rows w, w + 16, ...,
+        // lanes stride the row; a fixed order, so every CTA gets the same scale
+        float sa = 0.f;
+        for (int r = warp; r < nrows; r += kSatWarps) {
+            const int s0 = S.rs[r], l = S.rl[r];
+            for (int k = lane; k < l; k += 32) sa += fabsf(p.rec[s0 + k].amp);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, d);
+        if (lane == 0) S.red[warp] = sa;
+        __syncthreads();
+        float tot = 0.f;
+        for (int w = 0; w < kSatWarps; ++w) tot += S.red[w];
+        if (!(tot > 0.f)) continue;   // no bump of this bucket reaches the tile
+        const float bound = 1.001f * tot;                 // >= every |S_ij|
+        const float scale = 1073741824.f / bound;         // 2^30 / bound
+        const float inv = bound * (1.f / 1073741824.f);   // 1 / scale (exact power-of-two step)
+        const float2 ux = S.ph[kT + cx];                  // (cos a_X, sin a_X) of this column
+
+        for (int i = 0; i < 3; ++i) {   // component group p_i: S_i0, S_i1, S_i2
+            for (int k = tid; k < 3 * kT * kT / 4; k += kSatThreads)
+                reinterpret_cast<uint4*>(&S.E[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
+            __syncthreads();
+            // ---- corner events
+            for (int r = warp; r < nrows; r += kSatWarps) {
+                const int s0 = S.rs[r], l = S.rl[r];
+                for (int base = 0; base < l; base += 32) {
+                    const int k = base + lane;
+                    bool ov = false;
+                    int a = 0, b = 0, c = 0, d = 0;
+                    uint32_t w0 = 0u, w1 = 0u, w2 = 0u;
+                    if (k < l) {
+                        const float4* rp = reinterpret_cast<const float4*>(p.rec + s0 + k);
+                        const float4 rx = rp[0];   // x, cos, sin, id
+                        const float4 ry = rp[1];   // y, cos, sin, A
+                        const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
+                        // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
+                        a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
+                        b = clamp_t(-((X0 - xb - bk.R) >> 16));
+                        c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
+                        d = clamp_t(-((Y0 - yb - bk.R) >> 16));
+                        ov = a < b && c < d;
+                        if (ov) {
+                            const float pi = i == 0 ? 1.f : (i == 1 ? rx.y : rx.z);
+                            const float m = ry.w * pi * scale;
+                            w0 = (uint32_t)__float2int_rn(m);
+                            w1 = (uint32_t)__float2int_rn(m * ry.y);
+                            w2 = (uint32_t)__float2int_rn(m * ry.z);
+                        }
+                    }
+                    // the corner (0, 0) is shared by every bump that covers the
+                    // tile's first texel: summed over the warp first
+                    const bool z = ov && a == 0 && c == 0;
+                    if (__any_sync(0xffffffffu, z)) {
+                        const uint32_t v0 = __reduce_add_sync(0xffffffffu, z ? w0 : 0u);
+                        const uint32_t v1 = __reduce_add_sync(0xffffffffu, z ? w1 : 0u);
+                        const uint32_t v2 = __reduce_add_sync(0xffffffffu, z ? w2 : 0u);
+                        if (lane == 0) event3(S, 0, 0, v0, v1, v2);
+                    }
+                    if (ov) {
+                        if (!z) event3(S, a, c, w0, w1, w2);
+                        if (b < kT) event3(S, b, c, 0u - w0, 0u - w1, 0u - w2);
+                        if (d < kT) event3(S, a, d, 0u - w0, 0u - w1, 0u - w2);
+                        if (b < kT && d < kT) event3(S, b, d, w0, w1, w2);
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- prefix along x: one row of one component per thread
+            if (tid < 3 * kT) {
+                uint32_t* E = S.E[tid / kT];
+                const int y = tid % kT;
+                uint32_t run = 0u;
+#pragma unroll 16
+                for (int x = 0; x < kT; ++x) {
+                    const int o = sw(y, x);
+                    run += E[o];
+                    E[o] = run;
+                }
+            }
+            __syncthreads();
+            // ---- prefix along y, in two steps: segment column sums ...
+            {
+                uint32_t s0 = 0u, s1 = 0u, s2 = 0u;
+#pragma unroll
+                for (int r = 0; r < kSegRows; ++r) {
+                    const int o = sw(sg * kSegRows + r, cx);
+                    s0 += S.E[0][o];
+                    s1 += S.E[1][o];
+                    s2 += S.E[2][o];
+                }
+                S.seg[sg][0][cx] = s0;
+                S.seg[sg][1][cx] = s1;
+                S.seg[sg][2][cx] = s2;
+            }
+            __syncthreads();
+            // ... then this segment's rows from the sums of the segments above
+            uint32_t run0 = 0u, run1 = 0u, run2 = 0u;
+            for (int s = 0; s < sg; ++s) {
+                run0 += S.seg[s][0][cx];
+                run1 += S.seg[s][1][cx];
+                run2 += S.seg[s][2][cx];
+            }
+            // u_i(X), u'_i(X) with the constant factors and 1 / scale
+            const float u = i == 0 ? 1.f : (i == 1 ? ux.x : -ux.y);
+            const float up = i == 0 ? 0.f : (i == 1 ? ux.y : ux.x);
+            const float ku = 0.25f * u * inv, kup = lamq * up * inv, kud = lamq * u * inv;
+#pragma unroll
+            for (int r = 0; r < kSegRows; ++r) {
+                const int y = sg * kSegRows + r;
+                const int o = sw(y, cx);
+                run0 += S.E[0][o];
+                run1 += S.E[1][o];
+                run2 += S.E[2][o];
+                const float2 vy = S.ph[y];   // (cos a_Y, sin a_Y)
+                const float f0 = (float)(int32_t)run0, f1 = (float)(int32_t)run1, f2 = (float)(int32_t)run2;
+                const float t = fmaf(-vy.y, f2, fmaf(vy.x, f1, f0));   // v . S_i.
+                const float tp = fmaf(vy.y, f1, vy.x * f2);            // v' . S_i.
+                ah[r] = fmaf(ku, t, ah[r]);
+                adx[r] = fmaf(kup, t, adx[r]);
+                ady[r] = fmaf(kud, tp, ady[r]);
+            }
+            __syncthreads();   // E and seg are rewritten by the next group
+        }
+    }
+
+    // ---- store: the group's partial planes, or (one group) the blended maps
+    const int x = tx0 + cx;
+    if (x >= sp.W) return;
+    const size_t plane = (size_t)sp.W * sp.H;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        float* const dst = (G > 1 ? p.partial + ((size_t)g * 3 + f) * plane : p.out + (size_t)f * plane) + x;
+#pragma unroll
+        for (int r = 0; r < kSegRows; ++r) {
+            const int y = ty0 + sg * kSegRows + r;
+            const float v = f == 0 ? ah[r] : (f == 1 ? adx[r] : ady[r]);
+            if (y < sp.H) dst[(size_t)y * sp.W] = G > 1 ? v : blend1(sp, x, y, f, v);
+        }
+    }
+}
+
+cudaError_t sat_attributes() {
+    return cudaFuncSetAttribute(k_synth_sat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SatSmem));
+}
+
+}  // namespace
+
+int synth_sat_tile() { return kT; }
+
+// resident CTAs per SM from the SM's limits (shared memory, registers, threads)
+int synth_sat_ctas_per_sm() {
+    if (sat_attributes() != cudaSuccess) return 0;
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
+    cudaFuncAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&a, k_synth_sat) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 0;
+    const int warps = kSatThreads / 32;
+    const int regs_warp = ((a.numRegs * 32 + 255) / 256) * 256;
+    int n = smem_sm / (int)(sizeof(SatSmem) + a.sharedSizeBytes + resv);
+    n = min(n, regs_sm / (regs_warp * warps));
+    n = min(n, thr_sm / kSatThreads);
+    return n;
+}
+
+cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
+                             const BlendSpan* spans, int n_spans, cudaStream_t st) {
+    cudaError_t e = sat_attributes();
+    if (e != cudaSuccess) return e;
+    if (n_items > 0) {
+        k_synth_sat<<<n_items, kSatThreads, sizeof(SatSmem), st>>>(items, pdevs, sps);
+        count_launches(1);
+    }
+    if (n_spans > 0) return launch_blend_spans(spans, n_spans, pdevs, sps, st);
+    return cudaGetLastError();
+}
+
+}  // namespace scwp

@@ -22,7 +22,7 @@ from . import _build
 MAX_BUCKETS = 64
 WAKE_DIRS = 4096
 FIELD_H, FIELD_DX, FIELD_DY = 0, 1, 2
-SYNTH_GATHER, SYNTH_LAYERED, SYNTH_GATHER_FP32, SYNTH_GATHER_FP16 = 0, 1, 2, 3
+SYNTH_GATHER, SYNTH_LAYERED, SYNTH_GATHER_FP32, SYNTH_GATHER_FP16, SYNTH_SAT = 0, 1, 2, 3, 4
 (TAB_OMEGA, TAB_K, TAB_C, TAB_R, TAB_E, TAB_EDGES, TAB_AMP, TAB_RQ, TAB_VX, TAB_VY, TAB_QX,
  TAB_QY, TAB_WAKE_VX, TAB_WAKE_VY, TAB_WAKE_QX, TAB_WAKE_QY, TAB_CARRY) = range(17)
 STATUS = {0: "SCWP_OK", 1: "SCWP_E_INVALID", 2: "SCWP_E_NOMEM", 3: "SCWP_E_CAPACITY",
