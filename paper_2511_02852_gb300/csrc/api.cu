@@ -434,7 +434,12 @@ void plan_patch(PatchHost& P, int slots, bool sat = false) {
     double best_cost = 0.0;
     int& groups = sat ? P.sat_groups : P.dev.groups_tc;
     std::vector<TcItem>& plan = sat ? P.sat_items : P.tc_items;
-    for (int G = 1; G <= std::min(nb, 16); ++G) {
+    // the summed-area items cost about the same per bucket; the smallest G
+    // that gives three waves over the slots, as far as the buckets allow
+    int g_lo = 1;
+    if (sat)
+        while (g_lo < std::min(nb, 16) && (double)tiles * g_lo < 3.0 * slots) ++g_lo;
+    for (int G = g_lo; G <= std::min(nb, 16); ++G) {
         std::vector<double> work((size_t)tiles * G);
         for (int t = 0; t < tiles; ++t)
             for (int g = 0; g < G; ++g) work[(size_t)t * G + g] = item_work(est, nb, t, g, G);
@@ -443,7 +448,7 @@ void plan_patch(PatchHost& P, int slots, bool sat = false) {
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
         const double blend = G > 1 ? (G + 1) * 12.0 * P.T.W * P.T.H / kHbmBytesPerUs : 0.0;
         const double cost = makespan(work, order, slots) * kStageUs + blend;
-        if (G == 1 || cost < best_cost) {
+        if (G == g_lo || cost < best_cost) {
             best_cost = cost;
             groups = G;
             plan.clear();
@@ -796,6 +801,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         const int ts = synth_tc_tile();
         D.phase_len = std::max((T.W + ts - 1) / ts, (T.H + ts - 1) / ts) * ts;
         D.phase = (float2*)dalloc(ctx, (size_t)T.nb * D.phase_len * sizeof(float2));
+        D.amax = (float*)dalloc(ctx, (size_t)T.nb * sizeof(float));
     }
     D.hist = (uint32_t*)dalloc(ctx, ((size_t)256 * D.nblk_s + 256) * 4);
     D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
@@ -836,7 +842,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         }
     }
     D.stats = (unsigned long long*)dalloc(ctx, (5 + (size_t)T.nb) * sizeof(unsigned long long));
-    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.phase && D.hist &&
+    ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.phase && D.amax && D.hist &&
          D.offsets && D.rec && D.out && D.stats;
     if (!ok) {
         delete P;
@@ -909,6 +915,14 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         }
     }
     CU(cudaMemcpyAsync(D.phase, phase.data(), phase.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
+    // |A| bound per bucket: its directions' amplitudes and, with an emitter,
+    // the wake amplitude (wake directions may sit in any bucket)
+    std::vector<float> amax(T.nb, 0.f);
+    for (int i = 0; i < T.nb; ++i) {
+        for (int j = 0; j < T.nth; ++j) amax[i] = std::max(amax[i], std::fabs(ampf[(size_t)i * T.nth + j]));
+        if (D.emitter) amax[i] = std::max(amax[i], std::fabs(D.wake_amp));
+    }
+    CU(cudaMemcpyAsync(D.amax, amax.data(), amax.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
     CU(cudaMemsetAsync(D.stats, 0, (5 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));

@@ -57,6 +57,7 @@ struct PatchDev {
     float2* phase = nullptr;              // [nb][phase_len] (cos, sin)(pi (X_n mod 2 R_i) / R_i), X_n the
                                           // Q16.16 centre of texel n (float64 on the host, rounded)
     int phase_len = 0;                    // texels per bucket row of `phase` (whole tiles)
+    float* amax = nullptr;                // [nb] bound on |A| of any bump of the bucket
     uint32_t* keys[2] = {nullptr, nullptr};  // [2 cap] bin keys (sort ping-pong)
     uint32_t* vals[2] = {nullptr, nullptr};  // [2 cap] bump ids
     uint32_t* hist = nullptr;             // [256 * nblk_s] per-block digit counts, then [256] digit totals

@@ -22,12 +22,13 @@
 // no longer grows with the number of bumps covering a texel.
 //
 // Exactness of the prefix sums: the corner weights are rounded once to
-// 32-bit integers with a per-(tile, bucket) scale 2^30 / (1.001 sum_b |A_b|)
-// over the tile's candidate bumps.  Every S_ij then fits in 31 bits, the
+// 32-bit integers with a per-(tile, bucket) scale 2^30 / (1.001 n A_max),
+// n the tile's candidate bumps and A_max the bucket's bound on |A| (its
+// direction amplitudes, and the wake's).  Every S_ij then fits in 31 bits, the
 // events accumulate exactly in any order (integer shared-memory atomics:
 // deterministic results), and the prefix sums are exact modulo 2^32 (their
 // intermediate values may wrap; the final ones do not).  The contraction is
-// FP32.  The rounding error of a weight is at most 2^-31 sum |A|, far below
+// FP32.  The rounding error of a weight is at most 2^-31 n A_max, far below
 // the FP32 map tolerance.
 //
 // One CTA per (tile, bucket group) item, 512 threads, two CTAs per SM.  The
@@ -48,7 +49,8 @@ constexpr int kSatThreads = 512;
 constexpr int kSatWarps = kSatThreads / 32;
 constexpr int kSegs = kSatThreads / kT;      // row segments of the column pass
 constexpr int kSegRows = kT / kSegs;         // rows per segment
-constexpr int kSatMaxRows = 512;             // bin rows of one bucket that reach a tile
+constexpr int kSatRowCap = 1024;             // bin rows of the item's buckets held at once
+constexpr int kSatStage = 1280;              // candidates of a bucket staged in shared memory
 constexpr int32_t kQs = 65536, kHalfs = 32768;
 static_assert(kSegs * kSegRows == kT && kSegs == 8, "column-pass mapping");
 
@@ -56,8 +58,15 @@ struct SatSmem {
     uint32_t E[3][kT * kT];               // difference array, then prefix sums (one component group)
     uint32_t seg[kSegs][3][kT];           // column sums of each row segment
     float2 ph[2 * kT];                    // the bucket's texel phases (cos, sin) a: rows, then columns
-    int32_t rs[kSatMaxRows], rl[kSatMaxRows];   // candidate record range of each bin row
-    float red[kSatWarps];                 // per-warp sums of |A|
+    float4 c4[kSatStage];                 // staged candidates: A, cos, sin (x), cos (y)
+    float2 c2[kSatStage];                 //                    sin (y), support box (bits)
+    int32_t rs[kSatRowCap];               // first record of each bin row (all buckets of a batch)
+    int32_t cum[kSatRowCap];              // candidates of the bucket before the row
+    BucketDev bk[kMaxBuckets];            // the item's buckets
+    int32_t bx_lo[kMaxBuckets], bx_hi[kMaxBuckets], by_lo[kMaxBuckets], nrows[kMaxBuckets];
+    int32_t rb[kMaxBuckets + 1];          // first row of each bucket of the batch
+    int32_t ncand[kMaxBuckets];           // candidates of each bucket
+    int32_t batch_end;                    // one past the last bucket of the batch
     alignas(16) unsigned char pd[sizeof(PatchDev)];
     alignas(16) unsigned char spd[sizeof(SynthParams)];
 };
@@ -75,6 +84,16 @@ __device__ __forceinline__ void event3(SatSmem& S, int x, int y, uint32_t w0, ui
     atomicAdd(&S.E[0][o], w0);
     atomicAdd(&S.E[1][o], w1);
     atomicAdd(&S.E[2][o], w2);
+}
+
+// inclusive warp scan of v
+__device__ __forceinline__ uint32_t warp_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
 }
 
 __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* items, const PatchDev* pdevs,
@@ -99,10 +118,26 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
     const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
     const int b_begin = max((g * sp.nb) / G, sp.b_lo);
     const int b_end = min(((g + 1) * sp.nb) / G, sp.b_hi);
+    const int nbk = max(0, b_end - b_begin);
     // Q16.16 centres of the tile's first and last texel columns and rows
     const int32_t X0 = tx0 * kQs + kHalfs, X1 = X0 + (kT - 1) * kQs;
     const int32_t Y0 = ty0 * kQs + kHalfs, Y1 = Y0 + (kT - 1) * kQs;
     const float lamq = 0.5f * sp.lam_half;   // lam / 4
+
+    // ---- the item's buckets and the bin rows that reach the tile
+    // (bins hold x_b + R in [bx C, (bx + 1) C))
+    for (int t = tid; t < nbk; t += kSatThreads) {
+        const BucketDev bk = p.bk[b_begin + t];
+        S.bk[t] = bk;
+        const int bx_lo = (int)((int64_t)X0 / bk.C);
+        const int bx_hi = min((int)(((int64_t)X1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nbx - 1);
+        const int by_lo = (int)((int64_t)Y0 / bk.C);
+        const int by_hi = min((int)(((int64_t)Y1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nby - 1);
+        S.bx_lo[t] = bx_lo;
+        S.bx_hi[t] = bx_hi;
+        S.by_lo[t] = by_lo;
+        S.nrows[t] = (bx_lo > bx_hi || by_lo > by_hi) ? 0 : by_hi - by_lo + 1;
+    }
 
     // column pass: this thread owns texel column cx of rows sg*8 .. sg*8 + 7
     const int cx = tid & (kT - 1), sg = tid / kT;
@@ -110,80 +145,134 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
 #pragma unroll
     for (int r = 0; r < kSegRows; ++r) ah[r] = adx[r] = ady[r] = 0.f;
 
-    for (int bi = b_begin; bi < b_end; ++bi) {
-        const BucketDev bk = p.bk[bi];
-        // bins whose bumps can reach the tile (x_b + R in [bx C, (bx + 1) C))
-        int bx_lo = (int)((int64_t)X0 / bk.C);
-        int bx_hi = (int)(((int64_t)X1 + 2 * (int64_t)bk.R - 1) / bk.C);
-        int by_lo = (int)((int64_t)Y0 / bk.C);
-        int by_hi = (int)(((int64_t)Y1 + 2 * (int64_t)bk.R - 1) / bk.C);
-        bx_hi = min(bx_hi, bk.nbx - 1);
-        by_hi = min(by_hi, bk.nby - 1);
-        if (bx_lo > bx_hi || by_lo > by_hi) continue;
-        const int nrows = by_hi - by_lo + 1;
-        if (nrows > kSatMaxRows) {
-            if (tid == 0) atomicOr(p.stats + 2, (unsigned long long)kErrCapacity);
-            continue;
+    // buckets in batches whose bin rows fit the row tables
+    for (int bb = 0; bb < nbk;) {
+        __syncthreads();   // bucket geometry written; the previous batch is done with the tables
+        if (tid == 0) {
+            int n = 0, be = bb;
+            while (be < nbk && (be == bb || n + S.nrows[be] <= kSatRowCap)) {
+                S.rb[be - bb] = n;
+                n += min(S.nrows[be], kSatRowCap);
+                ++be;
+            }
+            S.rb[be - bb] = n;
+            S.batch_end = be;
         }
-        __syncthreads();   // the previous bucket is done with rs, rl, ph and E
-        for (int r = tid; r < nrows; r += kSatThreads) {
-            const int key0 = bk.base + (by_lo + r) * bk.nbx;
-            const int s0 = (int)p.offsets[key0 + bx_lo];
-            S.rs[r] = s0;
-            S.rl[r] = (int)p.offsets[key0 + bx_hi + 1] - s0;
-        }
-        for (int k = tid; k < 2 * kT; k += kSatThreads)
-            S.ph[k] = p.phase[(size_t)bi * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
         __syncthreads();
-        // sum of |A| over the candidates: warp w takes rows w, w + 16, ...,
-        // lanes stride the row; a fixed order, so every CTA gets the same scale
-        float sa = 0.f;
-        for (int r = warp; r < nrows; r += kSatWarps) {
-            const int s0 = S.rs[r], l = S.rl[r];
-            for (int k = lane; k < l; k += 32) sa += fabsf(p.rec[s0 + k].amp);
+        const int be = S.batch_end;
+        const int nq = S.rb[be - bb];
+        // every row of the batch: record range from the bin offsets
+        for (int q = tid; q < nq; q += kSatThreads) {
+            int t = 0;
+            while (S.rb[t + 1] <= q) ++t;
+            const int bi = bb + t, r = q - S.rb[t];
+            const BucketDev& bk = S.bk[bi];
+            const int key0 = bk.base + (S.by_lo[bi] + r) * bk.nbx;
+            const int s0 = (int)p.offsets[key0 + S.bx_lo[bi]];
+            S.rs[q] = s0;
+            S.cum[q] = (int)p.offsets[key0 + S.bx_hi[bi] + 1] - s0;   // row length for now
         }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, d);
-        if (lane == 0) S.red[warp] = sa;
         __syncthreads();
-        float tot = 0.f;
-        for (int w = 0; w < kSatWarps; ++w) tot += S.red[w];
-        if (!(tot > 0.f)) continue;   // no bump of this bucket reaches the tile
-        const float bound = 1.001f * tot;                 // >= every |S_ij|
-        const float scale = 1073741824.f / bound;         // 2^30 / bound
-        const float inv = bound * (1.f / 1073741824.f);   // 1 / scale (exact power-of-two step)
-        const float2 ux = S.ph[kT + cx];                  // (cos a_X, sin a_X) of this column
+        // per bucket: exclusive prefix of the row lengths (warp w takes buckets w, w + 16, ...)
+        for (int t = warp; t < be - bb; t += kSatWarps) {
+            const int q0 = S.rb[t], q1 = S.rb[t + 1];
+            uint32_t carry = 0u;
+            for (int q = q0; q < q1; q += 32) {
+                const uint32_t l = q + lane < q1 ? (uint32_t)S.cum[q + lane] : 0u;
+                const uint32_t inc = warp_scan(l, lane);
+                if (q + lane < q1) S.cum[q + lane] = (int32_t)(carry + inc - l);
+                carry += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            if (lane == 0) S.ncand[bb + t] = (int32_t)carry;
+        }
+        __syncthreads();
 
-        for (int i = 0; i < 3; ++i) {   // component group p_i: S_i0, S_i1, S_i2
-            for (int k = tid; k < 3 * kT * kT / 4; k += kSatThreads)
-                reinterpret_cast<uint4*>(&S.E[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
-            __syncthreads();
-            // ---- corner events
-            for (int r = warp; r < nrows; r += kSatWarps) {
-                const int s0 = S.rs[r], l = S.rl[r];
-                for (int base = 0; base < l; base += 32) {
-                    const int k = base + lane;
-                    bool ov = false;
-                    int a = 0, b = 0, c = 0, d = 0;
-                    uint32_t w0 = 0u, w1 = 0u, w2 = 0u;
-                    if (k < l) {
-                        const float4* rp = reinterpret_cast<const float4*>(p.rec + s0 + k);
-                        const float4 rx = rp[0];   // x, cos, sin, id
-                        const float4 ry = rp[1];   // y, cos, sin, A
-                        const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
-                        // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
-                        a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
-                        b = clamp_t(-((X0 - xb - bk.R) >> 16));
-                        c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
-                        d = clamp_t(-((Y0 - yb - bk.R) >> 16));
-                        ov = a < b && c < d;
-                        if (ov) {
-                            const float pi = i == 0 ? 1.f : (i == 1 ? rx.y : rx.z);
-                            const float m = ry.w * pi * scale;
-                            w0 = (uint32_t)__float2int_rn(m);
-                            w1 = (uint32_t)__float2int_rn(m * ry.y);
-                            w2 = (uint32_t)__float2int_rn(m * ry.z);
+        for (int bi = bb; bi < be; ++bi) {
+            const int t = bi - bb;
+            const int ncand = S.ncand[bi];
+            const float amax = p.amax[b_begin + bi];
+            if (ncand == 0 || !(amax > 0.f)) continue;   // no bump of this bucket reaches the tile
+            if (S.nrows[bi] > kSatRowCap) {              // rows beyond the tables: not synthesised
+                if (tid == 0) atomicOr(p.stats + 2, (unsigned long long)kErrCapacity);
+                continue;
+            }
+            const BucketDev bk = S.bk[bi];
+            const int q0 = S.rb[t], q1 = S.rb[t + 1];
+            for (int k = tid; k < 2 * kT; k += kSatThreads)
+                S.ph[k] = p.phase[(size_t)(b_begin + bi) * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
+            // stage the first kSatStage candidates: warp w takes rows w, w + 16, ...
+            for (int q = q0 + warp; q < q1; q += kSatWarps) {
+                const int f_row = S.cum[q];
+                const int l = (q + 1 < q1 ? S.cum[q + 1] : ncand) - f_row;
+                const int r0 = S.rs[q];
+                for (int k = lane; k < l && f_row + k < kSatStage; k += 32) {
+                    const float4* rp = reinterpret_cast<const float4*>(p.rec + r0 + k);
+                    const float4 rx = rp[0];   // x, cos, sin, id
+                    const float4 ry = rp[1];   // y, cos, sin, A
+                    const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
+                    // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
+                    const int a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
+                    const int b = clamp_t(-((X0 - xb - bk.R) >> 16));
+                    const int c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
+                    const int d = clamp_t(-((Y0 - yb - bk.R) >> 16));
+                    const uint32_t box = (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) |
+                                                                ((uint32_t)d << 21)
+                                                          : 0u;
+                    S.c4[f_row + k] = make_float4(ry.w, rx.y, rx.z, ry.y);
+                    S.c2[f_row + k] = make_float2(ry.z, __uint_as_float(box));
+                }
+            }
+            const float bound = 1.001f * (float)ncand * amax;   // >= every |S_ij|
+            const float scale = 1073741824.f / bound;         // 2^30 / bound
+            const float inv = bound * (1.f / 1073741824.f);   // 1 / scale
+
+            for (int i = 0; i < 3; ++i) {   // component group p_i: S_i0, S_i1, S_i2
+                for (int k = tid; k < 3 * kT * kT / 4; k += kSatThreads)
+                    reinterpret_cast<uint4*>(&S.E[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
+                __syncthreads();
+                // ---- corner events; candidate f of the bucket, all lanes of a
+                // warp in the same trips (the warp-wide sums below)
+                for (int f0 = warp * 32; f0 < ncand; f0 += kSatThreads) {
+                    const int f = f0 + lane;
+                    float A = 0.f, pc = 0.f, ps = 0.f, qc = 0.f, qs = 0.f;
+                    uint32_t box = 0u;   // empty box: no events
+                    if (f < ncand) {
+                        if (f < kSatStage) {
+                            const float4 c = S.c4[f];
+                            const float2 e = S.c2[f];
+                            A = c.x; pc = c.y; ps = c.z; qc = c.w; qs = e.x;
+                            box = __float_as_uint(e.y);
+                        } else {
+                            // the row holding candidate f, and its record
+                            int lo = q0, hi = q1 - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (S.cum[mid] <= f) lo = mid; else hi = mid - 1;
+                            }
+                            const float4* rp = reinterpret_cast<const float4*>(p.rec + S.rs[lo] + (f - S.cum[lo]));
+                            const float4 rx = rp[0];   // x, cos, sin, id
+                            const float4 ry = rp[1];   // y, cos, sin, A
+                            const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
+                            // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
+                            const int a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
+                            const int b = clamp_t(-((X0 - xb - bk.R) >> 16));
+                            const int c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
+                            const int d = clamp_t(-((Y0 - yb - bk.R) >> 16));
+                            box = (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) |
+                                                         ((uint32_t)d << 21)
+                                                   : 0u;
+                            A = ry.w; pc = rx.y; ps = rx.z; qc = ry.y; qs = ry.z;
                         }
+                    }
+                    const int a = box & 127, b = (box >> 7) & 127, c = (box >> 14) & 127, d = (box >> 21) & 127;
+                    const bool ov = a < b;   // (an empty box has a = b = 0)
+                    uint32_t w0 = 0u, w1 = 0u, w2 = 0u;
+                    if (ov) {
+                        const float pi = i == 0 ? 1.f : (i == 1 ? pc : ps);
+                        const float m = A * pi * scale;
+                        w0 = (uint32_t)__float2int_rn(m);
+                        w1 = (uint32_t)__float2int_rn(m * qc);
+                        w2 = (uint32_t)__float2int_rn(m * qs);
                     }
                     // the corner (0, 0) is shared by every bump that covers the
                     // tile's first texel: summed over the warp first
@@ -201,64 +290,78 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                         if (b < kT && d < kT) event3(S, b, d, w0, w1, w2);
                     }
                 }
-            }
-            __syncthreads();
-            // ---- prefix along x: one row of one component per thread
-            if (tid < 3 * kT) {
-                uint32_t* E = S.E[tid / kT];
-                const int y = tid % kT;
-                uint32_t run = 0u;
-#pragma unroll 16
-                for (int x = 0; x < kT; ++x) {
-                    const int o = sw(y, x);
-                    run += E[o];
-                    E[o] = run;
+                __syncthreads();
+                // ---- prefix along x: one row of one plane per thread, in
+                // chunks of 4 with the next chunk loaded before this one is
+                // stored (the loads need not wait for the stores)
+                if (tid < 3 * kT) {
+                    uint32_t* E = S.E[tid / kT];
+                    const int y = tid % kT;
+                    uint32_t cur[4], nxt[4], run = 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cur[k] = E[sw(y, k)];
+#pragma unroll
+                    for (int x0 = 0; x0 < kT; x0 += 4) {
+                        if (x0 + 4 < kT) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) nxt[k] = E[sw(y, x0 + 4 + k)];
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            run += cur[k];
+                            E[sw(y, x0 + k)] = run;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+                    }
                 }
-            }
-            __syncthreads();
-            // ---- prefix along y, in two steps: segment column sums ...
-            {
-                uint32_t s0 = 0u, s1 = 0u, s2 = 0u;
+                __syncthreads();
+                // ---- prefix along y, in two steps: segment column sums ...
+                {
+                    uint32_t s0 = 0u, s1 = 0u, s2 = 0u;
+#pragma unroll
+                    for (int r = 0; r < kSegRows; ++r) {
+                        const int o = sw(sg * kSegRows + r, cx);
+                        s0 += S.E[0][o];
+                        s1 += S.E[1][o];
+                        s2 += S.E[2][o];
+                    }
+                    S.seg[sg][0][cx] = s0;
+                    S.seg[sg][1][cx] = s1;
+                    S.seg[sg][2][cx] = s2;
+                }
+                __syncthreads();
+                // ... then this segment's rows from the sums of the segments above
+                uint32_t run0 = 0u, run1 = 0u, run2 = 0u;
+                for (int s = 0; s < sg; ++s) {
+                    run0 += S.seg[s][0][cx];
+                    run1 += S.seg[s][1][cx];
+                    run2 += S.seg[s][2][cx];
+                }
+                // u_i(X), u'_i(X) with the constant factors and 1 / scale
+                const float2 ux = S.ph[kT + cx];   // (cos a_X, sin a_X) of this column
+                const float u = i == 0 ? 1.f : (i == 1 ? ux.x : -ux.y);
+                const float up = i == 0 ? 0.f : (i == 1 ? ux.y : ux.x);
+                const float ku = 0.25f * u * inv, kup = lamq * up * inv, kud = lamq * u * inv;
 #pragma unroll
                 for (int r = 0; r < kSegRows; ++r) {
-                    const int o = sw(sg * kSegRows + r, cx);
-                    s0 += S.E[0][o];
-                    s1 += S.E[1][o];
-                    s2 += S.E[2][o];
+                    const int y = sg * kSegRows + r;
+                    const int o = sw(y, cx);
+                    run0 += S.E[0][o];
+                    run1 += S.E[1][o];
+                    run2 += S.E[2][o];
+                    const float2 vy = S.ph[y];   // (cos a_Y, sin a_Y)
+                    const float f0 = (float)(int32_t)run0, f1 = (float)(int32_t)run1, f2 = (float)(int32_t)run2;
+                    const float t = fmaf(-vy.y, f2, fmaf(vy.x, f1, f0));   // v . S_i.
+                    const float tp = fmaf(vy.y, f1, vy.x * f2);            // v' . S_i.
+                    ah[r] = fmaf(ku, t, ah[r]);
+                    adx[r] = fmaf(kup, t, adx[r]);
+                    ady[r] = fmaf(kud, tp, ady[r]);
                 }
-                S.seg[sg][0][cx] = s0;
-                S.seg[sg][1][cx] = s1;
-                S.seg[sg][2][cx] = s2;
+                __syncthreads();   // E and seg are rewritten by the next group
             }
-            __syncthreads();
-            // ... then this segment's rows from the sums of the segments above
-            uint32_t run0 = 0u, run1 = 0u, run2 = 0u;
-            for (int s = 0; s < sg; ++s) {
-                run0 += S.seg[s][0][cx];
-                run1 += S.seg[s][1][cx];
-                run2 += S.seg[s][2][cx];
-            }
-            // u_i(X), u'_i(X) with the constant factors and 1 / scale
-            const float u = i == 0 ? 1.f : (i == 1 ? ux.x : -ux.y);
-            const float up = i == 0 ? 0.f : (i == 1 ? ux.y : ux.x);
-            const float ku = 0.25f * u * inv, kup = lamq * up * inv, kud = lamq * u * inv;
-#pragma unroll
-            for (int r = 0; r < kSegRows; ++r) {
-                const int y = sg * kSegRows + r;
-                const int o = sw(y, cx);
-                run0 += S.E[0][o];
-                run1 += S.E[1][o];
-                run2 += S.E[2][o];
-                const float2 vy = S.ph[y];   // (cos a_Y, sin a_Y)
-                const float f0 = (float)(int32_t)run0, f1 = (float)(int32_t)run1, f2 = (float)(int32_t)run2;
-                const float t = fmaf(-vy.y, f2, fmaf(vy.x, f1, f0));   // v . S_i.
-                const float tp = fmaf(vy.y, f1, vy.x * f2);            // v' . S_i.
-                ah[r] = fmaf(ku, t, ah[r]);
-                adx[r] = fmaf(kup, t, adx[r]);
-                ady[r] = fmaf(kud, tp, ady[r]);
-            }
-            __syncthreads();   // E and seg are rewritten by the next group
         }
+        bb = be;
     }
 
     // ---- store: the group's partial planes, or (one group) the blended maps
