@@ -42,6 +42,15 @@ UNIT = "evals/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # tensor work of one operand stage of the tile gather: 6 MMAs of M = N = 128, K = 16
 FLOPS_PER_STAGE = 6 * 2 * 128 * 128 * 16
+# issue-rate peak of one GB300 in thread instructions: 152 SMs x 4 schedulers x
+# 32 lanes x 2.070 GHz
+ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+# algorithmic operations of the summed-area synthesis per (texel, bucket): for
+# each of the 9 S_ij components one add in each prefix pass and one
+# int-to-float conversion (27), and the contraction of h, Dx and Dy with the
+# texel's u, u', v, v' factors (21 multiply-adds); the per-bump corner events
+# are not counted (a lower bound on the work)
+SAT_OPS_PER_TEXEL_BUCKET = 48
 
 
 def tensor_peak():
@@ -349,6 +358,66 @@ def run_sweep(args):
 
 
 # ---- ours ----------------------------------------------------------------------------
+def tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, fp16):
+    """Tensor roofline of the tile gather (k_synth_tc with its bucket-group
+    blend), timed by the library's events around the synthesis stage on the
+    stream it launches on.  Executed tensor work: operand stages x the work of
+    6 MMAs of 128x128x16 (hi*hi, hi*lo, lo*hi over two K = 16 steps; issued as
+    one N = 256 and one N = 128 MMA per step), a third of that with single
+    FP16 operands."""
+    stages = sum(sc.stats(p).mma_stages for p in range(len(cfg["patches"])))
+    mma_flops = stages * FLOPS_PER_STAGE // (3 if fp16 else 1)
+    peak, peak_src = tensor_peak()
+    achieved = mma_flops / (synth_ms / 1000.0) / 1e12
+    fp32_eq = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
+    r = {"bound": "tensor", "kernel": "k_synth_tc", "achieved": achieved, "peak": peak,
+         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+         "flops_per_launch": mma_flops, "operand_stages_per_launch": stages, "avg_launch_ms": synth_ms,
+         "fp32_equivalent": {"flops_per_launch": evals_per_step * FLOPS_PER_EVAL, "achieved": fp32_eq,
+                             "peak": FP32_PEAK_TFLOPS, "frac": fp32_eq / FP32_PEAK_TFLOPS,
+                             "note": "6 flop per bump-texel eval against the FP32 CUDA-core "
+                                     "FMA peak (152 SMs x 128 lanes x 2 flop x 2070 MHz)"},
+         "stage_ms": stage_info}
+    r["traffic"] = profiled_traffic(cfg, "k_synth_tc")
+    return r
+
+
+def sat_roofline(sc, cfg, synth_ms, evals_per_step, stage_info):
+    """ALU roofline of the summed-area synthesis (k_synth_sat with its
+    bucket-group blend), timed by the library's events around the synthesis
+    stage.  Algorithmic work: SAT_OPS_PER_TEXEL_BUCKET operations per (texel,
+    bucket) of every patch, against the instruction-issue peak."""
+    tb = 0
+    for p in range(len(cfg["patches"])):
+        H, W = sc.patch_shape(p)
+        tb += W * H * sc.info(p).n_buckets
+    ops = tb * SAT_OPS_PER_TEXEL_BUCKET
+    achieved = ops / (synth_ms / 1000.0) / 1e12
+    fp32_eq = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
+    return {"bound": "alu", "kernel": "k_synth_sat", "achieved": achieved, "peak": ALU_PEAK_TOPS,
+            "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS, "traffic": profiled_traffic(cfg, "k_synth_sat"),
+            "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (thread instructions)",
+            "ops_per_launch": ops, "texel_buckets_per_launch": tb, "avg_launch_ms": synth_ms,
+            "fp32_equivalent": {"flops_per_launch": evals_per_step * FLOPS_PER_EVAL, "achieved": fp32_eq,
+                                "peak": FP32_PEAK_TFLOPS, "frac": fp32_eq / FP32_PEAK_TFLOPS,
+                                "note": "the direct gather's 6 flop per bump-texel eval, for the same sums"},
+            "stage_ms": stage_info}
+
+
+def profiled_traffic(cfg, kernel):
+    """DRAM bytes per launch of `kernel` on this workload from the committed
+    ncu summary (null when there is none for this kernel and workload)."""
+    rfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tr = json.load(open(rfile))
+    except Exception:
+        return None
+    for e in (tr if isinstance(tr, list) else [tr]):
+        if e.get("workload") == cfg["name"] and e.get("kernel") == kernel:
+            return e.get("dram_bytes_per_launch")
+    return None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -365,8 +434,8 @@ def run_ours(args):
     sc = scwp.Scene(cfg, device=local)
     if args.batched:
         sc.set_batched(True)
-    if args.fp16:
-        sc.set_synth_mode(scwp.SYNTH_GATHER_FP16)
+    modes = {"sat": scwp.SYNTH_SAT, "gather": scwp.SYNTH_GATHER, "fp16": scwp.SYNTH_GATHER_FP16}
+    sc.set_synth_mode(modes[args.synth])
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     dt = cfg["dt"]
@@ -423,41 +492,43 @@ def run_ours(args):
     total_s_all, total_evals_all = reduce_over_ranks(total_s, total_evals, world, "cuda")
     value = total_evals_all / total_s_all
 
-    # dominant kernel: tensor-core tile gather (k_synth_tc, with its bucket-group
-    # blend epilogue), timed by the library's events around the synthesis
-    # stage on the stream it launches on.  Executed tensor work: operand stages
-    # x the work of 6 MMAs of 128x128x16 (hi*hi, hi*lo, lo*hi over two K = 16
-    # steps; issued as one N = 256 and one N = 128 MMA per step).
     synth_ms = stage_ms[2] / max(frames, 1)
     evals_per_step = total_evals / args.steps
-    stages = sum(sc.stats(p).mma_stages for p in range(len(cfg["patches"])))
-    mma_flops = stages * FLOPS_PER_STAGE // (3 if args.fp16 else 1)   # single operands: 2 MMAs a stage
-    peak, peak_src = tensor_peak()
-    achieved = mma_flops / (synth_ms / 1000.0) / 1e12
-    fp32_eq = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
-    roofline = {"bound": "tensor", "kernel": "k_synth_tc", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_src,
-                "flops_per_launch": mma_flops, "operand_stages_per_launch": stages,
-                "avg_launch_ms": synth_ms,
-                "fp32_equivalent": {"flops_per_launch": evals_per_step * FLOPS_PER_EVAL,
-                                    "achieved": fp32_eq, "peak": FP32_PEAK_TFLOPS,
-                                    "frac": fp32_eq / FP32_PEAK_TFLOPS,
-                                    "note": "6 flop per bump-texel eval against the FP32 CUDA-core "
-                                            "FMA peak (152 SMs x 128 lanes x 2 flop x 2070 MHz)"},
-                "stage_source": "library events on the timed frames" if stage_events else
-                                "library events on eager frames after the timed (graph-replayed) ones",
-                "stage_ms": {"fft": stage_ms[0] / max(frames, 1),
-                             "particles": stage_ms[1] / max(frames, 1),
-                             "synth_blend": synth_ms, "frame": stage_ms[3] / max(frames, 1)}}
-    rfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(rfile):
-        try:
-            tr = json.load(open(rfile))
-            if tr.get("workload") == cfg["name"] and tr.get("kernel") == "k_synth_tc":
-                roofline["traffic"] = tr.get("dram_bytes_per_launch")
-        except Exception:
-            pass
+    stage_info = {"source": "library events on the timed frames" if stage_events else
+                            "library events on eager frames after the timed (graph-replayed) ones",
+                  "fft": stage_ms[0] / max(frames, 1), "particles": stage_ms[1] / max(frames, 1),
+                  "synth_blend": synth_ms, "frame": stage_ms[3] / max(frames, 1)}
+    if args.synth == "sat":
+        roofline = sat_roofline(sc, cfg, synth_ms, evals_per_step, stage_info)
+    else:
+        roofline = tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, args.synth == "fp16")
+    # the other synthesis on the same scene: the tensor-core gather beside the
+    # summed-area default (its own roofline), for comparison
+    other = None
+    if args.synth == "sat" and not args.no_compare:
+        sc.set_synth_mode(scwp.SYNTH_GATHER)
+        for _ in range(3):
+            flush.zero_()
+            sc.step(dt)
+        sc.set_timing(True)
+        sc.timing_read()
+        n_cmp = max(10, min(args.steps // 4, 150))
+        ev_c = 0
+        for _ in range(n_cmp):
+            flush.zero_()
+            sc.step(dt)
+            ev_c += sum(sc.stats(p).eval_count for p in range(len(cfg["patches"])))
+        torch.cuda.synchronize()
+        ms_c, fr_c = sc.timing_read()
+        sc.set_timing(False)
+        sc.set_synth_mode(scwp.SYNTH_SAT)
+        s_ms = ms_c[2] / max(fr_c, 1)
+        other = {"synthesis": "tensor-core tile gather (SCWP_SYNTH_GATHER)", "frames": n_cmp,
+                 "value": ev_c / (ms_c[3] / 1000.0), "unit": UNIT, "ms_per_step": ms_c[3] / max(fr_c, 1),
+                 "roofline": tc_roofline(sc, cfg, s_ms, ev_c / n_cmp,
+                                         {"source": "library events, eager frames", "fft": ms_c[0] / max(fr_c, 1),
+                                          "particles": ms_c[1] / max(fr_c, 1), "synth_blend": s_ms,
+                                          "frame": ms_c[3] / max(fr_c, 1)}, False)}
 
     # end to end through the C ABI: step + read of the blended maps to pinned host memory
     e2e = None
@@ -501,14 +572,17 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * total_s_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16 operands, f32 sums" if args.fp16 else "f32",
+            "dtype": {"sat": "f32 (int32 prefix sums)", "gather": "f32 (f16 hi/lo operands)",
+                      "fp16": "f16 operands, f32 sums"}[args.synth],
             "data": "synthetic", "config": dict(describe(cfg), parallelism=f"replicas{world}",
                                                 mode="batched" if args.batched else "plain",
-                                                synth_groups=[sc.info(p).synth_groups
+                                                synthesis=args.synth,
+                                                synth_groups=[sc.info(p).sat_groups if args.synth == "sat"
+                                                              else sc.info(p).synth_groups
                                                               for p in range(len(cfg["patches"]))]),
             "p50_ms": p50, "p99_ms": p99, "evals_per_step": evals_per_step,
             "live_particles": sc.stats(0).live_particles,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gather_tc": other,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line))
@@ -530,8 +604,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--inflight", type=int, default=3, help="serving: ticks outstanding")
     ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
-    ap.add_argument("--fp16", action="store_true",
-                    help="single-FP16 tensor-core synthesis operands (SCWP_SYNTH_GATHER_FP16)")
+    ap.add_argument("--synth", default="sat", choices=["sat", "gather", "fp16"],
+                    help="synthesis: summed-area (default, SCWP_SYNTH_SAT), tensor-core gather "
+                         "(SCWP_SYNTH_GATHER) or its single-FP16 operands (SCWP_SYNTH_GATHER_FP16)")
+    ap.add_argument("--fp16", action="store_true", help="same as --synth fp16")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the tensor-core gather measured beside the summed-area default")
     ap.add_argument("--batched", action="store_true",
                     help="one synthesis launch over all patches of the frame (scwp_set_batched)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -540,6 +618,8 @@ def main():
     ap.add_argument("--ref-total-seconds", type=float, default=60.0, help="reference: strip seconds in all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.fp16:
+        args.synth = "fp16"
     if args.impl == "reference":
         if args.workload in ("serving", "sweep"):
             print(json.dumps({"impl": "reference", "unavailable": f"no oracle counterpart of the {args.workload} "

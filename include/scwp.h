@@ -56,7 +56,7 @@ enum { SCWP_SPREAD_COS2S_MITSUYASU = 0, SCWP_SPREAD_COS2 = 1 };
 enum { SCWP_AMP_NORMALIZED = 0, SCWP_AMP_LITERAL = 1 };
 enum { SCWP_FIELD_H = 0, SCWP_FIELD_DX = 1, SCWP_FIELD_DY = 2 };
 /* Synthesis modes (Sec. 4.2):
- *   SCWP_SYNTH_GATHER       tile gather on the tensor cores (default): tcgen05
+ *   SCWP_SYNTH_GATHER       tile gather on the tensor cores: tcgen05
  *                           FP16 MMAs with a hi/lo operand split, FP32
  *                           accumulation; the FP32 contract (1e-4 Hs);
  *   SCWP_SYNTH_LAYERED      the paper's layered-texture formulation;
@@ -73,7 +73,7 @@ enum { SCWP_FIELD_H = 0, SCWP_FIELD_DX = 1, SCWP_FIELD_DY = 2 };
  *                           sums of the bumps' support-box corners (integer
  *                           events, exact prefix sums, FP32 contraction);
  *                           the FP32 contract; the cost no longer grows with
- *                           the bumps that cover a texel. */
+ *                           the bumps that cover a texel.  The default. */
 enum { SCWP_SYNTH_GATHER = 0, SCWP_SYNTH_LAYERED = 1, SCWP_SYNTH_GATHER_FP32 = 2, SCWP_SYNTH_GATHER_FP16 = 3,
        SCWP_SYNTH_SAT = 4 };
 
@@ -173,6 +173,9 @@ typedef struct scwp_patch_info {
     int32_t synth_groups;      /* bucket groups of the tensor-core synthesis (planned at creation) */
     int32_t synth_items;       /* its (tile, group) work items = CTAs per synthesis launch */
     int32_t synth_slots;       /* resident CTA slots of the device the plan assumed */
+    int32_t sat_groups;        /* bucket groups of the summed-area synthesis */
+    int32_t sat_items;         /* its (tile, group) work items */
+    int32_t sat_slots;         /* resident CTA slots its plan assumed */
 } scwp_patch_info;
 
 /* Table identifiers for scwp_get_table (element type, count). */
@@ -259,10 +262,11 @@ scwp_status scwp_get_bins(scwp_ctx* ctx, int32_t patch_id, uint32_t* counts, uin
 
 /* Recompute the synthesis and blend of every patch from the current
  * particles and background without advancing the frame (the bins are
- * rebuilt).  mode: SCWP_SYNTH_GATHER (tile gather on the tensor cores, the
- * default path of scwp_step), SCWP_SYNTH_GATHER_FP32 (the same gather on the
- * FP32 CUDA cores) or SCWP_SYNTH_LAYERED (per-bucket layer splat + separable
- * x / y passes + layer sum, Sec. 4.2). */
+ * rebuilt).  mode: any SCWP_SYNTH_* (SCWP_SYNTH_SAT, the default path of
+ * scwp_step; SCWP_SYNTH_GATHER, the tile gather on the tensor cores;
+ * SCWP_SYNTH_GATHER_FP32, the same gather on the FP32 CUDA cores;
+ * SCWP_SYNTH_GATHER_FP16; SCWP_SYNTH_LAYERED, per-bucket layer splat +
+ * separable x / y passes + layer sum, Sec. 4.2). */
 scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode);
 
 /* Select the synthesis used by scwp_step (SCWP_SYNTH_*). */
@@ -275,13 +279,14 @@ scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode);
  * synthesis modes ignore the range. */
 scwp_status scwp_set_bucket_range(scwp_ctx* ctx, int32_t b_lo, int32_t b_hi);
 
-/* Batched frame step (on != 0): the tensor-core synthesis of all patches of
+/* Batched frame step (on != 0): the synthesis of all patches of
  * the context runs as one launch over the (patch, tile, bucket group) items
  * of every patch, heaviest first by a work estimate, followed by one
  * group-sum blend launch; per-patch bucket-group counts are planned for the
  * whole frame instead of for each patch alone.  The results are the same
  * sums as the one-patch-per-launch path (with another grouping, the same
- * values up to FP32 rounding order).  Applies to SCWP_SYNTH_GATHER; the
+ * values up to FP32 rounding order).  Applies to SCWP_SYNTH_SAT,
+ * SCWP_SYNTH_GATHER and SCWP_SYNTH_GATHER_FP16; the
  * paper has no counterpart (its frame is one scene on one GPU).  Returns
  * SCWP_E_INVALID for a null context; takes effect at the next synthesis. */
 scwp_status scwp_set_batched(scwp_ctx* ctx, int32_t on);
@@ -345,9 +350,11 @@ void scwp_destroy(scwp_ctx* ctx);
  * created by the server on the server's stream and allocator, in batched
  * mode.  scwp_server_tick takes every scene that has a pending request and
  * no frame in flight, enqueues each one's background and particle stages
- * (on eight internal streams) and runs the tensor-core synthesis of all of
- * them as ONE launch over the union of their planned (patch, tile, bucket
- * group) items, heaviest first, followed by one group-sum blend launch.
+ * (on eight internal streams) and runs the synthesis of all of them as ONE
+ * launch over the union of their planned (patch, tile, bucket group) items,
+ * heaviest first, followed by one group-sum blend launch (one such pair per
+ * synthesis mode in use: a scene keeps its context's mode, by default
+ * SCWP_SYNTH_SAT; SCWP_SYNTH_GATHER selects the tensor-core gather).
  * Per scene the arithmetic is that of a batched scwp_step, so each result
  * is the same whether the scene runs alone or in a mix.  At most
  * max_inflight ticks are outstanding; the next tick's particle stages

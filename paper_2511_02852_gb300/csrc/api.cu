@@ -109,7 +109,7 @@ struct scwp_ctx {
     bool bg_valid = false;
     std::vector<PatchHost*> patches;
     std::vector<void*> allocs;
-    int synth_mode = SCWP_SYNTH_GATHER;
+    int synth_mode = SCWP_SYNTH_SAT;
     bool timing = false;
     std::vector<FrameEvents> ring;
     int ring_n = 0;
@@ -1465,6 +1465,9 @@ scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info
     out->synth_groups = P->dev.groups_tc;
     out->synth_items = (int32_t)P->tc_items.size();
     out->synth_slots = P->tc_slots;
+    out->sat_groups = P->sat_groups;
+    out->sat_items = (int32_t)P->sat_items.size();
+    out->sat_slots = P->sat_slots;
     for (int i = 0; i < P->T.nb; ++i) {
         out->bin_cells[i] = P->bin_cells[i];
         out->nbx[i] = P->bk[i].nbx;
@@ -1878,12 +1881,14 @@ scwp_status scwp_server_tick(scwp_server* sv, int32_t* started) {
             SCU(cudaEventRecord(sv->pev[q], sv->pst[q]));
             SCU(cudaStreamWaitEvent(sv->st, sv->pev[q], 0));
         }
-    // the union of the scenes' synthesis plans, heaviest first
+    // the union of the scenes' synthesis plans, heaviest first: one list for
+    // the scenes on the summed-area synthesis (the default), one for those on
+    // the tensor-core gather
     std::vector<PatchDev> pd;
     std::vector<SynthParams> sp;
-    std::vector<TcItem> items;
-    std::vector<double> work;
-    std::vector<BlendSpan> spans;
+    std::vector<TcItem> items[2];
+    std::vector<double> work[2];
+    std::vector<BlendSpan> spans[2];
     for (int i : take) {
         scwp_ctx* c = sv->scenes[i].ctx;
         const int base = (int)pd.size();
@@ -1891,24 +1896,34 @@ scwp_status scwp_server_tick(scwp_server* sv, int32_t* started) {
             pd.push_back(c->patches[p]->dev);
             sp.push_back(c->h_sps[p]);
         }
-        for (size_t k = 0; k < c->b_items.size(); ++k) {
-            TcItem it = c->b_items[k];
+        const int m = c->synth_mode == SCWP_SYNTH_SAT ? 1 : 0;
+        const std::vector<TcItem>& ci = m ? c->s_items : c->b_items;
+        const std::vector<double>& cw = m ? c->s_work : c->b_work;
+        for (size_t k = 0; k < ci.size(); ++k) {
+            TcItem it = ci[k];
             it.patch += base;
-            items.push_back(it);
-            work.push_back(c->b_work[k]);
+            items[m].push_back(it);
+            work[m].push_back(cw[k]);
         }
-        for (BlendSpan b : c->b_spans) {
+        for (BlendSpan b : (m ? c->s_spans : c->b_spans)) {
             b.patch += base;
-            spans.push_back(b);
+            spans[m].push_back(b);
         }
     }
-    std::vector<int> order(items.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<int> order[2];
+    for (int m = 0; m < 2; ++m) {
+        order[m].resize(items[m].size());
+        for (size_t k = 0; k < order[m].size(); ++k) order[m][k] = (int)k;
+        const std::vector<double>& w = work[m];
+        std::stable_sort(order[m].begin(), order[m].end(), [&](int a, int b) { return w[a] > w[b]; });
+    }
     const size_t o_sp = align16(pd.size() * sizeof(PatchDev));
-    const size_t o_it = o_sp + align16(sp.size() * sizeof(SynthParams));
-    const size_t o_bs = o_it + align16(items.size() * sizeof(TcItem));
-    const size_t bytes = o_bs + align16(std::max<size_t>(1, spans.size()) * sizeof(BlendSpan));
+    size_t o_it[2], o_bs[2];
+    o_it[0] = o_sp + align16(sp.size() * sizeof(SynthParams));
+    o_bs[0] = o_it[0] + align16(items[0].size() * sizeof(TcItem));
+    o_it[1] = o_bs[0] + align16(spans[0].size() * sizeof(BlendSpan));
+    o_bs[1] = o_it[1] + align16(items[1].size() * sizeof(TcItem));
+    const size_t bytes = o_bs[1] + align16(std::max<size_t>(1, spans[1].size()) * sizeof(BlendSpan));
     if (sv->stage_cap[slot] < bytes) {
         if (sv->hstage[slot]) cudaFreeHost(sv->hstage[slot]);
         sv_free(sv, sv->dstage[slot]);
@@ -1928,14 +1943,21 @@ scwp_status scwp_server_tick(scwp_server* sv, int32_t* started) {
     unsigned char* h = (unsigned char*)sv->hstage[slot];
     memcpy(h, pd.data(), pd.size() * sizeof(PatchDev));
     memcpy(h + o_sp, sp.data(), sp.size() * sizeof(SynthParams));
-    TcItem* hi = reinterpret_cast<TcItem*>(h + o_it);
-    for (size_t k = 0; k < order.size(); ++k) hi[k] = items[order[k]];
-    if (!spans.empty()) memcpy(h + o_bs, spans.data(), spans.size() * sizeof(BlendSpan));
+    for (int m = 0; m < 2; ++m) {
+        TcItem* hi = reinterpret_cast<TcItem*>(h + o_it[m]);
+        for (size_t k = 0; k < order[m].size(); ++k) hi[k] = items[m][order[m][k]];
+        if (!spans[m].empty()) memcpy(h + o_bs[m], spans[m].data(), spans[m].size() * sizeof(BlendSpan));
+    }
     unsigned char* dv = (unsigned char*)sv->dstage[slot];
     SCU(cudaMemcpyAsync(dv, h, bytes, cudaMemcpyHostToDevice, sv->st));
-    SCU(launch_synth_tc(reinterpret_cast<const TcItem*>(dv + o_it), (int)items.size(),
-                        reinterpret_cast<const PatchDev*>(dv), reinterpret_cast<const SynthParams*>(dv + o_sp),
-                        reinterpret_cast<const BlendSpan*>(dv + o_bs), (int)spans.size(), sv->st));
+    const PatchDev* dpd = reinterpret_cast<const PatchDev*>(dv);
+    const SynthParams* dsp = reinterpret_cast<const SynthParams*>(dv + o_sp);
+    if (!items[0].empty())
+        SCU(launch_synth_tc(reinterpret_cast<const TcItem*>(dv + o_it[0]), (int)items[0].size(), dpd, dsp,
+                            reinterpret_cast<const BlendSpan*>(dv + o_bs[0]), (int)spans[0].size(), sv->st));
+    if (!items[1].empty())
+        SCU(launch_synth_sat(reinterpret_cast<const TcItem*>(dv + o_it[1]), (int)items[1].size(), dpd, dsp,
+                             reinterpret_cast<const BlendSpan*>(dv + o_bs[1]), (int)spans[1].size(), sv->st));
     SCU(cudaEventRecord(tk.done, sv->st));
     sv->slot_busy[slot] = true;
     *started = (int32_t)tk.reqs.size();

@@ -71,7 +71,8 @@ class scwp_patch_info(C.Structure):
                 ("total_bins", C.c_int32), ("capacity", C.c_int32),
                 ("bin_cells", C.c_int32 * MAX_BUCKETS), ("nbx", C.c_int32 * MAX_BUCKETS),
                 ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS),
-                ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32)]
+                ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32),
+                ("sat_groups", C.c_int32), ("sat_items", C.c_int32), ("sat_slots", C.c_int32)]
 
 
 class scwp_server_desc(C.Structure):
@@ -374,7 +375,7 @@ class Scene:
                                    len(entries), C.byref(n)), self.ctx)
         return counts, offsets, entries[:n.value]
 
-    def resynthesize(self, mode=SYNTH_GATHER):
+    def resynthesize(self, mode=SYNTH_SAT):
         _check(lib().scwp_resynthesize(self.ctx, mode), self.ctx)
 
     def set_synth_mode(self, mode):

@@ -1,4 +1,6 @@
-"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI, with
+the synthesis on the tensor-core gather (the summed-area synthesis has its
+own file, test_gpu_sat.py).
 
 Contract: integer particle state, bins and eval counts bit-exact; float32
 maps within max |d| <= 1e-4 Hs and relative L2 <= 1e-5 of the FP64 oracle
@@ -29,9 +31,13 @@ def _cuda():
     torch.cuda.synchronize()
 
 
-def make(cfg):
+def make(cfg, mode=None):
+    """A scene on the tensor-core gather (this file's path) unless `mode`
+    names another synthesis."""
     from paper_2511_02852_gb300 import scwp
-    return scwp.Scene(cfg, device=0)
+    sc = scwp.Scene(cfg, device=0)
+    sc.set_synth_mode(scwp.SYNTH_GATHER if mode is None else mode)
+    return sc
 
 
 def compare_state(sc, orc, p):
@@ -164,9 +170,11 @@ def test_realistic_full_size_state_bins_and_sampled_maps():
     sc.close()
 
 
-def test_single_particle_closed_form_on_gpu():
+@pytest.mark.parametrize("mode_name", ["SYNTH_GATHER", "SYNTH_SAT"])
+def test_single_particle_closed_form_on_gpu(mode_name):
     """One particle moving along +x: on the crest-to-trough segment the GPU map
-    is A cos(pi s / R) (Fig. 1 pair), away from the blend band."""
+    is A cos(pi s / R) (Fig. 1 pair), away from the blend band; a 300 x 40
+    patch, so the tiles are ragged in both directions."""
     cfg = wl.scene("one", wl.spectrum(n_buckets=3, n_theta=16, wind_dir=math.pi / 16,
                                       fft_n=16, fft_L=64.0, seed=1),
                    [wl.patch(width=300, height=40, cell=0.5, band=1.0, max_particles=16,
@@ -181,7 +189,7 @@ def test_single_particle_closed_form_on_gpu():
     X = 200 * 65536 + 4321
     Y = 20 * 65536 + 32768
     sc.set_particles(0, [X], [Y], [(b << 16) | j])
-    sc.resynthesize()
+    sc.resynthesize(getattr(scwp, mode_name))
     h, dx, dy = sc.maps(0)
     Rb = int(R[b])
     for ix in range(2, 298):

@@ -32,13 +32,20 @@ def _drain(sv, want):
     raise AssertionError(f"only {len(done)} of {want} requests completed")
 
 
-def test_each_scene_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("modes", ["sat", "gather", "mixed"])
+def test_each_scene_same_alone_and_in_the_mix(modes):
+    """Scenes on the summed-area synthesis (the default), on the tensor-core
+    gather, or both in the same ticks (two synthesis launches a tick)."""
     from paper_2511_02852_gb300 import scwp
     cfgs = _mix()
     frames = [3, 2, 4, 5]
+    mode = [scwp.SYNTH_SAT if modes == "sat" or (modes == "mixed" and k % 2 == 0) else scwp.SYNTH_GATHER
+            for k in range(len(cfgs))]
     sv = scwp.Server(max_inflight=3)
     ids = [sv.add_scene(c) for c in cfgs]
     assert all(i is not None for i in ids)
+    for s, m in zip(ids, mode):
+        sv.scene(s).set_synth_mode(m)
     rid = 0
     order = {}
     # interleaved submissions: the scenes share ticks
@@ -56,9 +63,10 @@ def test_each_scene_same_alone_and_in_the_mix():
     info = sv.info()
     assert info.requests_done == rid and info.ticks_launched >= max(frames)
     torch.cuda.synchronize()
-    for s, c, n in zip(ids, cfgs, frames):
+    for s, c, n, m in zip(ids, cfgs, frames, mode):
         alone = scwp.Scene(c)
         alone.set_batched(True)
+        alone.set_synth_mode(m)
         for _ in range(n):
             alone.step(c["dt"])
         view = sv.scene(s)
