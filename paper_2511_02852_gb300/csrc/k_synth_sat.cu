@@ -49,8 +49,8 @@ constexpr int kSatThreads = 512;
 constexpr int kSatWarps = kSatThreads / 32;
 constexpr int kSegs = kSatThreads / kT;      // row segments of the column pass
 constexpr int kSegRows = kT / kSegs;         // rows per segment
-constexpr int kSatRowCap = 1024;             // bin rows of the item's buckets held at once
-constexpr int kSatStage = 1280;              // candidates of a bucket staged in shared memory
+constexpr int kSatRowCap = 512;              // bin rows of the item's buckets held at once
+constexpr int kSatStage = 1984;              // candidates of a bucket staged in shared memory
 constexpr int32_t kQs = 65536, kHalfs = 32768;
 static_assert(kSegs * kSegRows == kT && kSegs == 8, "column-pass mapping");
 
