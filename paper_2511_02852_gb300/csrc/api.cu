@@ -788,7 +788,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         D.vals[k] = (uint32_t*)dalloc(ctx, 2 * cap * 4);
         ok = ok && D.x[k] && D.y[k] && D.bd[k] && D.keys[k] && D.vals[k];
     }
-    D.count = (int32_t*)dalloc(ctx, 2 * sizeof(int32_t));
+    D.count = (int32_t*)dalloc(ctx, 3 * sizeof(int32_t));
     D.flags = (uint8_t*)dalloc(ctx, cap);
     D.blk = (uint32_t*)dalloc(ctx, ((size_t)D.nblk_c + 1) * 4);
     const size_t ng = (size_t)T.nb * T.nth;
@@ -881,7 +881,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     }
     int32_t n0 = (int32_t)std::min<size_t>(px.size(), cap);
     uint64_t flags0 = px.size() > cap ? kErrCapacity : 0;
-    int32_t counts[2] = {n0, n0};
+    int32_t counts[3] = {n0, n0, n0};
     CU(cudaMemcpyAsync(D.amp, ampf.data(), ng * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(D.bk, P->bk.data(), T.nb * sizeof(BucketDev), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(P->d_items, P->tc_items.data(), P->tc_items.size() * sizeof(TcItem), cudaMemcpyHostToDevice,

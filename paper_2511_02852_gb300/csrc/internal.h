@@ -45,7 +45,7 @@ struct PatchDev {
     int32_t* x[2] = {nullptr, nullptr};
     int32_t* y[2] = {nullptr, nullptr};
     uint32_t* bd[2] = {nullptr, nullptr}; // bucket << 16 | direction
-    int32_t* count = nullptr;             // [0] live, [1] live after compaction
+    int32_t* count = nullptr;             // [0] live, [1] live after compaction, [2] live before it
     uint8_t* flags = nullptr;             // [cap] alive flags
     uint32_t* blk = nullptr;              // [nblk_c + 1] compaction block sums
     int nblk_c = 0;

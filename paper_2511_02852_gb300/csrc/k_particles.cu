@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blk, int nblk, i
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        count[2] = count[0];   // the pre-compaction count, for the scatter
         count[0] = (int32_t)s_carry;
         count[1] = (int32_t)s_carry;
     }
@@ -148,8 +149,8 @@ __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
     int32_t* Xd = p.x[1 - p.cur];
     int32_t* Yd = p.y[1 - p.cur];
     uint32_t* Bd = p.bd[1 - p.cur];
-    // flags past the pre-compaction live count are zero (cleared after every
-    // compaction), so only this frame's survivors are moved.
+    // only the pre-compaction live particles (count[2]) carry this frame's flags
+    const int n = p.count[2];
     uint8_t f[kItems];
     uint32_t mine = 0;
     const uint32_t blk_off = p.blk[blockIdx.x];
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int i = base + threadIdx.x * kItems + k;
-        f[k] = (i < p.cap) ? p.flags[i] : 0;
+        f[k] = (i < n) ? p.flags[i] : 0;
         mine += f[k];
     }
     uint32_t total;
@@ -175,11 +176,6 @@ __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
             ++off;
         }
     }
-}
-
-__global__ void k_clear_flags(uint8_t* flags, int cap) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
-        flags[i] = 0;
 }
 
 // ---- a4 + a5: injection and wake emission -------------------------------------
@@ -421,26 +417,24 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
     }
 }
 
-// offsets[k] = first sorted position with key >= k (k = 0..total_bins),
-// from the sorted keys in one pass: position e is the answer for every k in
-// (key[e-1], key[e]] (for e = 0 from 0, for e = n up to total_bins)
-__global__ void k_bin_offsets(const uint32_t* keys, const int32_t* count, uint32_t* offsets,
-                              int total_bins) {
-    const int n = 2 * count[0];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n; e += gridDim.x * blockDim.x) {
-        const int lo = e == 0 ? 0 : (int)keys[e - 1] + 1;
-        const int hi = e == n ? total_bins : min((int)keys[e], total_bins);
-        for (int k = lo; k <= hi; ++k) offsets[k] = (uint32_t)e;
-    }
-}
-
-// bump records in bin order: (X, Y, signed amplitude bits, bump id)
-__global__ void k_records(PatchDev p, const uint32_t* vals) {
-    const int nvalid = (int)p.offsets[p.total_bins];
+// One pass over the sorted (key, bump id) pairs:
+//  * offsets[k] = first sorted position with key >= k (k = 0..total_bins):
+//    position e is the answer for every k in (key[e-1], key[e]] (for e = 0
+//    from 0, for e = n up to total_bins);
+//  * the bump records in bin order (X, Y, signed amplitude, id and the
+//    kernel phase pairs) of the entries with a bin (key < total_bins; the
+//    others sort last).
+__global__ void k_offsets_records(PatchDev p, const uint32_t* keys, const uint32_t* vals) {
+    const int n = 2 * p.count[0];
     const int32_t* X = p.x[p.cur];
     const int32_t* Y = p.y[p.cur];
     const uint32_t* BD = p.bd[p.cur];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nvalid; e += gridDim.x * blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n; e += gridDim.x * blockDim.x) {
+        const uint32_t key = e < n ? keys[e] : (uint32_t)p.total_bins;
+        const int lo = e == 0 ? 0 : (int)keys[e - 1] + 1;
+        const int hi = e == n ? p.total_bins : min((int)key, p.total_bins);
+        for (int k = lo; k <= hi; ++k) p.offsets[k] = (uint32_t)e;
+        if (e == n || key >= (uint32_t)p.total_bins) continue;
         const uint32_t id = vals[e];
         const int i = (int)(id >> 1);
         const bool trough = id & 1u;
@@ -460,13 +454,13 @@ __global__ void k_records(PatchDev p, const uint32_t* vals) {
         if (xm < 0) xm += R2;
         if (ym < 0) ym += R2;
         const float invR = p.bk[bd >> 16].invR;
-        float s, c;
-        sincospif((float)xm * invR, &s, &c);
-        r.cx = c;
-        r.sx = -s;
-        sincospif((float)ym * invR, &s, &c);
-        r.cy = c;
-        r.sy = -s;
+        float sn, cs;
+        sincospif((float)xm * invR, &sn, &cs);
+        r.cx = cs;
+        r.sx = -sn;
+        sincospif((float)ym * invR, &sn, &cs);
+        r.cy = cs;
+        r.sy = -sn;
         p.rec[e] = r;
     }
 }
@@ -483,8 +477,7 @@ cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st) {
 cudaError_t launch_compact(const PatchDev& p, cudaStream_t st) {
     k_scan_blocks<<<1, 1024, 0, st>>>(p.blk, p.nblk_c, p.count);
     k_compact_scatter<<<p.nblk_c, kTpb, 0, st>>>(p);
-    k_clear_flags<<<(p.cap + 1023) / 1024 < 1024 ? (p.cap + 1023) / 1024 : 1024, 1024, 0, st>>>(p.flags, p.cap);
-    count_launches(3);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -519,13 +512,10 @@ cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
                                                    p.vals[1 - src], p.count, shift, p.hist, dtot, p.nblk_s);
         src = 1 - src;
     }
-    int ob = (2 * p.cap + 1 + kTpb - 1) / kTpb;
-    if (ob > 152 * 8) ob = 152 * 8;
-    k_bin_offsets<<<ob, kTpb, 0, st>>>(p.keys[src], p.count, p.offsets, p.total_bins);
-    int rb = (2 * p.cap + kTpb - 1) / kTpb;
+    int rb = (2 * p.cap + 1 + kTpb - 1) / kTpb;
     if (rb > 152 * 16) rb = 152 * 16;
-    k_records<<<rb, kTpb, 0, st>>>(p, p.vals[src]);
-    count_launches(3 + 3 * passes);
+    k_offsets_records<<<rb, kTpb, 0, st>>>(p, p.keys[src], p.vals[src]);
+    count_launches(2 + 3 * passes);
     return cudaGetLastError();
 }
 
