@@ -243,11 +243,17 @@ __global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) { 
 __global__ void __launch_bounds__(kTpb) k_inject_dev(PatchDev p, const InjectParams* ip) { inject_body(p, *ip); }
 
 // ---- a6: binning ---------------------------------------------------------------
+// Block b takes the particles of sort tile b (kTileS / 2 particles, two
+// bump keys each) and also produces the tile's histogram of the lowest key
+// digit: the first radix pass needs no separate histogram launch.
 __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, uint32_t* vals) {
     __shared__ unsigned long long s_ev[kTpb / 32];
     __shared__ unsigned int s_bin[kTpb / 32];
     __shared__ unsigned int s_live[kMaxBuckets];
+    __shared__ uint32_t s_h[256];
+    static_assert(kTpb == 256, "one digit counter per thread");
     for (int i = threadIdx.x; i < p.nb; i += blockDim.x) s_live[i] = 0;
+    s_h[threadIdx.x] = 0;
     __syncthreads();
     const int n = p.count[0];
     const int32_t* X = p.x[p.cur];
@@ -255,7 +261,8 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
     const uint32_t* BD = p.bd[p.cur];
     unsigned long long ev = 0;
     unsigned int binned = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int i_end = min(n, (blockIdx.x + 1) * (kTileS / 2));
+    for (int i = blockIdx.x * (kTileS / 2) + threadIdx.x; i < i_end; i += blockDim.x) {
         const uint32_t bd = BD[i];
         const int b = (int)(bd >> 16);
         const int4 vq = lookup_vq(p, bd);
@@ -276,6 +283,7 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
             }
             keys[2 * i + k] = key;
             vals[2 * i + k] = (uint32_t)(2 * i + k);
+            atomicAdd(&s_h[key & 255u], 1u);
         }
     }
     // block reductions (integers: order-independent)
@@ -304,6 +312,7 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
     }
     for (int i = threadIdx.x; i < p.nb; i += blockDim.x)
         if (s_live[i]) atomicAdd(&p.stats[3 + i], (unsigned long long)s_live[i]);
+    p.hist[threadIdx.x * p.nblk_s + blockIdx.x] = s_h[threadIdx.x];   // (after the barrier above)
 }
 
 // LSD radix sort pass, 8-bit digit, stable.  Per-block digit histograms.
@@ -497,15 +506,13 @@ cudaError_t launch_inject_dev(const PatchDev& p, const InjectParams* ip, cudaStr
 }
 
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
-    int kb = (p.cap + kTpb - 1) / kTpb;
-    if (kb > 152 * 8) kb = 152 * 8;
-    if (kb < 1) kb = 1;
-    k_bin_keys<<<kb, kTpb, 0, st>>>(p, p.keys[0], p.vals[0]);
+    // one block per sort tile: keys, vals and the first digit's histograms
+    k_bin_keys<<<p.nblk_s, kTpb, 0, st>>>(p, p.keys[0], p.vals[0]);
     const int passes = (p.key_bits + 7) / 8;
     int src = 0;
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = 8 * ps;
-        k_radix_hist<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.count, shift, p.hist, p.nblk_s);
+        if (ps > 0) k_radix_hist<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.count, shift, p.hist, p.nblk_s);
         uint32_t* dtot = p.hist + (size_t)256 * p.nblk_s;
         k_scan_digits<<<256, kTpb, 0, st>>>(p.hist, p.nblk_s, dtot);
         k_radix_scatter<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.vals[src], p.keys[1 - src],
@@ -515,7 +522,7 @@ cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
     int rb = (2 * p.cap + 1 + kTpb - 1) / kTpb;
     if (rb > 152 * 16) rb = 152 * 16;
     k_offsets_records<<<rb, kTpb, 0, st>>>(p, p.keys[src], p.vals[src]);
-    count_launches(2 + 3 * passes);
+    count_launches(1 + 3 * passes);
     return cudaGetLastError();
 }
 
