@@ -611,13 +611,17 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the tensor-core gather measured beside the summed-area default")
     ap.add_argument("--batched", action="store_true",
-                    help="one synthesis launch over all patches of the frame (scwp_set_batched)")
+                    help="one synthesis launch over all patches of the frame, frames replayed as CUDA "
+                         "graphs (scwp_set_batched; the default)")
+    ap.add_argument("--plain", action="store_true",
+                    help="one synthesis launch per patch, frames launched eagerly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="reference: strip seconds per step at most")
     ap.add_argument("--ref-total-seconds", type=float, default=60.0, help="reference: strip seconds in all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.batched = not args.plain
     if args.fp16:
         args.synth = "fp16"
     if args.impl == "reference":
