@@ -182,3 +182,24 @@ def test_sat_empty_patch_is_background():
     assert ev == 0
     compare_maps(sc.maps(0), ref, orc.spec.Hs(), "sat empty")
     sc.close()
+
+
+def test_sat_fine_bins_many_rows_and_three_radix_passes():
+    """One-cell bins: 64 + 2R bin rows per bucket and tile (more than the
+    kernel's 512-row table over the item's buckets, so the buckets go in
+    batches), 20-bit bin keys (three radix passes); bins bit-exact and maps
+    within the contract."""
+    cfg = wl.scaled(wl.small_jonswap(), bin_cells=1)
+    sc = sat_scene(cfg)
+    orc = OracleScene(cfg)
+    for _ in range(2):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    info = sc.info(0)
+    assert info.bin_cells[0] == 1 and info.total_bins > 1 << 16
+    compare_state(sc, orc, 0)
+    compare_bins(sc, orc, 0)
+    ref, _ = orc.patch_maps(0)
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), "sat one-cell bins")
+    assert sc.stats(0).error_flags == 0
+    sc.close()
