@@ -2,11 +2,14 @@
 """Frame-step benchmark of the hybrid WP/FFT ocean synthesis on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload realistic|tiny|small_jonswap]
+                    [--workload realistic|batched|mixed_large|serving|sweep|...]
+                    [--synth sat|gather|fp16] [--plain]
 
 One step = one whole frame of the hot path (background spectrum update and
 inverse FFT, advection/expiry/compaction, injection, wake emission, binning,
-tile-gather synthesis with blend) on the workload's resident scene.  The
+synthesis with blend) on the workload's resident scene, by default in
+batched mode (frames replayed as CUDA graphs) with the summed-area
+synthesis; the tensor-core gather is timed on the same scene beside it.  The
 metric is particle-pixel (bump-texel) evaluations per second, the eval count
 being the exact integer count of (bump, texel-centre) pairs inside the
 kernel supports (checked bit-exact against the FP64 oracle by the tests);

@@ -11,14 +11,17 @@
 // whose quadrants are 4 S h^T, (2 S/lam) Dx^T, (2 S/lam) Dy^T (the fourth is
 // unused; the constant factors are applied when the sums are read out; S is
 // a power of two that puts the largest |A| of the patch near 2^13), computed
-// by tcgen05.mma (M = 128, N = 128, K = 16, kind::f16) into FP32 accumulators
-// in tensor memory.  Each operand is split as hi + lo in FP16: hi = x
+// by tcgen05.mma (kind::f16, M = 128, K = 16) into FP32 accumulators in
+// tensor memory.  Each operand is split as hi + lo in FP16: hi = x
 // truncated to 10 mantissa bits (exact in FP16), lo = x - hi (exact in FP32,
 // then rounded to FP16): 22 significant bits together, the precision of a
 // TF32 pair at twice the tensor rate and half the shared-memory bytes.
 // hi*hi accumulates in one accumulator and the small corrections
 // hi*lo + lo*hi in a second one, so the large sum takes one rounding per step
-// and the two are added in FP32 when read out.
+// and the two are added in FP32 when read out.  Per K step: one N = 256 MMA
+// of Ahi against the stacked [Bhi; Blo] (the two accumulators side by side
+// in tensor memory, Ahi read from shared memory once) and one N = 128 MMA of
+// Alo against Bhi.
 //
 // Warps 0-7 produce the operands of each 32-bump chunk into a 3-stage ring in
 // shared memory (no-swizzle K-major canonical layout: 8-row x 16-byte core
@@ -28,7 +31,8 @@
 // the chunk's size and kernel radius beside them.  Each producer thread owns
 // two tile rows or columns and a quarter of the chunk's bumps; the kernel phase
 // pi (X_n - x_b)/R of its sample is the product of its own
-// e^{i pi (X_n mod 2R)/R} (one sincospi per bucket) and the bump's
+// e^{i pi (X_n mod 2R)/R} (from the patch's float64 phase table, once per
+// bucket) and the bump's
 // e^{-i pi (x_b mod 2R)/R} (in the record, read as one 16-byte half per
 // role), so a sample costs one complex multiply and an integer support test.
 // Bumps whose support covers the whole tile on both axes (whole bins of
