@@ -485,6 +485,9 @@ void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vec
                 for (int g = 0; g < G; ++g) mx = std::max(mx, item_work(est[k], nb, t, g, G));
             if (mx <= cap || G >= gmax) break;
         }
+        // summed-area items: no more groups than the patch's own plan takes
+        // (enough waves for the patch alone; more only adds blend traffic)
+        if (sat) G = std::max(1, std::min(G, P.sat_groups));
         for (int t = 0; t < tiles[k]; ++t)
             for (int g = 0; g < G; ++g) {
                 items.push_back(TcItem{P.index, t, g, G});
