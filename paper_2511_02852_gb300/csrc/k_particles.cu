@@ -74,6 +74,7 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* s_warp, u
 __global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
     __shared__ uint32_t s_warp[kTpb / 32];
     const int n = p.count[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.count[2] = n;   // the pre-compaction count
     const int base = blockIdx.x * kTileC;
     int32_t* X = p.x[p.cur];
     int32_t* Y = p.y[p.cur];
@@ -100,46 +101,6 @@ __global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
     if (threadIdx.x == 0) p.blk[blockIdx.x] = total;
 }
 
-// exclusive scan of the per-block survivor counts (one block, in place)
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blk, int nblk, int32_t* count) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int start = 0; start < nblk; start += 1024) {
-        const int i = start + threadIdx.x;
-        const uint32_t v = i < nblk ? blk[i] : 0u;
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t w = s_warp[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        const uint32_t carry = s_carry;
-        const uint32_t excl = carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
-        if (i < nblk) blk[i] = excl;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        count[2] = count[0];   // the pre-compaction count, for the scatter
-        count[0] = (int32_t)s_carry;
-        count[1] = (int32_t)s_carry;
-    }
-}
-
 __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
     __shared__ uint32_t s_warp[kTpb / 32];
     const int base = blockIdx.x * kTileC;
@@ -153,10 +114,18 @@ __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
     const int n = p.count[2];
     uint8_t f[kItems];
     uint32_t mine = 0;
-    const uint32_t blk_off = p.blk[blockIdx.x];
-    const uint32_t blk_end = (blockIdx.x + 1 < (unsigned)p.nblk_c) ? p.blk[blockIdx.x + 1]
-                                                                   : (uint32_t)p.count[1];
-    const uint32_t blk_cnt = blk_end - blk_off;
+    // survivors of the earlier blocks (their counts from the advection),
+    // summed by this block (integers: any order); the last block also
+    // publishes the total as the new live count
+    uint32_t before = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kTpb) before += p.blk[b];
+    uint32_t blk_off;
+    block_exscan(before, s_warp, blk_off);
+    const uint32_t blk_cnt = p.blk[blockIdx.x];
+    if (blockIdx.x + 1 == (unsigned)p.nblk_c && threadIdx.x == 0) {
+        p.count[0] = (int32_t)(blk_off + blk_cnt);
+        p.count[1] = (int32_t)(blk_off + blk_cnt);
+    }
     if (blk_cnt == 0) return;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -484,9 +453,8 @@ cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st) {
 }
 
 cudaError_t launch_compact(const PatchDev& p, cudaStream_t st) {
-    k_scan_blocks<<<1, 1024, 0, st>>>(p.blk, p.nblk_c, p.count);
     k_compact_scatter<<<p.nblk_c, kTpb, 0, st>>>(p);
-    count_launches(2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
