@@ -413,14 +413,17 @@ def test_normal_map_matches_oracle_formula():
     sc.close()
 
 
-def test_ring_ripples_state_bins_and_maps_match_oracle():
+@pytest.mark.parametrize("mode_name", ["SYNTH_GATHER", "SYNTH_SAT"])
+def test_ring_ripples_state_bins_and_maps_match_oracle(mode_name):
     """A heaving object (ring ripples, Sec. 4.3 vertical motion) on top of
     its Kelvin wake: particle state and bins bit-exact, injected energy and
-    counts equal, maps within the contract."""
+    counts equal, maps within the contract (both syntheses: the wake
+    amplitude enters the summed-area bound)."""
+    from paper_2511_02852_gb300 import scwp
     cfg = wl.small_jonswap()
     cfg["patches"][0].update(emitter=1, wake_rate=1, heave_period=20 * cfg["dt"], ring_rate=6,
                              obj_radius=3.0, obj_speed=2.0, obj_path_radius=6.0)
-    sc = make(cfg)
+    sc = make(cfg, getattr(scwp, mode_name))
     orc = OracleScene(cfg)
     for f in range(1, 31):
         sc.step(cfg["dt"])
@@ -434,5 +437,5 @@ def test_ring_ripples_state_bins_and_maps_match_oracle():
     assert st.injected_total == ps.injected
     assert np.allclose([st.injected_energy[i] for i in range(st.n_buckets)], ps.energy, rtol=1e-12, atol=0)
     ref, _ = orc.patch_maps(0)
-    compare_maps(sc.maps(0), ref, orc.spec.Hs(), "ring ripples")
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), f"ring ripples {mode_name}")
     sc.close()
