@@ -231,7 +231,10 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                     reinterpret_cast<uint4*>(&S.E[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
                 __syncthreads();
                 // ---- corner events; candidate f of the bucket, all lanes of a
-                // warp in the same trips (the warp-wide sums below)
+                // warp in the same trips.  The corner (0, 0) is shared by
+                // every bump that covers the tile's first texel: its weights
+                // are summed per thread here and per warp after the loop.
+                uint32_t z0 = 0u, z1 = 0u, z2 = 0u;
                 for (int f0 = warp * 32; f0 < ncand; f0 += kSatThreads) {
                     const int f = f0 + lane;
                     float A = 0.f, pc = 0.f, ps = 0.f, qc = 0.f, qs = 0.f;
@@ -274,14 +277,11 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                         w1 = (uint32_t)__float2int_rn(m * qc);
                         w2 = (uint32_t)__float2int_rn(m * qs);
                     }
-                    // the corner (0, 0) is shared by every bump that covers the
-                    // tile's first texel: summed over the warp first
                     const bool z = ov && a == 0 && c == 0;
-                    if (__any_sync(0xffffffffu, z)) {
-                        const uint32_t v0 = __reduce_add_sync(0xffffffffu, z ? w0 : 0u);
-                        const uint32_t v1 = __reduce_add_sync(0xffffffffu, z ? w1 : 0u);
-                        const uint32_t v2 = __reduce_add_sync(0xffffffffu, z ? w2 : 0u);
-                        if (lane == 0) event3(S, 0, 0, v0, v1, v2);
+                    if (z) {
+                        z0 += w0;
+                        z1 += w1;
+                        z2 += w2;
                     }
                     if (ov) {
                         if (!z) event3(S, a, c, w0, w1, w2);
@@ -289,6 +289,12 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                         if (d < kT) event3(S, a, d, 0u - w0, 0u - w1, 0u - w2);
                         if (b < kT && d < kT) event3(S, b, d, w0, w1, w2);
                     }
+                }
+                {
+                    const uint32_t v0 = __reduce_add_sync(0xffffffffu, z0);
+                    const uint32_t v1 = __reduce_add_sync(0xffffffffu, z1);
+                    const uint32_t v2 = __reduce_add_sync(0xffffffffu, z2);
+                    if (lane == 0 && (v0 | v1 | v2)) event3(S, 0, 0, v0, v1, v2);
                 }
                 __syncthreads();
                 // ---- prefix along x: one row of one plane per thread, in
