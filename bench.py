@@ -221,7 +221,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": describe(cfg),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": host_cpu(),
                          "sample": f"per step: one oracle frame update of the whole scene plus the "
                                    f"FP64 synthesis of a {rows_used}-row strip of the "
                                    f"{cfg['patches'][0]['width']}-wide patch"},
@@ -360,6 +360,20 @@ def run_sweep(args):
 
 
 # ---- ours ----------------------------------------------------------------------------
+def host_cpu():
+    """The host CPU's model name (from /proc/cpuinfo where it has one)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "Hardware"):
+                    return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, fp16):
     """Tensor roofline of the tile gather (k_synth_tc with its bucket-group
     blend), timed by the library's events around the synthesis stage on the
@@ -560,7 +574,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, ev, secs, rows, threads = oracle_strip_rate(cfg, target_s=args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": host_cpu(),
                "sample": f"FP64 oracle synthesis of a {rows}-row strip of the "
                          f"{cfg['patches'][0]['width']}-wide patch after one frame "
                          f"({ev} evals in {secs:.1f} s)"}
