@@ -1138,8 +1138,7 @@ static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>&
             CU(launch_inject_dev(D, ip_dev + k, pst));
         else if (ips[k].total > 0)
             CU(launch_inject(D, ips[k], pst));
-        if ((s = reset_frame_stats(ctx, *P, pst)) != SCWP_OK) return s;
-        CU(launch_bin(D, pst));
+        CU(launch_bin(D, pst));   // (the frame's statistics were zeroed by the advection)
     }
     if (multi)
         for (size_t k = 0; k < ctx->pst.size(); ++k) {
@@ -1173,8 +1172,7 @@ static scwp_status enqueue_prepare(scwp_ctx* ctx, const std::vector<InjectParams
             CU(launch_inject_dev(D, ip_dev + k, ctx->st));
         else if (ips[k].total > 0)
             CU(launch_inject(D, ips[k], ctx->st));
-        if ((s = reset_frame_stats(ctx, *P, ctx->st)) != SCWP_OK) return s;
-        CU(launch_bin(D, ctx->st));
+        CU(launch_bin(D, ctx->st));   // (the frame's statistics were zeroed by the advection)
     }
     CU(cudaGetLastError());
     return SCWP_OK;

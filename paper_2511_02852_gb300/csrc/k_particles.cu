@@ -73,8 +73,15 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* s_warp, u
 // ---- a3: advect, expire ------------------------------------------------------
 __global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
     __shared__ uint32_t s_warp[kTpb / 32];
+    pdl_enter();
     const int n = p.count[0];
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.count[2] = n;   // the pre-compaction count
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) p.count[2] = n;   // the pre-compaction count
+        // this frame's statistics start from zero (evals, binned, live per
+        // bucket, operand stages; the error flags stay)
+        if (threadIdx.x < 2) p.stats[threadIdx.x] = 0ull;
+        if (threadIdx.x <= p.nb) p.stats[3 + threadIdx.x] = 0ull;
+    }
     const int base = blockIdx.x * kTileC;
     int32_t* X = p.x[p.cur];
     int32_t* Y = p.y[p.cur];
@@ -103,6 +110,7 @@ __global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
 
 __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
     __shared__ uint32_t s_warp[kTpb / 32];
+    pdl_enter();
     const int base = blockIdx.x * kTileC;
     const int32_t* Xs = p.x[p.cur];
     const int32_t* Ys = p.y[p.cur];
@@ -113,35 +121,40 @@ __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
     // only the pre-compaction live particles (count[2]) carry this frame's flags
     const int n = p.count[2];
     uint8_t f[kItems];
+    int32_t xs[kItems], ys[kItems];
+    uint32_t bs[kItems];
     uint32_t mine = 0;
-    // survivors of the earlier blocks (their counts from the advection),
-    // summed by this block (integers: any order); the last block also
-    // publishes the total as the new live count
+    // every load first (one round trip): the earlier blocks' survivor
+    // counts, this tile's flags and particles (dead ones too: few)
     uint32_t before = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += kTpb) before += p.blk[b];
+    const uint32_t blk_cnt = p.blk[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int i = base + threadIdx.x * kItems + k;
+        f[k] = (i < n) ? p.flags[i] : 0;
+        xs[k] = (i < n) ? Xs[i] : 0;
+        ys[k] = (i < n) ? Ys[i] : 0;
+        bs[k] = (i < n) ? Bs[i] : 0u;
+        mine += f[k];
+    }
+    // survivors of the earlier blocks, summed by this block (integers: any
+    // order); the last block also publishes the total as the new live count
     uint32_t blk_off;
     block_exscan(before, s_warp, blk_off);
-    const uint32_t blk_cnt = p.blk[blockIdx.x];
     if (blockIdx.x + 1 == (unsigned)p.nblk_c && threadIdx.x == 0) {
         p.count[0] = (int32_t)(blk_off + blk_cnt);
         p.count[1] = (int32_t)(blk_off + blk_cnt);
     }
     if (blk_cnt == 0) return;
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const int i = base + threadIdx.x * kItems + k;
-        f[k] = (i < n) ? p.flags[i] : 0;
-        mine += f[k];
-    }
     uint32_t total;
     uint32_t off = block_exscan(mine, s_warp, total) + blk_off;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         if (f[k]) {
-            const int i = base + threadIdx.x * kItems + k;
-            Xd[off] = Xs[i];
-            Yd[off] = Ys[i];
-            Bd[off] = Bs[i];
+            Xd[off] = xs[k];
+            Yd[off] = ys[k];
+            Bd[off] = bs[k];
             ++off;
         }
     }
@@ -206,10 +219,10 @@ __device__ __forceinline__ void inject_body(const PatchDev& p, const InjectParam
     }
 }
 
-__global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) { inject_body(p, ip); }
+__global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) { pdl_enter(); inject_body(p, ip); }
 
 // the same with the frame's parameters in device memory (CUDA-graph replay)
-__global__ void __launch_bounds__(kTpb) k_inject_dev(PatchDev p, const InjectParams* ip) { inject_body(p, *ip); }
+__global__ void __launch_bounds__(kTpb) k_inject_dev(PatchDev p, const InjectParams* ip) { pdl_enter(); inject_body(p, *ip); }
 
 // ---- a6: binning ---------------------------------------------------------------
 // Block b takes the particles of sort tile b (kTileS / 2 particles, two
@@ -221,6 +234,7 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
     __shared__ unsigned int s_live[kMaxBuckets];
     __shared__ uint32_t s_h[256];
     static_assert(kTpb == 256, "one digit counter per thread");
+    pdl_enter();
     for (int i = threadIdx.x; i < p.nb; i += blockDim.x) s_live[i] = 0;
     s_h[threadIdx.x] = 0;
     __syncthreads();
@@ -288,29 +302,45 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
 __global__ void __launch_bounds__(kTpb) k_radix_hist(const uint32_t* keys, const int32_t* count,
                                                      int shift, uint32_t* hist, int nblk) {
     __shared__ uint32_t s_h[256];
+    pdl_enter();
     s_h[threadIdx.x] = 0;
     __syncthreads();
     const int n = 2 * count[0];
     const int base = blockIdx.x * kTileS;
-    for (int k = 0; k < kSortItems; ++k) {
+    uint32_t key[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {   // all loads first: one round trip
         const int i = base + k * kTpb + threadIdx.x;
-        if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
+        key[k] = i < n ? keys[i] : 0xFFFFFFFFu;
     }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+        if (base + k * kTpb + (int)threadIdx.x < n) atomicAdd(&s_h[(key[k] >> shift) & 255u], 1u);
     __syncthreads();
     hist[threadIdx.x * nblk + blockIdx.x] = s_h[threadIdx.x];
 }
 
 // exclusive scan of one digit's row of the digit-major histogram (block d
-// scans hist[d * nblk .. + nblk)) and that digit's total into dtot[d]
+// scans hist[d * nblk .. + nblk)) and that digit's total into dtot[d]; each
+// thread takes kScanItems consecutive entries per chunk, loaded together
+constexpr int kScanItems = 4;
+
 __global__ void __launch_bounds__(kTpb) k_scan_digits(uint32_t* hist, int nblk, uint32_t* dtot) {
     __shared__ uint32_t s_warp[kTpb / 32];
+    pdl_enter();
     uint32_t* row = hist + (size_t)blockIdx.x * nblk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t carry = 0;
-    for (int start = 0; start < nblk; start += kTpb) {
-        const int i = start + threadIdx.x;
-        const uint32_t v = i < nblk ? row[i] : 0u;
-        uint32_t x = v;
+    for (int start = 0; start < nblk; start += kTpb * kScanItems) {
+        const int i0 = start + threadIdx.x * kScanItems;
+        uint32_t v[kScanItems];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            v[q] = i0 + q < nblk ? row[i0 + q] : 0u;
+            sum += v[q];
+        }
+        uint32_t x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -325,7 +355,12 @@ __global__ void __launch_bounds__(kTpb) k_scan_digits(uint32_t* hist, int nblk, 
             if (w < warp) before += t;
             all += t;
         }
-        if (i < nblk) row[i] = carry + before + x - v;
+        uint32_t run = carry + before + x - sum;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            if (i0 + q < nblk) row[i0 + q] = run;
+            run += v[q];
+        }
         carry += all;
         __syncthreads();
     }
@@ -343,9 +378,20 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_wc[kTpb / 32][256];
     __shared__ uint32_t s_dw[kTpb / 32];
+    pdl_enter();
     const int n = 2 * count[0];
     const int base = blockIdx.x * kTileS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // every load of the block first (one round trip): the tile's keys and
+    // ids, this digit's total and its count in the earlier tiles
+    uint32_t kk[kSortItems], vv[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const int i = base + k * kTpb + threadIdx.x;
+        kk[k] = i < n ? kin[i] : 0u;
+        vv[k] = i < n ? vin[i] : 0u;
+    }
+    const uint32_t h_before = hist[threadIdx.x * nblk + blockIdx.x];
     {
         // exclusive scan of the digit totals (one digit per thread)
         const uint32_t v = dtot[threadIdx.x];
@@ -361,18 +407,15 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
 #pragma unroll
         for (int w = 0; w < kTpb / 32; ++w)
             if (w < warp) before += s_dw[w];
-        s_base[threadIdx.x] = before + x - v + hist[threadIdx.x * nblk + blockIdx.x];
+        s_base[threadIdx.x] = before + x - v + h_before;
     }
     const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const int i = base + k * kTpb + threadIdx.x;
         const bool act = i < n;
-        uint32_t key = 0, val = 0, d = 0x100u + (uint32_t)warp;  // inactive sentinel
-        if (act) {
-            key = kin[i];
-            val = vin[i];
-            d = (key >> shift) & 255u;
-        }
+        const uint32_t key = kk[k], val = vv[k];
+        const uint32_t d = act ? (key >> shift) & 255u : 0x100u + (uint32_t)warp;  // inactive sentinel
 #pragma unroll
         for (int w = 0; w < kTpb / 32; ++w) s_wc[w][threadIdx.x] = 0;
         __syncthreads();
@@ -387,11 +430,11 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
             vout[off] = val;
         }
         __syncthreads();
+        // (the next chunk reads s_base only after its first barrier)
         uint32_t add = 0;
 #pragma unroll
         for (int w = 0; w < kTpb / 32; ++w) add += s_wc[w][threadIdx.x];
         s_base[threadIdx.x] += add;
-        __syncthreads();
     }
 }
 
@@ -403,6 +446,7 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
 //    kernel phase pairs) of the entries with a bin (key < total_bins; the
 //    others sort last).
 __global__ void k_offsets_records(PatchDev p, const uint32_t* keys, const uint32_t* vals) {
+    pdl_enter();
     const int n = 2 * p.count[0];
     const int32_t* X = p.x[p.cur];
     const int32_t* Y = p.y[p.cur];
@@ -447,51 +491,58 @@ __global__ void k_offsets_records(PatchDev p, const uint32_t* keys, const uint32
 
 // ---- launchers -------------------------------------------------------------------
 cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st) {
-    k_advect_flag<<<p.nblk_c, kTpb, 0, st>>>(p);
+    const cudaError_t e = launch_pdl(k_advect_flag, p.nblk_c, kTpb, 0, st, p);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_compact(const PatchDev& p, cudaStream_t st) {
-    k_compact_scatter<<<p.nblk_c, kTpb, 0, st>>>(p);
+    const cudaError_t e = launch_pdl(k_compact_scatter, p.nblk_c, kTpb, 0, st, p);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_t st) {
     int blocks = (ip.total + kTpb - 1) / kTpb;
     if (blocks < 1) blocks = 1;
     if (blocks > 1024) blocks = 1024;
-    k_inject<<<blocks, kTpb, 0, st>>>(p, ip);
+    const cudaError_t e = launch_pdl(k_inject, blocks, kTpb, 0, st, p, ip);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_inject_dev(const PatchDev& p, const InjectParams* ip, cudaStream_t st) {
-    k_inject_dev<<<152 * 2, kTpb, 0, st>>>(p, ip);
+    const cudaError_t e = launch_pdl(k_inject_dev, 152 * 2, kTpb, 0, st, p, ip);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
     // one block per sort tile: keys, vals and the first digit's histograms
-    k_bin_keys<<<p.nblk_s, kTpb, 0, st>>>(p, p.keys[0], p.vals[0]);
+    cudaError_t e = launch_pdl(k_bin_keys, p.nblk_s, kTpb, 0, st, p, p.keys[0], p.vals[0]);
     const int passes = (p.key_bits + 7) / 8;
     int src = 0;
-    for (int ps = 0; ps < passes; ++ps) {
+    uint32_t* dtot = p.hist + (size_t)256 * p.nblk_s;
+    for (int ps = 0; ps < passes && e == cudaSuccess; ++ps) {
         const int shift = 8 * ps;
-        if (ps > 0) k_radix_hist<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.count, shift, p.hist, p.nblk_s);
-        uint32_t* dtot = p.hist + (size_t)256 * p.nblk_s;
-        k_scan_digits<<<256, kTpb, 0, st>>>(p.hist, p.nblk_s, dtot);
-        k_radix_scatter<<<p.nblk_s, kTpb, 0, st>>>(p.keys[src], p.vals[src], p.keys[1 - src],
-                                                   p.vals[1 - src], p.count, shift, p.hist, dtot, p.nblk_s);
+        if (ps > 0)
+            e = launch_pdl(k_radix_hist, p.nblk_s, kTpb, 0, st, (const uint32_t*)p.keys[src],
+                           (const int32_t*)p.count, shift, p.hist, p.nblk_s);
+        if (e == cudaSuccess) e = launch_pdl(k_scan_digits, 256, kTpb, 0, st, p.hist, p.nblk_s, dtot);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_radix_scatter, p.nblk_s, kTpb, 0, st, (const uint32_t*)p.keys[src],
+                           (const uint32_t*)p.vals[src], p.keys[1 - src], p.vals[1 - src],
+                           (const int32_t*)p.count, shift, (const uint32_t*)p.hist, (const uint32_t*)dtot,
+                           p.nblk_s);
         src = 1 - src;
     }
     int rb = (2 * p.cap + 1 + kTpb - 1) / kTpb;
     if (rb > 152 * 16) rb = 152 * 16;
-    k_offsets_records<<<rb, kTpb, 0, st>>>(p, p.keys[src], p.vals[src]);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_offsets_records, rb, kTpb, 0, st, p, (const uint32_t*)p.keys[src],
+                       (const uint32_t*)p.vals[src]);
     count_launches(1 + 3 * passes);
-    return cudaGetLastError();
+    return e;
 }
 
 int sorted_buffer_index(const PatchDev& p) { return ((p.key_bits + 7) / 8) & 1; }

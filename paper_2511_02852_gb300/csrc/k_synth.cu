@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(256) k_blend_groups(PatchDev p, SynthParams sp
 // the same over spans of any patches: one CTA per span
 __global__ void __launch_bounds__(256) k_blend_spans(const BlendSpan* spans, const PatchDev* pdevs,
                                                      const SynthParams* sps) {
+    pdl_enter();
     const BlendSpan sn = spans[blockIdx.x];
     const PatchDev& p = pdevs[sn.patch];
     const SynthParams& sp = sps[sn.patch];
@@ -523,9 +524,9 @@ cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaSt
 
 cudaError_t launch_blend_spans(const BlendSpan* spans, int n_spans, const PatchDev* pdevs, const SynthParams* sps,
                                cudaStream_t st) {
-    k_blend_spans<<<n_spans, 256, 0, st>>>(spans, pdevs, sps);
+    const cudaError_t e = launch_pdl(k_blend_spans, n_spans, 256, 0, st, spans, pdevs, sps);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_blend(const PatchDev& p, const SynthParams& sp, const float* src, int groups,

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SatSmem& S = *reinterpret_cast<SatSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    pdl_enter();
     const TcItem it = items[blockIdx.x];
     {
         static_assert(sizeof(PatchDev) % 4 == 0 && sizeof(SynthParams) % 4 == 0, "descriptor copy");
@@ -418,8 +419,9 @@ cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* p
     cudaError_t e = sat_attributes();
     if (e != cudaSuccess) return e;
     if (n_items > 0) {
-        k_synth_sat<<<n_items, kSatThreads, sizeof(SatSmem), st>>>(items, pdevs, sps);
+        e = launch_pdl(k_synth_sat, n_items, kSatThreads, sizeof(SatSmem), st, items, pdevs, sps);
         count_launches(1);
+        if (e != cudaSuccess) return e;
     }
     if (n_spans > 0) return launch_blend_spans(spans, n_spans, pdevs, sps, st);
     return cudaGetLastError();

@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_synth_tc(const TcItem* items, c
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    pdl_enter();
     // this CTA's (patch, tile, bucket group) item, in the host-planned order
     const TcItem it = items[blockIdx.x];
     {
@@ -755,11 +756,10 @@ cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pd
     cudaError_t e = tc_attributes();
     if (e != cudaSuccess) return e;
     if (n_items > 0) {
-        if (split)
-            k_synth_tc<true><<<n_items, kThreads, sm, st>>>(items, pdevs, sps);
-        else
-            k_synth_tc<false><<<n_items, kThreads, sm, st>>>(items, pdevs, sps);
+        e = split ? launch_pdl(k_synth_tc<true>, n_items, kThreads, sm, st, items, pdevs, sps)
+                  : launch_pdl(k_synth_tc<false>, n_items, kThreads, sm, st, items, pdevs, sps);
         count_launches(1);
+        if (e != cudaSuccess) return e;
     }
     if (n_spans > 0) return launch_blend_spans(spans, n_spans, pdevs, sps, st);
     return cudaGetLastError();
