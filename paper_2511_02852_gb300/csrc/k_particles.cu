@@ -244,17 +244,31 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
     const uint32_t* BD = p.bd[p.cur];
     unsigned long long ev = 0;
     unsigned int binned = 0;
-    const int i_end = min(n, (blockIdx.x + 1) * (kTileS / 2));
-    for (int i = blockIdx.x * (kTileS / 2) + threadIdx.x; i < i_end; i += blockDim.x) {
-        const uint32_t bd = BD[i];
-        const int b = (int)(bd >> 16);
-        const int4 vq = lookup_vq(p, bd);
+    // the thread's kBinItems particles: every independent load first
+    constexpr int kBinItems = (kTileS / 2) / kTpb;
+    static_assert(kBinItems * kTpb == kTileS / 2, "whole particles per thread");
+    const int i0 = blockIdx.x * (kTileS / 2) + threadIdx.x;
+    uint32_t bd[kBinItems];
+    int32_t px[kBinItems], py[kBinItems];
+#pragma unroll
+    for (int m = 0; m < kBinItems; ++m) {
+        const int i = i0 + m * kTpb;
+        bd[m] = i < n ? BD[i] : 0u;
+        px[m] = i < n ? X[i] : 0;
+        py[m] = i < n ? Y[i] : 0;
+    }
+#pragma unroll
+    for (int m = 0; m < kBinItems; ++m) {
+        const int i = i0 + m * kTpb;
+        if (i >= n) continue;
+        const int b = (int)(bd[m] >> 16);
+        const int4 vq = lookup_vq(p, bd[m]);
         const BucketDev bk = p.bk[b];
         atomicAdd(&s_live[b], 1u);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int32_t cx = k ? X[i] - vq.z : X[i];
-            const int32_t cy = k ? Y[i] - vq.w : Y[i];
+            const int32_t cx = k ? px[m] - vq.z : px[m];
+            const int32_t cy = k ? py[m] - vq.w : py[m];
             const int nx = span_count(cx, bk.R, p.W), ny = span_count(cy, bk.R, p.H);
             uint32_t key = (uint32_t)p.total_bins;
             if (nx > 0 && ny > 0) {
