@@ -8,12 +8,15 @@
 One step = one whole frame of the hot path (background spectrum update and
 inverse FFT, advection/expiry/compaction, injection, wake emission, binning,
 synthesis with blend) on the workload's resident scene, by default in
-batched mode (frames replayed as CUDA graphs) with the summed-area
-synthesis; the tensor-core gather is timed on the same scene beside it.  The
+batched mode (several patches: frames replayed as CUDA graphs; one patch:
+eager launches chained by programmatic dependent launch) with the summed-area
+synthesis; the same frames in plain mode (one patch per launch, eager) and
+the tensor-core gather are timed on the same scene beside it.  The
 metric is particle-pixel (bump-texel) evaluations per second, the eval count
 being the exact integer count of (bump, texel-centre) pairs inside the
 kernel supports (checked bit-exact against the FP64 oracle by the tests);
-p50/p99 frame-step latency is reported beside it.
+p50/p99 frame-step latency is reported beside it, and the same evals over the
+synthesis stage alone.
 
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
 scene's stream, L2 flushed (256 MiB write) between timed steps, barrier +
@@ -467,8 +470,8 @@ def run_ours(args):
     barrier()
     launches0 = sc.launch_count()
     # library stage events force one-kernel-at-a-time launches; batched
-    # frames are timed as captured graphs and broken down into stages by a
-    # separate eager run below
+    # frames are timed as launched (captured graphs when the scene has
+    # several patches) and broken down into stages by a separate run below
     stage_events = not args.batched
     if stage_events:
         sc.set_timing(True)
@@ -511,13 +514,39 @@ def run_ours(args):
     synth_ms = stage_ms[2] / max(frames, 1)
     evals_per_step = total_evals / args.steps
     stage_info = {"source": "library events on the timed frames" if stage_events else
-                            "library events on eager frames after the timed (graph-replayed) ones",
+                            "library events on eager frames after the timed ones",
                   "fft": stage_ms[0] / max(frames, 1), "particles": stage_ms[1] / max(frames, 1),
                   "synth_blend": synth_ms, "frame": stage_ms[3] / max(frames, 1)}
     if args.synth == "sat":
         roofline = sat_roofline(sc, cfg, synth_ms, evals_per_step, stage_info)
     else:
         roofline = tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, args.synth == "fp16")
+    # the same scene and synthesis in plain mode (one patch per launch, eager
+    # launches, no graph), timed like the main loop: batched vs plain on
+    # every line
+    plain = None
+    if args.batched and not args.no_compare:
+        sc.set_batched(False)
+        for _ in range(3):
+            flush.zero_()
+            sc.step(dt)
+        n_pl = max(10, min(args.steps // 4, 150))
+        st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_pl)]
+        en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_pl)]
+        ev_p = 0
+        for k in range(n_pl):
+            flush.zero_()
+            st_ev[k].record(stream)
+            sc.step(dt)
+            en_ev[k].record(stream)
+            ev_p += sum(sc.stats(p).eval_count for p in range(len(cfg["patches"])))
+        torch.cuda.synchronize()
+        pm = sorted(a.elapsed_time(b) for a, b in zip(st_ev, en_ev))
+        sc.set_batched(True)
+        plain = {"mode": "plain: one patch per launch, eager launches", "frames": n_pl,
+                 "value": ev_p / (sum(pm) / 1000.0), "unit": UNIT, "ms_per_step": sum(pm) / n_pl,
+                 "p50_ms": pm[len(pm) // 2], "p99_ms": pm[min(len(pm) - 1, int(math.ceil(0.99 * len(pm))) - 1)]}
+
     # the other synthesis on the same scene: the tensor-core gather beside the
     # summed-area default (its own roofline), for comparison
     other = None
@@ -597,8 +626,10 @@ def run_ours(args):
                                                               else sc.info(p).synth_groups
                                                               for p in range(len(cfg["patches"]))]),
             "p50_ms": p50, "p99_ms": p99, "evals_per_step": evals_per_step,
+            # the same evals over the synthesis stage alone (library events)
+            "synthesis_evals_per_s": evals_per_step / (synth_ms / 1000.0) if synth_ms > 0 else None,
             "live_particles": sc.stats(0).live_particles,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gather_tc": other,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain, "gather_tc": other,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line))
