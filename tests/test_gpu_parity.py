@@ -170,6 +170,23 @@ def test_realistic_full_size_state_bins_and_sampled_maps():
     sc.close()
 
 
+def test_bins_exact_with_sort_tiles_past_one_scan_chunk():
+    """600k particles in a 700k-particle patch: 1.2M bump keys fill more
+    than 1024 sort tiles, so the scan of each digit's per-tile counts runs
+    in several chunks (4 entries per thread per chunk).  Particle state and
+    bins (counts, offsets, entries) bit-exact after two frames."""
+    cfg = wl.scaled(wl.realistic(), max_particles=700000, prefill=600000)
+    sc = make(cfg)
+    orc = OracleScene(cfg)
+    for _ in range(2):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    assert 2 * sc.stats(0).live_particles > 1024 * 1024
+    compare_state(sc, orc, 0)
+    compare_bins(sc, orc, 0)
+    sc.close()
+
+
 @pytest.mark.parametrize("mode_name", ["SYNTH_GATHER", "SYNTH_SAT"])
 def test_single_particle_closed_form_on_gpu(mode_name):
     """One particle moving along +x: on the crest-to-trough segment the GPU map
