@@ -357,3 +357,45 @@ def test_ring_directions_visit_the_whole_grid():
     successive ring particles take 4096 distinct directions."""
     from oracle.particles import WAKE_DIRS
     assert len({(k * 2531) % WAKE_DIRS for k in range(WAKE_DIRS)}) == WAKE_DIRS
+
+
+@pytest.mark.parametrize("n_theta", [8, 12, 16, 32])
+def test_direction_grid_half_offset_never_parallel_to_an_edge(n_theta):
+    """The fixed grid theta_j = theta_w - pi + (j + 1/2) dtheta (reading of
+    Sec. 4.2 / Eq. 13): with the wind along +x no direction is parallel to
+    a patch edge, so every direction flows in through exactly one edge of
+    each pair; the grid is symmetric about the wind and covers the circle
+    evenly."""
+    th, rel, dth = sp.directions(0.0, n_theta)
+    assert dth == pytest.approx(2 * math.pi / n_theta)
+    assert np.all(np.abs(np.cos(th)) > 1e-3) and np.all(np.abs(np.sin(th)) > 1e-3)
+    assert np.allclose(np.sort(rel), np.sort(-rel), atol=1e-12)      # symmetric about the wind
+    assert np.allclose(np.diff(th), dth, atol=1e-12)
+    assert rel[0] == pytest.approx(-math.pi + dth / 2) and rel[-1] == pytest.approx(math.pi - dth / 2)
+
+
+def test_injection_carry_sums_to_floor_of_total_rate():
+    """The FP64 carry of the fractional group counts (reading of Eqs. 15-17):
+    with dyadic rates (every sum exact in FP64) the groups injected over F
+    frames through each (bucket, edge pair) are exactly floor(F n), the
+    carry left is frac(F n), and each group adds one particle per direction
+    with A_ij > 0 that flows in through that pair."""
+    cfg = wl.small_jonswap()
+    ps = PatchState(sp.Spectrum(cfg["spectrum"]), cfg["spectrum"], dict(cfg["patches"][0], prefill=0),
+                    0, 3, cfg["dt"])
+    T = ps.T
+    rng = np.random.default_rng(2)
+    rates = rng.integers(1, 400, size=(T.nb, 2)) / 128.0          # dyadic: k / 2^7
+    T.injection_rate = lambda i, s: float(rates[i, s])
+    F = 97
+    for f in range(F):
+        ps.inject(f)
+    expect = 0
+    for i in range(T.nb):
+        for s in (0, 1):
+            total = F * rates[i, s]
+            assert ps.carry[i, s] == total - math.floor(total)
+            vn = T.vx[i] if s == 0 else T.vy[i]
+            ndir = int(((T.A[i] > 0) & (vn != 0)).sum())
+            expect += math.floor(total) * ndir
+    assert len(ps.X) == expect
