@@ -193,3 +193,23 @@ def test_paper_default_scene_constants():
     g = golden()["paper_default"]
     spec = sp.Spectrum(wl.spectrum(wind_speed=5.0, fetch=10000.0))
     assert spec.wp == pytest.approx(g["omega_p"], rel=1e-3)
+
+
+def test_realistic_scene_peak_and_depth():
+    """The realistic scene (U10 = 15 m/s, fetch 100 km, depth 50 m): Eq. 4's
+    peak wp = 22 (g^2 / (U10 F))^(1/3) = 0.881 rad/s, where k d = 3.96 and
+    tanh(k d) > 0.999 (depth changes the peak's phase speed by under 0.1%),
+    while at the lowest bucket edge (0.5 wp) tanh(k d) = 0.83, so the
+    finite-depth reading of O5 matters there."""
+    cfg = wl.realistic()["spectrum"]
+    spec = sp.Spectrum(cfg)
+    wp = 22.0 * (G * G / (15.0 * 100e3)) ** (1.0 / 3.0)
+    assert spec.wp == pytest.approx(wp, rel=1e-12)
+    assert wp == pytest.approx(0.8807, abs=5e-4)
+    kp = spec.k_of_omega(wp)
+    assert kp * 50.0 == pytest.approx(3.96, abs=0.01)
+    assert math.tanh(kp * 50.0) > 0.999
+    deep_c = G / wp
+    assert abs(wp / kp - deep_c) / deep_c < 1e-3
+    k_lo = spec.k_of_omega(0.5 * wp)
+    assert math.tanh(k_lo * 50.0) == pytest.approx(0.83, abs=0.005)
