@@ -196,6 +196,25 @@ def oracle_strip_rate(cfg, target_s=10.0, frames=1, state=None, rows=None):
     return ev / dt, ev, dt, rows, threads
 
 
+def oracle_rate_one_core(workload, target_s=2.0):
+    """The same strip timing with the oracle on one host core, in a child
+    process with OMP_NUM_THREADS=1 (the parent's thread pool is left as it
+    is).  Returns (evals/s, evals, seconds, rows), or None if the child
+    fails."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_strip_rate(bench.workload_config(%r), target_s=%r); "
+            "print(json.dumps([r[0], r[1], r[2], r[3]]))") % (ROOT, workload, float(target_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=300)
+        if out.returncode != 0:
+            return None
+        return tuple(json.loads(out.stdout.strip().splitlines()[-1]))
+    except Exception:
+        return None
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -607,6 +626,11 @@ def run_ours(args):
                "sample": f"FP64 oracle synthesis of a {rows}-row strip of the "
                          f"{cfg['patches'][0]['width']}-wide patch after one frame "
                          f"({ev} evals in {secs:.1f} s)"}
+        one = oracle_rate_one_core(args.workload)
+        if one is not None:
+            cpu["value_1core"] = one[0]
+            cpu["sample_1core"] = (f"the same on one core (OMP_NUM_THREADS=1): a {one[3]}-row strip, "
+                                   f"{one[1]} evals in {one[2]:.1f} s")
 
     if rank == 0:
         ms_sorted = sorted(step_ms)
