@@ -249,6 +249,11 @@ def run_reference(args):
                                    f"{cfg['patches'][0]['width']}-wide patch"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    one = oracle_rate_one_core(args.workload)
+    if one is not None:
+        line["cpu_baseline"]["value_1core"] = one[0]
+        line["cpu_baseline"]["sample_1core"] = (f"a {one[3]}-row strip on one core (OMP_NUM_THREADS=1): "
+                                                f"{one[1]} evals in {one[2]:.1f} s")
     print(json.dumps(line))
     return 0
 
