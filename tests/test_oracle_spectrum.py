@@ -213,3 +213,27 @@ def test_realistic_scene_peak_and_depth():
     assert abs(wp / kp - deep_c) / deep_c < 1e-3
     k_lo = spec.k_of_omega(0.5 * wp)
     assert math.tanh(k_lo * 50.0) == pytest.approx(0.83, abs=0.005)
+
+
+def test_literal_over_normalised_energy_is_the_midpoint_rule():
+    """O8's two amplitude modes: LITERAL (Eq. A) carries S(w_i) dw_i per
+    bucket (times the direction sum), NORMALIZED the exact bucket integral
+    E_i.  Their per-bucket energy ratio is the midpoint rule's error on the
+    bucket: on the interior buckets it shrinks as the buckets narrow (8, 16,
+    64 equal-energy buckets), while on the lowest one, which spans the steep
+    low-frequency flank from 0.5 wp, the value at the energy median
+    overstates the integral more than twice at every count.  That is why
+    NORMALIZED is the default."""
+    devs = []
+    for n in (8, 16, 64):
+        spec = sp.Spectrum(wl.spectrum(n_buckets=n, n_theta=16))
+        b = sp.Buckets(spec, n)
+        lit = sp.amplitudes(spec, b, 16, sp.AMP_LITERAL)
+        nor = sp.amplitudes(spec, b, 16, sp.AMP_NORMALIZED)
+        assert np.allclose((nor ** 2).sum(axis=1) / 2, b.E, rtol=1e-12)
+        ratio = (lit ** 2).sum(axis=1) / (nor ** 2).sum(axis=1)
+        print(f"[O8] {n} buckets: LITERAL/NORMALIZED energy {np.round(ratio, 4)}")
+        assert ratio[0] > 2.0
+        devs.append(np.abs(ratio[1:-1] - 1).max())
+    assert devs[0] > devs[1] > devs[2]
+    assert devs[2] < 0.015
