@@ -166,3 +166,65 @@ print(json.dumps(out.view(-1, 4).tolist()))
         got = philox_scalar(c[0] & 0xFFFFFFFF, c[1] & 0xFFFFFFFF, c[2] & 0xFFFFFFFF,
                             c[3] & 0xFFFFFFFF, seed)
         assert list(got) == [x & 0xFFFFFFFF for x in r]
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the published known-answer vectors of the
+    Random123 distribution (Salmon et al., SC'11): counter, key -> output.
+    This needs nothing but the oracle, so it cannot skip."""
+    kat = [
+        ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+         (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+        ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+         (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+        ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+         (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+    ]
+    for ctr, (k0, k1), want in kat:
+        key = k0 | (k1 << 32)                  # the oracle's key: k0 low word, k1 high word
+        assert philox_scalar(*ctr, key) == want
+        got = philox4x32_10(*[np.array([c], dtype=np.uint64) for c in ctr], key)
+        assert tuple(int(x[0]) for x in got) == want
+
+
+def test_h0_gaussian_draw_is_unit_complex_normal():
+    """xi = (g1 + i g2)/sqrt 2 with g1, g2 standard normal (Box-Muller): over
+    the 512^2 draws mean |xi|^2 = 1, mean Re^2 = mean Im^2 = 1/2, Re and Im
+    uncorrelated, all within 5 standard errors; sqrt 2 Re and sqrt 2 Im pass
+    a Kolmogorov-Smirnov test against N(0, 1) and |xi|^2 against Exp(1).  A
+    missing 1/sqrt 2, a Box-Muller radius without its factor 2, or cos used
+    for both parts each fail."""
+    from scipy import stats
+    N = 512
+    xi = bg.gaussian_pairs(N, 0x5EED).ravel()
+    n = xi.size
+    a = np.abs(xi) ** 2
+    assert abs(a.mean() - 1.0) < 5.0 / math.sqrt(n)           # var |xi|^2 = 1
+    for part in (xi.real, xi.imag):
+        assert abs((part ** 2).mean() - 0.5) < 5.0 * math.sqrt(0.5) / math.sqrt(n)   # var = 1/2
+        assert abs(part.mean()) < 5.0 * math.sqrt(0.5 / n)
+        assert stats.kstest(part * math.sqrt(2.0), "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(xi.real, xi.imag)[0, 1]) < 5.0 / math.sqrt(n)
+    assert stats.kstest(a, "expon").pvalue > 1e-4
+
+
+def test_h0_and_evolved_energy_against_the_power_spectrum():
+    """sum |h0|^2 / sum P = 1 within 5 standard errors (the error of a sum of
+    P-weighted Exp(1) draws is sqrt(sum P^2) / sum P); the evolved spectrum
+    carries sum |h~(k, t)|^2 = 2 sum P in expectation (h~ holds the +k and -k
+    draws), checked at three times on the realistic 512^2 grid; and the
+    background's mean square equals sum |h~|^2 (Parseval for the
+    unnormalised inverse)."""
+    cfg = wl.realistic()["spectrum"]
+    spec = sp.Spectrum(cfg)
+    N, L = 512, 1000.0
+    P = bg.power(spec, N, L)
+    h0 = bg.h0_grid(spec, N, L, int(cfg["seed"]))
+    se = math.sqrt((P ** 2).sum()) / P.sum()
+    assert abs((np.abs(h0) ** 2).sum() / P.sum() - 1.0) < 5.0 * se
+    for t in (0.0, 3.7, 41.0):
+        ht, _, _ = bg.evolve(spec, h0, L, t, 1.0)
+        e = (np.abs(ht) ** 2).sum()
+        assert abs(e / (2.0 * P.sum()) - 1.0) < 5.0 * math.sqrt(2.0) * se
+        h, _, _, _ = bg.background(spec, h0, L, t, 1.0)
+        assert (h ** 2).mean() == pytest.approx(e, rel=1e-10)

@@ -237,3 +237,75 @@ def test_literal_over_normalised_energy_is_the_midpoint_rule():
         devs.append(np.abs(ratio[1:-1] - 1).max())
     assert devs[0] > devs[1] > devs[2]
     assert devs[2] < 0.025
+
+
+# ---- Eq. 3: the JONSWAP peak enhancement gamma^r and its two sigma branches
+def _gamma1_twin(cfg):
+    """The same spectrum with gamma = 1: alpha and wp (Eqs. 2 and 4) do not
+    depend on gamma, so the ratio S / S_{gamma=1} is the peak factor alone."""
+    return sp.Spectrum(dict(cfg, gamma=1.0))
+
+
+@pytest.mark.parametrize("gamma", [3.3, 0.0])   # given, and Eq. 4's (gamma <= 0)
+def test_jonswap_peak_factor_sigma_branches(gamma):
+    """Eq. 3: S(w) / S_{gamma=1}(w) = gamma^r, r = exp(-(w - wp)^2 / (2 sigma^2 wp^2)).
+    At w = wp the ratio is gamma exactly; at w = wp (1 + d) it is
+    gamma^exp(-d^2 / (2 sigma^2)) with sigma = 0.07 below the peak and 0.09
+    above.  A swapped sigma, a dropped square or a wrong branch fails."""
+    cfg = wl.spectrum(wind_speed=13.0, fetch=70e3, gamma=gamma)
+    spec = sp.Spectrum(cfg)
+    base = _gamma1_twin(cfg)
+    assert spec.wp == base.wp and spec.alpha == base.alpha
+    g = spec.gamma
+    assert spec.S1s(spec.wp) / base.S1s(spec.wp) == pytest.approx(g, rel=1e-14)
+    for d in (-0.3, -0.2, -0.1, -0.05, -0.01, 0.01, 0.05, 0.1, 0.2, 0.3):
+        w = spec.wp * (1.0 + d)
+        sigma = 0.07 if d < 0 else 0.09
+        want = g ** math.exp(-d * d / (2.0 * sigma * sigma))
+        assert spec.S1s(w) / base.S1s(w) == pytest.approx(want, rel=1e-13), d
+    # the two flanks differ: the same |d| gives a larger factor above the peak
+    lo = spec.S1s(spec.wp * 0.9) / base.S1s(spec.wp * 0.9)
+    hi = spec.S1s(spec.wp * 1.1) / base.S1s(spec.wp * 1.1)
+    assert hi > lo > 1.0
+
+
+def test_jonswap_eq4_gamma_at_a_decade_of_dimensionless_fetch():
+    """Eq. 4: gamma = 7.0 (g F / U^2)^-0.142.  With g F / U^2 = 10^4 that is
+    7 * 10^-0.568 = 1.8927708548762 (30-digit decimal arithmetic); seen through the spectrum itself as the peak
+    factor S(wp) / S_{gamma=1}(wp).  At 10^3 and 10^5 the factor follows the
+    same power law (ratio 10^0.142 per decade)."""
+    U = 10.0
+    vals = []
+    for dec in (3, 4, 5):
+        F = 10.0 ** dec * U * U / G
+        cfg = wl.spectrum(wind_speed=U, fetch=F, gamma=0.0)
+        spec = sp.Spectrum(cfg)
+        vals.append(spec.S1s(spec.wp) / _gamma1_twin(cfg).S1s(spec.wp))
+    assert vals[1] == pytest.approx(1.8927708548762, rel=1e-12)
+    assert vals[0] / vals[1] == pytest.approx(10.0 ** 0.142, rel=1e-12)
+    assert vals[1] / vals[2] == pytest.approx(10.0 ** 0.142, rel=1e-12)
+
+
+def test_literal_ratio_per_bucket_against_independent_quadrature():
+    """Eq. A's per-bucket energy S(w_i) dw_i sum_j Dir_ij dtheta over the exact
+    bucket integral E_i, checked bucket by bucket: E_i against a composite
+    Simpson rule of its own (4000 panels per bucket, independent of the
+    oracle's adaptive quadrature) and the LITERAL/NORMALIZED ratio against
+    S_1(w_i) dw_i sum_j Dir_ij dtheta / E_i built from that Simpson value."""
+    n = 64
+    spec = sp.Spectrum(wl.spectrum(n_buckets=n, n_theta=16))
+    b = sp.Buckets(spec, n)
+    lit = sp.amplitudes(spec, b, 16, sp.AMP_LITERAL)
+    nor = sp.amplitudes(spec, b, 16, sp.AMP_NORMALIZED)
+    ratio = (lit ** 2).sum(axis=1) / (nor ** 2).sum(axis=1)
+    dth = 2 * math.pi / 16
+    _, rel, _ = sp.directions(spec.theta_w, 16)
+    for i in range(n):
+        a, c = b.edges[i], b.edges[i + 1]
+        x = np.linspace(a, c, 4001)
+        y = spec.S1(x)
+        simpson = (c - a) / 12000.0 * (y[0] + y[-1] + 4 * y[1:-1:2].sum() + 2 * y[2:-1:2].sum())
+        assert b.E[i] == pytest.approx(simpson, rel=1e-10)
+        dsum = float(np.sum(spec.Dir(b.omega[i], rel))) * dth
+        want = spec.S1s(b.omega[i]) * (c - a) * dsum / simpson
+        assert ratio[i] == pytest.approx(want, rel=1e-9), i
