@@ -48,7 +48,9 @@ typedef enum {
     SCWP_E_CAPACITY = 3,  /* particle pool full: injection was truncated   */
     SCWP_E_CUDA = 4,      /* CUDA error (sticky)                           */
     SCWP_E_TIMEOUT = 5,   /* a bounded device wait gave up (sticky)        */
-    SCWP_E_STATE = 6      /* call not valid in the current state           */
+    SCWP_E_STATE = 6,     /* call not valid in the current state           */
+    SCWP_E_INCOMPLETE = 7 /* a synthesis limit was reached: a bucket's share
+                             is missing from some tile of the last maps     */
 } scwp_status;
 
 enum { SCWP_SPECTRUM_JONSWAP = 0, SCWP_SPECTRUM_PHILLIPS = 1 };
@@ -125,7 +127,9 @@ typedef struct scwp_spectrum_desc {
  * steady state.  With `emitter`, an object of radius obj_radius moves on a
  * circle of radius obj_path_radius about the patch centre at obj_speed and
  * emits wake_rate particles per Kelvin arm per frame into the bucket whose
- * radius is closest to obj_radius, amplitude wake_amp. */
+ * radius is closest to obj_radius, amplitude wake_amp.  The wake's and the
+ * ring ripples' spawn points are placed on the host in float64 (they decide
+ * integer positions); the GPU path itself uses no float64. */
 typedef struct scwp_patch_desc {
     double origin_x, origin_y; /* world position of the patch corner, m    */
     double cell;               /* texel size, m                            */
@@ -137,7 +141,7 @@ typedef struct scwp_patch_desc {
     int32_t bin_cells;         /* bin side in texels; <= 0: automatic      */
     int32_t emitter;           /* 0/1                                      */
     double obj_radius, obj_speed, obj_path_radius, wake_amp;
-    int32_t wake_rate;         /* particles per arm per frame              */
+    int32_t wake_rate;         /* particles per arm per frame, 0..64       */
     int32_t n_buckets;         /* <= 0: the spectrum's                     */
     double heave_period;       /* s; > 0 (with emitter): the object heaves and emits
                                   ring ripples (Sec. 4.3, vertical motion)  */
@@ -153,7 +157,10 @@ typedef struct scwp_stats {
     int64_t eval_count;        /* sum over binned bumps of texels in support */
     int64_t injected_total;    /* particles injected since creation        */
     int32_t n_buckets;
-    int32_t error_flags;       /* bit 0: capacity, bit 1: timeout          */
+    int32_t error_flags;       /* bit 0: particle pool full (injection truncated);
+                                  bit 1: a bounded device wait timed out;
+                                  bit 2: a synthesis limit was reached (a bucket
+                                  of some tile was left out of the maps)   */
     int64_t live_per_bucket[SCWP_MAX_BUCKETS];
     double injected_energy[SCWP_MAX_BUCKETS]; /* sum 1/8 A^2 pi r^2 (Eq. 12 / rho g) */
     int64_t mma_stages;        /* operand stages (6 MMAs of 128x128x16 each) the last
@@ -216,11 +223,23 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
  * velocity tables are rebuilt (float64, host) whenever dt changes. */
 scwp_status scwp_step(scwp_ctx* ctx, double dt);
 
-/* Copy a finished map: patch_id >= 0 a patch's blended map (height x
- * width), patch_id = -1 the background (N x N).  dst_elems must be at
+/* Copy one field of a finished map (Sec. 4.1-4.2: the frame's output is
+ * the height field and the choppy horizontal displacement, the WP patch
+ * blended into the FFT background across its boundary band):
+ * patch_id >= 0 a patch's blended map (height x width), patch_id = -1 the
+ * background (N x N); field SCWP_FIELD_H / DX / DY.  dst_elems must be at
  * least the map size.  dst_on_device = 1: device-to-device copy ordered on
  * the stream (asynchronous); 0: device-to-host copy, synchronises the
- * stream. */
+ * stream.  SCWP_E_INVALID for a bad field, patch_id or size. */
+scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field,
+                            float* dst, size_t dst_elems, int32_t dst_on_device);
+
+/* All three fields of a finished map in one copy: dst receives [3][rows][cols]
+ * (h, Dx, Dy planes, each as scwp_height_map gives it), dst_elems >= 3 x the
+ * map size.  One device-to-host copy and one synchronisation for a host dst
+ * (dst_on_device = 0); an asynchronous device-to-device copy otherwise. */
+scwp_status scwp_height_maps(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t dst_elems, int32_t dst_on_device);
+
 /* Unit normals of a patch's last blended maps, [3][height][width] (nx, ny,
  * nz): the normal of the displaced surface p(i, j) = (i c + Dx, j c + Dy, h)
  * (c = the patch's cell size) by finite differences, central inside the
@@ -230,10 +249,11 @@ scwp_status scwp_step(scwp_ctx* ctx, double dt);
  * dst_on_device as in scwp_height_map. */
 scwp_status scwp_normal_map(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t dst_elems, int32_t dst_on_device);
 
-scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field,
-                            float* dst, size_t dst_elems, int32_t dst_on_device);
 
-/* Statistics of a patch after the last frame (synchronises the stream). */
+/* Statistics of a patch after the last frame (synchronises the stream).
+ * The statistics are filled in every case; the status reports the frame's
+ * error flags: SCWP_E_TIMEOUT (sticky) for bit 1, SCWP_E_INCOMPLETE for
+ * bit 2, SCWP_E_CAPACITY for bit 0, SCWP_OK when none is set. */
 scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out);
 
 /* Table and bin geometry of a patch. */
@@ -312,11 +332,13 @@ scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_de
  * pre-registered buffers, plug-ins whose host owns every allocation).  The
  * paper has no counterpart: this is a deployment variant of the background
  * update of scwp_step (spectrum evolution + inverse 2-D FFT).
- *   h0     device, float32 complex interleaved [n][n] (FFT-natural order)
- *   omega  device, float64 [n][n] dispersion w(k)
+ *   h0     device, float32 complex interleaved [n][n] (FFT-natural order),
+ *          8-byte aligned
+ *   omega  device, float64 [n][n] dispersion w(k), 8-byte aligned
  *   n      grid size: power of two, 8 <= n <= 512; larger grids are refused
  *          with SCWP_E_INVALID (the scratch is sized for 512 x 512)
- *   out    device, float32 [3][n][n]: h, Dx, Dy at x_j = j fft_L / n
+ *   out    device, float32 [3][n][n]: h, Dx, Dy at x_j = j fft_L / n,
+ *          4-byte aligned
  *   stream cudaStream_t (NULL: the legacy stream); asynchronous
  * The scratch (4 MiB + 4 KiB) is one static __device__ array of the library:
  * every GPU that loads the library holds it until the process exits, and
@@ -324,8 +346,9 @@ scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_de
  * other threads) race and must be serialised by the caller.  The first call
  * on a device does a one-time set-up (looks up the array's address and
  * copies the twiddle table with a synchronous cudaMemcpy): make that first
- * call before any stream capture.  Returns SCWP_E_INVALID on bad arguments,
- * SCWP_E_CUDA if the set-up or a launch fails. */
+ * call before any stream capture.  Returns SCWP_E_INVALID on bad arguments
+ * (a null or misaligned pointer, a grid size out of range; nothing is
+ * launched), SCWP_E_CUDA if the set-up or a launch fails. */
 scwp_status scwp_background_noalloc(const float* h0, const double* omega, int32_t n, double fft_L,
                                     double choppiness, double t, float* out, void* stream);
 

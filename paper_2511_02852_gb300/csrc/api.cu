@@ -25,9 +25,13 @@
 using namespace scwp;
 
 namespace scwp {
-static std::atomic<long long> g_launches{0};
-void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+// Kernels enqueued by the calling thread.  A context call diffs this counter
+// around its own work, which runs on the caller's thread, so launches made
+// meanwhile by other threads (other contexts, the allocation-free
+// background call) are never charged to it.
+static thread_local long long t_launches = 0;
+void count_launches(int n) { t_launches += n; }
+long long launches_total() { return t_launches; }
 }  // namespace scwp
 
 namespace {
@@ -223,7 +227,7 @@ scwp_status check_patch_desc(const scwp_patch_desc* d, std::string& why) {
     if (d->prefill < 0) { why = "prefill < 0"; return SCWP_E_INVALID; }
     if (d->n_buckets > SCWP_MAX_BUCKETS) { why = "n_buckets out of range"; return SCWP_E_INVALID; }
     if (d->emitter) {
-        if (!(d->obj_path_radius > 0) || !(d->obj_radius > 0) || d->wake_rate < 0 || d->wake_rate > 1 << 20 ||
+        if (!(d->obj_path_radius > 0) || !(d->obj_radius > 0) || d->wake_rate < 0 || d->wake_rate > kMaxWakeRate ||
             d->ring_rate < 0 || d->ring_rate > 1 << 20 || d->heave_period < 0) {
             why = "emitter parameters";
             return SCWP_E_INVALID;
@@ -1018,16 +1022,17 @@ static void frame_injection(scwp_ctx* ctx, PatchHost* P, InjectParams& ip_out) {
             }
             P->energy[i] += mi * e;
         }
+    int given = 0;
     if (D.emitter && P->d.wake_rate > 0) {
         // reading of Sec. 4.3: object on a circle about the patch centre
         const double dx = P->d.cell;
         const double Rp = P->d.obj_path_radius / dx;
         const double Om = P->d.obj_speed / P->d.obj_path_radius;
         const double phi = Om * ctx->t;
-        ip.Px = T.W * 0.5 + Rp * std::cos(phi);
-        ip.Py = T.H * 0.5 + Rp * std::sin(phi);
+        const double Px = T.W * 0.5 + Rp * std::cos(phi);
+        const double Py = T.H * 0.5 + Rp * std::sin(phi);
         const double psi = phi + M_PI / 2.0;
-        ip.rho = P->d.obj_radius / dx;
+        const double rho = P->d.obj_radius / dx;
         const double kelvin = M_PI / 2.0 - std::asin(1.0 / 3.0);
         const double dpsi = 2.0 * M_PI / kWakeDirs;
         for (int arm = 0; arm < 2; ++arm) {
@@ -1035,8 +1040,7 @@ static void frame_injection(scwp_ctx* ctx, PatchHost* P, InjectParams& ip_out) {
             const double psa = psi + sgn * kelvin;
             int64_t a = (int64_t)std::floor(psa / dpsi + 0.5);
             a = ((a % kWakeDirs) + kWakeDirs) % kWakeDirs;
-            ip.ca[arm] = T.wake_cos[a];
-            ip.sa[arm] = T.wake_sin[a];
+            const double ca = T.wake_cos[a], sa = T.wake_sin[a];
             Segment& g = ip.seg[nseg++];
             g.bucket = T.wake_bucket;
             g.s = 2;
@@ -1045,7 +1049,21 @@ static void frame_injection(scwp_ctx* ctx, PatchHost* P, InjectParams& ip_out) {
             g.ndir = P->d.wake_rate;
             g.arm = arm;
             g.wake_a = (int)a;
+            g.given = given;
             total += g.count;
+            // spawn points on the object's rim, tangential offset tau uniform in
+            // [-rho, rho) from Philox word u0 at counter (frame, patch,
+            // bucket | 2 << 16, arm * rate + n):
+            // rint((P + rho (ca, sa) + tau (-sa, ca)) Q), float64 in this order
+            for (int n = 0; n < P->d.wake_rate; ++n) {
+                const uint32_t ord = (uint32_t)(arm * P->d.wake_rate + n);
+                const U4 u = philox4x32_10(ip.frame, ip.patch, (uint32_t)T.wake_bucket | (2u << 16), ord, ip.seed);
+                const double tau = (((double)u.x * 0x1p-32) - 0.5) * 2.0 * rho;
+                ip.gx[given] = (int32_t)std::nearbyint(((Px + rho * ca) - tau * sa) * (double)kQ);
+                ip.gy[given] = (int32_t)std::nearbyint(((Py + rho * sa) + tau * ca) * (double)kQ);
+                ip.ga[given] = (int32_t)a;
+                ++given;
+            }
             const double rw = T.r[T.wake_bucket];
             P->energy[T.wake_bucket] +=
                 P->d.wake_rate * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
@@ -1078,13 +1096,15 @@ static void frame_injection(scwp_ctx* ctx, PatchHost* P, InjectParams& ip_out) {
             g.count = n;
             g.first = total;
             g.ndir = n;
+            g.given = given;
             total += n;
             for (int k = 0; k < n; ++k) {
                 const int a = (int)((P->ring_total * 2531) % kWakeDirs);
                 P->ring_total += 1;
-                ip.ring_x[k] = (int32_t)std::nearbyint((Px + rho * T.wake_cos[a]) * (double)kQ);
-                ip.ring_y[k] = (int32_t)std::nearbyint((Py + rho * T.wake_sin[a]) * (double)kQ);
-                ip.ring_a[k] = a;
+                ip.gx[given] = (int32_t)std::nearbyint((Px + rho * T.wake_cos[a]) * (double)kQ);
+                ip.gy[given] = (int32_t)std::nearbyint((Py + rho * T.wake_sin[a]) * (double)kQ);
+                ip.ga[given] = a;
+                ++given;
             }
             const double rw = T.r[T.wake_bucket];
             P->energy[T.wake_bucket] += n * 0.125 * P->d.wake_amp * P->d.wake_amp * M_PI * rw * rw;
@@ -1400,6 +1420,31 @@ scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field, floa
     return SCWP_OK;
 }
 
+scwp_status scwp_height_maps(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t dst_elems, int32_t dst_on_device) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (!dst) return fail(ctx, SCWP_E_INVALID, "dst");
+    const float* src;
+    size_t n;
+    if (patch_id == -1) {
+        n = (size_t)ctx->d.fft_n * ctx->d.fft_n;
+        src = ctx->bgout;
+    } else {
+        if (patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "patch_id");
+        const PatchHost* P = ctx->patches[patch_id];
+        n = (size_t)P->T.W * P->T.H;
+        src = P->dev.out;
+    }
+    if (dst_elems < 3 * n) return fail(ctx, SCWP_E_INVALID, "dst too small");
+    if (dst_on_device) {
+        CU(cudaMemcpyAsync(dst, src, 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    } else {
+        CU(cudaMemcpyAsync(dst, src, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    return SCWP_OK;
+}
+
 scwp_status scwp_normal_map(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t dst_elems, int32_t dst_on_device) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;
@@ -1450,6 +1495,9 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
         out->injected_energy[i] = P->energy[i];
     }
     if (st[2] & kErrTimeout) return fail(ctx, SCWP_E_TIMEOUT, "a device wait timed out");
+    if (st[2] & kErrSynthLimit)
+        return fail(ctx, SCWP_E_INCOMPLETE, "a bucket's bin rows exceeded the synthesis row table; its share of some tile is missing");
+    if (st[2] & kErrCapacity) return fail(ctx, SCWP_E_CAPACITY, "particle pool full: injection was truncated");
     return SCWP_OK;
 }
 

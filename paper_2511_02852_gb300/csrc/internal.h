@@ -11,8 +11,11 @@ constexpr int kRotN = 128;          // per-bucket phase-rotation table length
 constexpr int kSortTile = 1024;     // keys per block of the binning radix sort
 constexpr int kMaxSegments = 2 * kMaxBuckets + 3;
 constexpr int kMaxRing = 64;        // ring-ripple particles emitted per frame at most
+constexpr int kMaxWakeRate = 64;    // wake particles per Kelvin arm per frame at most
+constexpr int kMaxGiven = kMaxRing + 2 * kMaxWakeRate;   // host-placed particles per frame
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrSynthLimit = 4u;   // a synthesis table limit left a bucket of a tile out
 
 // Per-bucket constants read by the binning and synthesis kernels.
 struct BucketDev {
@@ -92,13 +95,13 @@ struct BlendSpan {
 // One spawn segment of a frame's injection (Sec. 3.3 Eqs. 15-17 / Sec. 4.3).
 struct Segment {
     int32_t bucket;
-    int32_t s;       // 0, 1: edge pairs; 2: wake arm
+    int32_t s;       // 0, 1: edge pairs; 2: wake arm; 3: ring ripples
     int32_t count;   // particles in the segment
     int32_t first;   // prefix of counts
     int32_t ndir;    // edge: number of valid directions; wake: rate
     int32_t arm;     // wake: arm index (0: +, 1: -)
     int32_t wake_a;  // wake: direction grid index
-    int32_t vn;      // unused padding
+    int32_t given;   // wake and rings: first of the segment's host-placed positions
 };
 
 struct InjectParams {
@@ -108,13 +111,11 @@ struct InjectParams {
     uint32_t patch;
     uint64_t seed;
     int W, H, nth;
-    // wake (float64 reading: rint((P + rho*(ca,sa) +- tau*(-sa,ca)) Q))
-    double Px, Py, rho;
-    double ca[2], sa[2];
     Segment seg[kMaxSegments];
-    // ring ripples (s = 3): positions and wake-grid directions computed on
-    // the host in float64
-    int32_t ring_x[kMaxRing], ring_y[kMaxRing], ring_a[kMaxRing];
+    // wake (s = 2) and ring-ripple (s = 3) particles: Q16.16 positions and
+    // wake-grid directions placed on the host in float64 (the operations that
+    // decide these integers stay off the GPU)
+    int32_t gx[kMaxGiven], gy[kMaxGiven], ga[kMaxGiven];
 };
 
 struct SynthParams {
@@ -128,8 +129,8 @@ struct SynthParams {
     int b_lo, b_hi;         // buckets synthesised: [b_lo, b_hi) (a diagnostic range; default all)
 };
 
-// Every launcher reports how many kernels it enqueued (process-wide counter,
-// read by the ABI layer around each call).
+// Every launcher reports how many kernels it enqueued (a counter per host
+// thread, read by the ABI layer around each call).
 void count_launches(int n);
 
 // Programmatic dependent launch.  A kernel launched by launch_pdl may be

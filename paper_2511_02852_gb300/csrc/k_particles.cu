@@ -197,21 +197,11 @@ __device__ __forceinline__ void inject_body(const PatchDev& p, const InjectParam
             x = sg.s == 0 ? across : along;
             y = sg.s == 0 ? along : across;
             bd = ((uint32_t)sg.bucket << 16) | (uint32_t)j;
-        } else if (sg.s == 3) {   // ring ripples: positions given
-            x = ip.ring_x[le];
-            y = ip.ring_y[le];
-            bd = ((uint32_t)sg.bucket << 16) | (uint32_t)(ip.nth + ip.ring_a[le]);
-        } else {
-            const uint32_t ord = (uint32_t)(sg.arm * sg.ndir + le);
-            const U4 u = philox4x32_10(ip.frame, ip.patch, (uint32_t)sg.bucket | (2u << 16), ord, ip.seed);
-            const double ca = ip.ca[sg.arm], sa = ip.sa[sg.arm];
-            // tau = ((u 2^-32 - 1/2) 2) rho ; explicit rounding, no contraction
-            double tau = __dmul_rn(__dmul_rn(__dsub_rn(__dmul_rn((double)u.x, 0x1p-32), 0.5), 2.0), ip.rho);
-            const double fx = __dmul_rn(__dsub_rn(__dadd_rn(ip.Px, __dmul_rn(ip.rho, ca)), __dmul_rn(tau, sa)), 65536.0);
-            const double fy = __dmul_rn(__dadd_rn(__dadd_rn(ip.Py, __dmul_rn(ip.rho, sa)), __dmul_rn(tau, ca)), 65536.0);
-            x = (int32_t)__double2ll_rn(fx);
-            y = (int32_t)__double2ll_rn(fy);
-            bd = ((uint32_t)sg.bucket << 16) | (uint32_t)(ip.nth + sg.wake_a);
+        } else {   // wake arms and ring ripples: positions placed on the host
+            const int gi = sg.given + le;
+            x = ip.gx[gi];
+            y = ip.gy[gi];
+            bd = ((uint32_t)sg.bucket << 16) | (uint32_t)(ip.nth + ip.ga[gi]);
         }
         X[idx] = x;
         Y[idx] = y;

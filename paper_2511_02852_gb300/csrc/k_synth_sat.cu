@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
             const float amax = p.amax[b_begin + bi];
             if (ncand == 0 || !(amax > 0.f)) continue;   // no bump of this bucket reaches the tile
             if (S.nrows[bi] > kSatRowCap) {              // rows beyond the tables: not synthesised
-                if (tid == 0) atomicOr(p.stats + 2, (unsigned long long)kErrCapacity);
+                if (tid == 0) atomicOr(p.stats + 2, (unsigned long long)kErrSynthLimit);
                 continue;
             }
             const BucketDev bk = S.bk[bi];

@@ -71,6 +71,9 @@ extern "C" scwp_status scwp_background_noalloc(const float* h0, const double* om
                                                void* stream) {
     if (!h0 || !omega || !out || !(fft_L > 0)) return SCWP_E_INVALID;
     if (n < 8 || n > kNoAllocMaxN || (n & (n - 1)) != 0) return SCWP_E_INVALID;
+    // h0 is read as 8-byte complex pairs and omega as doubles: an address off
+    // that alignment would fault the kernel, so it is refused here
+    if ((((uintptr_t)h0 | (uintptr_t)omega) & 7u) != 0 || ((uintptr_t)out & 3u) != 0) return SCWP_E_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
@@ -90,6 +93,7 @@ extern "C" scwp_status scwp_background_noalloc(const float* h0, const double* om
     if (n < kNoAllocMaxN) {
         float2* small = scratch + 2 * (size_t)n * n;
         k_gather_twiddles<<<1, 256, 0, st>>>(full_tw, small, n, kNoAllocMaxN / n);
+        scwp::count_launches(1);
         tw = small;
     }
     scwp::BgDev bg;

@@ -26,7 +26,10 @@ SYNTH_GATHER, SYNTH_LAYERED, SYNTH_GATHER_FP32, SYNTH_GATHER_FP16, SYNTH_SAT = 0
 (TAB_OMEGA, TAB_K, TAB_C, TAB_R, TAB_E, TAB_EDGES, TAB_AMP, TAB_RQ, TAB_VX, TAB_VY, TAB_QX,
  TAB_QY, TAB_WAKE_VX, TAB_WAKE_VY, TAB_WAKE_QX, TAB_WAKE_QY, TAB_CARRY) = range(17)
 STATUS = {0: "SCWP_OK", 1: "SCWP_E_INVALID", 2: "SCWP_E_NOMEM", 3: "SCWP_E_CAPACITY",
-          4: "SCWP_E_CUDA", 5: "SCWP_E_TIMEOUT", 6: "SCWP_E_STATE"}
+          4: "SCWP_E_CUDA", 5: "SCWP_E_TIMEOUT", 6: "SCWP_E_STATE", 7: "SCWP_E_INCOMPLETE"}
+# statuses of scwp_stats_get that still fill the statistics: the frame's
+# error flags say what happened (bit 0 pool full, bit 2 synthesis limit)
+_STATS_FLAGGED = (3, 7)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -91,6 +94,7 @@ EXPORTS = {
     "scwp_add_patch": (C.c_int, [C.c_void_p, C.POINTER(scwp_patch_desc), C.POINTER(C.c_int32)]),
     "scwp_step": (C.c_int, [C.c_void_p, C.c_double]),
     "scwp_height_map": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]),
+    "scwp_height_maps": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]),
     "scwp_stats_get": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(scwp_stats)]),
     "scwp_patch_info_get": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(scwp_patch_info)]),
     "scwp_get_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t]),
@@ -185,9 +189,15 @@ def scwp_height_map(ctx, patch_id, field, dst_ptr, dst_elems, dst_on_device):
     _check(lib().scwp_height_map(ctx, patch_id, field, dst_ptr, dst_elems, dst_on_device), ctx)
 
 
+def scwp_height_maps(ctx, patch_id, dst_ptr, dst_elems, dst_on_device):
+    _check(lib().scwp_height_maps(ctx, patch_id, dst_ptr, dst_elems, dst_on_device), ctx)
+
+
 def scwp_stats_get(ctx, patch_id):
     st = scwp_stats()
-    _check(lib().scwp_stats_get(ctx, patch_id, C.byref(st)), ctx)
+    rc = lib().scwp_stats_get(ctx, patch_id, C.byref(st))
+    if rc not in _STATS_FLAGGED:
+        _check(rc, ctx)
     return st
 
 

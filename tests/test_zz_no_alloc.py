@@ -72,15 +72,22 @@ def test_noalloc_background_matches_step_twice_in_a_row(N):
         ref = sc.maps(-1)                              # the ordinary path's background
         t = sc.stats(0).time
         out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
         rc = L.scwp_background_noalloc(_ptr(h0_t), _ptr(om_t), N, float(s["fft_L"]),
                                        float(s["choppiness"]), t, _ptr(out), stream)
         assert rc == 0, scwp.STATUS.get(rc, rc)
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call's set-up, a call takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
         _compare(out.cpu().numpy(), ref, spec.Hs())
     sc.close()
 
 
-def test_noalloc_background_refuses_grids_beyond_its_scratch():
+def test_noalloc_background_refuses_bad_sizes_and_misaligned_pointers():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2511_02852_gb300 import scwp
@@ -90,3 +97,14 @@ def test_noalloc_background_refuses_grids_beyond_its_scratch():
     for n in (1024, 300, 4):
         rc = L.scwp_background_noalloc(_ptr(buf), _ptr(om), n, 100.0, 1.0, 0.0, _ptr(buf), None)
         assert rc == 1      # SCWP_E_INVALID, nothing launched
+    # misaligned inputs (a 4-byte offset into a float buffer) are refused
+    # before any launch, as is a misaligned output
+    off = C.c_void_p(buf.data_ptr() + 4)
+    rc = L.scwp_background_noalloc(off, _ptr(om), 16, 100.0, 1.0, 0.0, _ptr(buf), None)
+    assert rc == 1
+    rc = L.scwp_background_noalloc(_ptr(buf), C.c_void_p(om.data_ptr() + 4), 16, 100.0, 1.0, 0.0,
+                                   _ptr(buf), None)
+    assert rc == 1
+    rc = L.scwp_background_noalloc(_ptr(buf), _ptr(om), 16, 100.0, 1.0, 0.0,
+                                   C.c_void_p(buf.data_ptr() + 2), None)
+    assert rc == 1
