@@ -7,16 +7,20 @@
 
 One step = one whole frame of the hot path (background spectrum update and
 inverse FFT, advection/expiry/compaction, injection, wake emission, binning,
-synthesis with blend) on the workload's resident scene, by default in
-batched mode (several patches: frames replayed as CUDA graphs; one patch:
-eager launches chained by programmatic dependent launch) with the summed-area
-synthesis; the same frames in plain mode (one patch per launch, eager) and
-the tensor-core gather are timed on the same scene beside it.  The
-metric is particle-pixel (bump-texel) evaluations per second, the eval count
-being the exact integer count of (bump, texel-centre) pairs inside the
-kernel supports (checked bit-exact against the FP64 oracle by the tests);
-p50/p99 frame-step latency is reported beside it, and the same evals over the
-synthesis stage alone.
+synthesis with blend) on the workload's resident scene.  The default
+workload is the largest single-GPU scene, mixed_large (2048^2 FFT over 4 km,
+8 patches of 1024^2 texels, 2M particles each, 32 buckets), stepped in
+batched mode (one synthesis launch over all patches, frames replayed as
+captured CUDA graphs; a one-patch scene launches eagerly, chained by
+programmatic dependent launch) with the summed-area synthesis.  Beside it on
+the same line: the same scene in plain mode (one synthesis launch per
+patch, eager launches), the tensor-core gather, and the metric's "batched vs
+plain" on the 32-patch batched workload (--compare-frames frames in each
+mode).  The metric is particle-pixel (bump-texel) evaluations per second,
+the eval count being the exact integer count of (bump, texel-centre) pairs
+inside the kernel supports (checked bit-exact against the FP64 oracle by the
+tests); p50/p99 frame-step latency is reported beside it, and the same
+evals over the synthesis stage alone.
 
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
 scene's stream, L2 flushed (256 MiB write) between timed steps, barrier +
@@ -43,8 +47,6 @@ from paper_2511_02852_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "particle-pixel evals/s + frame-step p50/p99 ms, batched vs plain, at \u22641e-4\u00b7Hs"
 UNIT = "evals/s"
-# FP32 FMA issue-rate peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # tensor work of one operand stage of the tile gather: 6 MMAs of M = N = 128, K = 16
 FLOPS_PER_STAGE = 6 * 2 * 128 * 128 * 16
 # issue-rate peak of one GB300 in thread instructions: 152 SMs x 4 schedulers x
@@ -66,7 +68,10 @@ def tensor_peak():
         return v, "measured: bf16 cuBLAS GEMM burst (FP16 dense has the same nominal rate)"
     except Exception:
         return 1900.0, "fallback: 1.9 PFLOP/s bf16 burst (FP16 dense has the same nominal rate)"
-FLOPS_PER_EVAL = 6          # 3 FMAs per bump-texel (h, Dx, Dy)
+# algorithmic bytes of the background FFT per grid point: h0 read (8), the
+# two complex planes written by the row pass and read by the column pass
+# (16 + 16), h, Dx, Dy written (12)
+FFT_BYTES_PER_POINT = 52
 
 
 def workload_config(name, rank=0):
@@ -123,12 +128,17 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        # the timed region starts only once the sampler is delivering
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -164,6 +174,16 @@ class ClockSampler:
 
 
 # ---- CPU oracle ------------------------------------------------------------------
+def first_patch(cfg):
+    """The scene with its first patch only: patch 0 evolves exactly as in the
+    whole scene (its particles depend on its own description, index and the
+    seed), so the oracle's sample needs no other patch."""
+    import copy
+    c = copy.deepcopy(cfg)
+    c["patches"] = c["patches"][:1]
+    return c
+
+
 def oracle_strip_rate(cfg, target_s=10.0, frames=1, state=None, rows=None):
     """Time the FP64 oracle's synthesis on a strip of rows of patch 0 (a
     bounded sample of the frame; `rows` given: that many, else as many as
@@ -173,7 +193,7 @@ def oracle_strip_rate(cfg, target_s=10.0, frames=1, state=None, rows=None):
     from oracle.synth import synth_maps
     orc = state
     if orc is None:
-        orc = OracleScene(cfg)
+        orc = OracleScene(first_patch(cfg))
         for _ in range(frames):
             orc.step(cfg["dt"])
     ps = orc.patches[0]
@@ -221,7 +241,7 @@ def run_reference(args):
         return 0
     cfg = workload_config(args.workload)
     from oracle.scene import OracleScene
-    orc = OracleScene(cfg)
+    orc = OracleScene(first_patch(cfg))
     rates, times, evs = [], [], []
     rows_used = None
     # each step: the oracle's frame update plus a strip of the synthesis,
@@ -244,9 +264,9 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": describe(cfg),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": host_cpu(),
-                         "sample": f"per step: one oracle frame update of the whole scene plus the "
-                                   f"FP64 synthesis of a {rows_used}-row strip of the "
-                                   f"{cfg['patches'][0]['width']}-wide patch"},
+                         "sample": f"per step: one oracle frame update of patch 0 (of "
+                                   f"{len(cfg['patches'])}) plus the FP64 synthesis of a {rows_used}-row "
+                                   f"strip of that {cfg['patches'][0]['width']}-wide patch"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     one = oracle_rate_one_core(args.workload)
@@ -401,7 +421,7 @@ def host_cpu():
     return platform.processor() or platform.machine()
 
 
-def tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, fp16):
+def tc_roofline(sc, cfg, synth_ms, stage_info, fp16):
     """Tensor roofline of the tile gather (k_synth_tc with its bucket-group
     blend), timed by the library's events around the synthesis stage on the
     stream it launches on.  Executed tensor work: operand stages x the work of
@@ -412,20 +432,13 @@ def tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, fp16):
     mma_flops = stages * FLOPS_PER_STAGE // (3 if fp16 else 1)
     peak, peak_src = tensor_peak()
     achieved = mma_flops / (synth_ms / 1000.0) / 1e12
-    fp32_eq = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
-    r = {"bound": "tensor", "kernel": "k_synth_tc", "achieved": achieved, "peak": peak,
-         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-         "flops_per_launch": mma_flops, "operand_stages_per_launch": stages, "avg_launch_ms": synth_ms,
-         "fp32_equivalent": {"flops_per_launch": evals_per_step * FLOPS_PER_EVAL, "achieved": fp32_eq,
-                             "peak": FP32_PEAK_TFLOPS, "frac": fp32_eq / FP32_PEAK_TFLOPS,
-                             "note": "6 flop per bump-texel eval against the FP32 CUDA-core "
-                                     "FMA peak (152 SMs x 128 lanes x 2 flop x 2070 MHz)"},
-         "stage_ms": stage_info}
-    r["traffic"] = profiled_traffic(cfg, "k_synth_tc")
-    return r
+    return {"bound": "tensor", "kernel": "k_synth_tc", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(cfg, "k_synth_tc"),
+            "peak_source": peak_src, "flops_per_launch": mma_flops, "operand_stages_per_launch": stages,
+            "avg_launch_ms": synth_ms, "stage_ms": stage_info}
 
 
-def sat_roofline(sc, cfg, synth_ms, evals_per_step, stage_info):
+def sat_roofline(sc, cfg, synth_ms, stage_info):
     """ALU roofline of the summed-area synthesis (k_synth_sat with its
     bucket-group blend), timed by the library's events around the synthesis
     stage.  Algorithmic work: SAT_OPS_PER_TEXEL_BUCKET operations per (texel,
@@ -436,15 +449,34 @@ def sat_roofline(sc, cfg, synth_ms, evals_per_step, stage_info):
         tb += W * H * sc.info(p).n_buckets
     ops = tb * SAT_OPS_PER_TEXEL_BUCKET
     achieved = ops / (synth_ms / 1000.0) / 1e12
-    fp32_eq = evals_per_step * FLOPS_PER_EVAL / (synth_ms / 1000.0) / 1e12
     return {"bound": "alu", "kernel": "k_synth_sat", "achieved": achieved, "peak": ALU_PEAK_TOPS,
             "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS, "traffic": profiled_traffic(cfg, "k_synth_sat"),
             "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (thread instructions)",
             "ops_per_launch": ops, "texel_buckets_per_launch": tb, "avg_launch_ms": synth_ms,
-            "fp32_equivalent": {"flops_per_launch": evals_per_step * FLOPS_PER_EVAL, "achieved": fp32_eq,
-                                "peak": FP32_PEAK_TFLOPS, "frac": fp32_eq / FP32_PEAK_TFLOPS,
-                                "note": "the direct gather's 6 flop per bump-texel eval, for the same sums"},
             "stage_ms": stage_info}
+
+
+def fft_roofline(cfg, fft_ms):
+    """HBM roofline of the background FFT (k_spectrum_rows + k_fft_cols with
+    the spectrum update fused in), timed by the library's events on the side
+    stream it runs on.  Algorithmic bytes per grid point: FFT_BYTES_PER_POINT
+    (h0 read, the two complex planes written by the row pass and read by the
+    column pass, h, Dx, Dy written)."""
+    N = int(cfg["spectrum"]["fft_n"])
+    peak, src = hbm_peak()
+    nbytes = FFT_BYTES_PER_POINT * N * N
+    achieved = nbytes / (fft_ms / 1000.0) / 1e9
+    return {"bound": "hbm", "kernel": "k_spectrum_rows + k_fft_cols", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(cfg, "fft"),
+            "peak_source": src, "bytes_per_launch": nbytes, "grid": f"{N}^2", "avg_launch_ms": fft_ms}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured: STREAM-style copy (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback: 6.8 TB/s"
 
 
 def profiled_traffic(cfg, kernel):
@@ -459,6 +491,58 @@ def profiled_traffic(cfg, kernel):
         if e.get("workload") == cfg["name"] and e.get("kernel") == kernel:
             return e.get("dram_bytes_per_launch")
     return None
+
+
+def pct(ms_sorted, q):
+    return ms_sorted[min(len(ms_sorted) - 1, max(0, int(math.ceil(q * len(ms_sorted))) - 1))]
+
+
+def timed_frames(sc, cfg, n, flush, stream):
+    """n frames timed one by one with CUDA events on the scene's stream (L2
+    flushed before each); returns (sorted ms list, evals)."""
+    import torch
+    st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    ev = 0
+    for k in range(n):
+        flush.zero_()
+        st_ev[k].record(stream)
+        sc.step(cfg["dt"])
+        en_ev[k].record(stream)
+        ev += sum(sc.stats(p).eval_count for p in range(len(cfg["patches"])))
+    torch.cuda.synchronize()
+    return sorted(a.elapsed_time(b) for a, b in zip(st_ev, en_ev)), ev
+
+
+def frame_summary(ms, ev, mode):
+    return {"mode": mode, "frames": len(ms), "value": ev / (sum(ms) / 1000.0), "unit": UNIT,
+            "ms_per_step": sum(ms) / len(ms), "frames_per_s": 1000.0 * len(ms) / sum(ms),
+            "p50_ms": pct(ms, 0.5), "p99_ms": pct(ms, 0.99), "max_ms": ms[-1]}
+
+
+def batched_vs_plain(args, flush, stream, frames):
+    """The metric's "batched vs plain" on the 32-patch batched workload: the
+    same scene stepped in batched mode (one synthesis launch over every
+    patch, frames replayed as captured CUDA graphs) and in plain mode (one
+    synthesis launch per patch, eager launches), `frames` timed frames each."""
+    import torch
+    from paper_2511_02852_gb300 import scwp
+    cfg = workload_config("batched")
+    sc = scwp.Scene(cfg)
+    sc.set_synth_mode(scwp.SYNTH_SAT)
+    out = {"workload": describe(cfg)["workload"]}
+    for mode, on in (("batched", True), ("plain", False)):
+        sc.set_batched(on)
+        for _ in range(5):
+            flush.zero_()
+            sc.step(cfg["dt"])
+        torch.cuda.synchronize()
+        ms, ev = timed_frames(sc, cfg, frames, flush, stream)
+        out[mode] = frame_summary(ms, ev, "one synthesis launch over all 32 patches, captured frame graph"
+                                  if on else "one synthesis launch per patch, eager launches")
+    out["speedup_frames_per_s"] = out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]
+    sc.close()
+    return out
 
 
 def run_ours(args):
@@ -482,6 +566,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     dt = cfg["dt"]
+    npatch = len(cfg["patches"])
 
     def barrier():
         if world > 1:
@@ -493,13 +578,6 @@ def run_ours(args):
         sc.step(dt)
     barrier()
     launches0 = sc.launch_count()
-    # library stage events force one-kernel-at-a-time launches; batched
-    # frames are timed as launched (captured graphs when the scene has
-    # several patches) and broken down into stages by a separate run below
-    stage_events = not args.batched
-    if stage_events:
-        sc.set_timing(True)
-        sc.timing_read()
     props = torch.cuda.get_device_properties(local)
     clk = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None) else local)
     clk.start()
@@ -512,64 +590,47 @@ def run_ours(args):
         starts[k].record(stream)
         sc.step(dt)
         ends[k].record(stream)
-        evals.append(sc.stats(0).eval_count + sum(sc.stats(p).eval_count
-                                                  for p in range(1, len(cfg["patches"]))))
+        evals.append(sum(sc.stats(p).eval_count for p in range(npatch)))
     barrier()
-    clocks = clk.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     launches = sc.launch_count() - launches0
-    if stage_events:
-        stage_ms, frames = sc.timing_read()
-        sc.set_timing(False)
-    else:
-        sc.set_timing(True)
-        sc.timing_read()
-        for _ in range(min(args.steps, 20)):
-            flush.zero_()
-            sc.step(dt)
-        torch.cuda.synchronize()
-        stage_ms, frames = sc.timing_read()
-        sc.set_timing(False)
+    # stage breakdown: library events force one-kernel-at-a-time launches, so
+    # it comes from eager frames after the timed ones
+    sc.set_timing(True)
+    sc.timing_read()
+    for _ in range(min(max(args.steps, 5), 20)):
+        flush.zero_()
+        sc.step(dt)
+    torch.cuda.synchronize()
+    stage_ms, frames = sc.timing_read()
+    sc.set_timing(False)
     total_s = sum(step_ms) / 1000.0
     total_evals = sum(evals)
     total_s_all, total_evals_all = reduce_over_ranks(total_s, total_evals, world, "cuda")
     value = total_evals_all / total_s_all
 
     synth_ms = stage_ms[2] / max(frames, 1)
+    fft_ms = stage_ms[0] / max(frames, 1)
     evals_per_step = total_evals / args.steps
-    stage_info = {"source": "library events on the timed frames" if stage_events else
-                            "library events on eager frames after the timed ones",
-                  "fft": stage_ms[0] / max(frames, 1), "particles": stage_ms[1] / max(frames, 1),
+    stage_info = {"source": "library events on eager frames after the timed ones",
+                  "fft": fft_ms, "particles": stage_ms[1] / max(frames, 1),
                   "synth_blend": synth_ms, "frame": stage_ms[3] / max(frames, 1)}
     if args.synth == "sat":
-        roofline = sat_roofline(sc, cfg, synth_ms, evals_per_step, stage_info)
+        roofline = sat_roofline(sc, cfg, synth_ms, stage_info)
     else:
-        roofline = tc_roofline(sc, cfg, synth_ms, evals_per_step, stage_info, args.synth == "fp16")
-    # the same scene and synthesis in plain mode (one patch per launch, eager
-    # launches, no graph), timed like the main loop: batched vs plain on
-    # every line
+        roofline = tc_roofline(sc, cfg, synth_ms, stage_info, args.synth == "fp16")
+    roof_fft = fft_roofline(cfg, fft_ms)
+
+    # the same scene in plain mode (one patch per launch, eager launches)
     plain = None
     if args.batched and not args.no_compare:
         sc.set_batched(False)
         for _ in range(3):
             flush.zero_()
             sc.step(dt)
-        n_pl = max(10, min(args.steps // 4, 150))
-        st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_pl)]
-        en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_pl)]
-        ev_p = 0
-        for k in range(n_pl):
-            flush.zero_()
-            st_ev[k].record(stream)
-            sc.step(dt)
-            en_ev[k].record(stream)
-            ev_p += sum(sc.stats(p).eval_count for p in range(len(cfg["patches"])))
-        torch.cuda.synchronize()
-        pm = sorted(a.elapsed_time(b) for a, b in zip(st_ev, en_ev))
+        ms, ev = timed_frames(sc, cfg, max(10, min(args.steps, 50)), flush, stream)
         sc.set_batched(True)
-        plain = {"mode": "plain: one patch per launch, eager launches", "frames": n_pl,
-                 "value": ev_p / (sum(pm) / 1000.0), "unit": UNIT, "ms_per_step": sum(pm) / n_pl,
-                 "p50_ms": pm[len(pm) // 2], "p99_ms": pm[min(len(pm) - 1, int(math.ceil(0.99 * len(pm))) - 1)]}
+        plain = frame_summary(ms, ev, "plain: one synthesis launch per patch, eager launches")
 
     # the other synthesis on the same scene: the tensor-core gather beside the
     # summed-area default (its own roofline), for comparison
@@ -581,12 +642,12 @@ def run_ours(args):
             sc.step(dt)
         sc.set_timing(True)
         sc.timing_read()
-        n_cmp = max(10, min(args.steps // 4, 150))
+        n_cmp = 10
         ev_c = 0
         for _ in range(n_cmp):
             flush.zero_()
             sc.step(dt)
-            ev_c += sum(sc.stats(p).eval_count for p in range(len(cfg["patches"])))
+            ev_c += sum(sc.stats(p).eval_count for p in range(npatch))
         torch.cuda.synchronize()
         ms_c, fr_c = sc.timing_read()
         sc.set_timing(False)
@@ -594,18 +655,22 @@ def run_ours(args):
         s_ms = ms_c[2] / max(fr_c, 1)
         other = {"synthesis": "tensor-core tile gather (SCWP_SYNTH_GATHER)", "frames": n_cmp,
                  "value": ev_c / (ms_c[3] / 1000.0), "unit": UNIT, "ms_per_step": ms_c[3] / max(fr_c, 1),
-                 "roofline": tc_roofline(sc, cfg, s_ms, ev_c / n_cmp,
+                 "roofline": tc_roofline(sc, cfg, s_ms,
                                          {"source": "library events, eager frames", "fft": ms_c[0] / max(fr_c, 1),
                                           "particles": ms_c[1] / max(fr_c, 1), "synth_blend": s_ms,
                                           "frame": ms_c[3] / max(fr_c, 1)}, False)}
 
-    # end to end through the C ABI: step + read of the blended maps to pinned host memory
+    # batched vs plain on the 32-patch batched workload (the metric's comparison)
+    bvp = None
+    if rank == 0 and not args.no_compare and args.workload != "batched":
+        bvp = batched_vs_plain(args, flush, stream, args.compare_frames)
+
+    # end to end through the C ABI: step + one copy of each patch's three
+    # blended planes into pinned host memory
     e2e = None
     if not args.no_e2e:
-        npatch = len(cfg["patches"])
         shapes = [sc.patch_shape(p) for p in range(npatch)]
-        host = [[torch.empty((H, W), dtype=torch.float32, pin_memory=True) for _ in range(3)]
-                for (H, W) in shapes]
+        host = [torch.empty((3, H, W), dtype=torch.float32, pin_memory=True) for (H, W) in shapes]
         import ctypes as C
         barrier()
         t0 = time.perf_counter()
@@ -613,23 +678,24 @@ def run_ours(args):
         for k in range(args.steps):
             sc.step(dt)
             for p, (H, W) in enumerate(shapes):
-                for f in range(3):
-                    scwp.scwp_height_map(sc.ctx, p, f, C.c_void_p(host[p][f].data_ptr()), H * W, 0)
+                scwp.scwp_height_maps(sc.ctx, p, C.c_void_p(host[p].data_ptr()), 3 * H * W, 0)
                 e2e_evals += sc.stats(p).eval_count
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8,
+        plan = sum(sc.info(p).frame_param_bytes for p in range(npatch))
+        e2e = {"value": e2e_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 + plan,
                "d2h_bytes_per_step": sum(3 * H * W * 4 for (H, W) in shapes),
-               "note": "scwp_step + scwp_height_map of h, Dx, Dy into pinned host buffers; "
-                       "the per-step host input is dt (the injection counts and wake state are "
-                       "computed by the library on the host and passed as kernel arguments)"}
+               "note": "scwp_step + scwp_height_maps (one device-to-host copy of h, Dx, Dy per patch) "
+                       "into pinned host memory, wall clock; host-to-device per step: dt and each "
+                       "patch's frame plan (injection counts and host-placed spawn points)"}
+    clocks = clk.stop()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, ev, secs, rows, threads = oracle_strip_rate(cfg, target_s=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": host_cpu(),
                "sample": f"FP64 oracle synthesis of a {rows}-row strip of the "
-                         f"{cfg['patches'][0]['width']}-wide patch after one frame "
+                         f"{cfg['patches'][0]['width']}-wide patch 0 after one frame "
                          f"({ev} evals in {secs:.1f} s)"}
         one = oracle_rate_one_core(args.workload)
         if one is not None:
@@ -639,8 +705,6 @@ def run_ours(args):
 
     if rank == 0:
         ms_sorted = sorted(step_ms)
-        p50 = ms_sorted[len(ms_sorted) // 2]
-        p99 = ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -650,16 +714,16 @@ def run_ours(args):
                       "fp16": "f16 operands, f32 sums"}[args.synth],
             "data": "synthetic", "config": dict(describe(cfg), parallelism=f"replicas{world}",
                                                 mode="batched" if args.batched else "plain",
-                                                synthesis=args.synth,
-                                                synth_groups=[sc.info(p).sat_groups if args.synth == "sat"
-                                                              else sc.info(p).synth_groups
-                                                              for p in range(len(cfg["patches"]))]),
-            "p50_ms": p50, "p99_ms": p99, "evals_per_step": evals_per_step,
+                                                synthesis=args.synth),
+            "p50_ms": pct(ms_sorted, 0.5), "p99_ms": pct(ms_sorted, 0.99), "evals_per_step": evals_per_step,
             # the same evals over the synthesis stage alone (library events)
             "synthesis_evals_per_s": evals_per_step / (synth_ms / 1000.0) if synth_ms > 0 else None,
-            "live_particles": sc.stats(0).live_particles,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "plain": plain, "gather_tc": other,
+            "live_particles": sum(sc.stats(p).live_particles for p in range(npatch)),
+            "roofline": roofline, "roofline_fft": roof_fft, "cpu_baseline": cpu, "e2e": e2e,
+            "plain": plain, "batched_vs_plain": bvp, "gather_tc": other,
             "gpu_launches": launches, "clocks": clocks,
+            "synth_groups": [sc.info(p).sat_groups if args.synth == "sat" else sc.info(p).synth_groups
+                             for p in range(npatch)],
         }
         print(json.dumps(line))
     sc.close()
@@ -674,7 +738,9 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="realistic", choices=sorted(wl.ALL) + ["serving", "sweep"])
+    ap.add_argument("--workload", default="mixed_large", choices=sorted(wl.ALL) + ["serving", "sweep"])
+    ap.add_argument("--compare-frames", type=int, default=200,
+                    help="frames timed in each mode of the batched-vs-plain comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0)

@@ -183,6 +183,8 @@ typedef struct scwp_patch_info {
     int32_t sat_groups;        /* bucket groups of the summed-area synthesis */
     int32_t sat_items;         /* its (tile, group) work items */
     int32_t sat_slots;         /* resident CTA slots its plan assumed */
+    int32_t frame_param_bytes; /* host-computed plan of one frame of this patch (injection
+                                  counts, host-placed spawn points) copied to the device */
 } scwp_patch_info;
 
 /* Table identifiers for scwp_get_table (element type, count). */
@@ -292,11 +294,11 @@ scwp_status scwp_resynthesize(scwp_ctx* ctx, int32_t mode);
 /* Select the synthesis used by scwp_step (SCWP_SYNTH_*). */
 scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode);
 
-/* Diagnostic: the tensor-core synthesis modes sum only the buckets
- * b_lo <= i < b_hi (clamped to each patch's count; default all), so that
- * the error against the FP64 oracle can be stated per bucket.  The paper has
- * no counterpart.  SCWP_E_INVALID if b_lo < 0 or b_hi <= b_lo.  The other
- * synthesis modes ignore the range. */
+/* Diagnostic: the summed-area and tensor-core synthesis modes sum only the
+ * buckets b_lo <= i < b_hi (clamped to each patch's count; default all), so
+ * that the error against the FP64 oracle can be stated per bucket.  The
+ * paper has no counterpart.  SCWP_E_INVALID if b_lo < 0 or b_hi <= b_lo.
+ * The CUDA-core gather and the layered mode ignore the range. */
 scwp_status scwp_set_bucket_range(scwp_ctx* ctx, int32_t b_lo, int32_t b_hi);
 
 /* Batched frame step (on != 0): the synthesis of all patches of

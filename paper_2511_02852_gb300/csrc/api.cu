@@ -1521,6 +1521,7 @@ scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info
     out->sat_groups = P->sat_groups;
     out->sat_items = (int32_t)P->sat_items.size();
     out->sat_slots = P->sat_slots;
+    out->frame_param_bytes = (int32_t)sizeof(InjectParams);
     for (int i = 0; i < P->T.nb; ++i) {
         out->bin_cells[i] = P->bin_cells[i];
         out->nbx[i] = P->bk[i].nbx;

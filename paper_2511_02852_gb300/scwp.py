@@ -75,7 +75,8 @@ class scwp_patch_info(C.Structure):
                 ("bin_cells", C.c_int32 * MAX_BUCKETS), ("nbx", C.c_int32 * MAX_BUCKETS),
                 ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS),
                 ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32),
-                ("sat_groups", C.c_int32), ("sat_items", C.c_int32), ("sat_slots", C.c_int32)]
+                ("sat_groups", C.c_int32), ("sat_items", C.c_int32), ("sat_slots", C.c_int32),
+                ("frame_param_bytes", C.c_int32)]
 
 
 class scwp_server_desc(C.Structure):
@@ -318,12 +319,9 @@ class Scene:
         """Blended (h, Dx, Dy) of patch p (or the background for p = -1) as
         host float32 arrays."""
         shape = (self.N, self.N) if p == -1 else self.patch_shape(p)
-        out = []
-        for f in range(3):
-            a = np.empty(shape, dtype=np.float32)
-            scwp_height_map(self.ctx, p, f, a.ctypes.data_as(C.c_void_p), a.size, 0)
-            out.append(a)
-        return out
+        a = np.empty((3,) + shape, dtype=np.float32)
+        scwp_height_maps(self.ctx, p, a.ctypes.data_as(C.c_void_p), a.size, 0)
+        return [a[0], a[1], a[2]]
 
     def maps_device(self, p, out):
         """Copy the maps into a device tensor out[3][H][W] (stream-ordered)."""

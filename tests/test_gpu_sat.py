@@ -203,3 +203,21 @@ def test_sat_fine_bins_many_rows_and_three_radix_passes():
     compare_maps(sc.maps(0), ref, orc.spec.Hs(), "sat one-cell bins")
     assert sc.stats(0).error_flags == 0
     sc.close()
+
+
+def test_sat_row_table_limit_is_reported_apart_from_pool_overflow():
+    """One-cell bins on a 0.1 m patch whose longest bucket has R = 290
+    cells: 64 + 2R = 645 bin rows of that bucket reach a tile, more than the
+    summed-area kernel's 512-row table.  The kernel leaves that bucket out
+    of those tiles and says so: error flag bit 2 and SCWP_E_INCOMPLETE from
+    scwp_stats_get, not the pool-overflow flag."""
+    import ctypes as C
+    from paper_2511_02852_gb300 import scwp
+    cfg = wl.scaled(wl.small_jonswap(), bin_cells=1, cell=0.1)
+    sc = sat_scene(cfg)
+    sc.step(cfg["dt"])
+    st = scwp.scwp_stats()
+    rc = scwp.lib().scwp_stats_get(sc.ctx, 0, C.byref(st))
+    assert rc == 7, scwp.STATUS.get(rc, rc)          # SCWP_E_INCOMPLETE
+    assert st.error_flags & 4 and not st.error_flags & 1
+    sc.close()
