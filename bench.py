@@ -58,6 +58,11 @@ ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 # texel's u, u', v, v' factors (21 multiply-adds); the per-bump corner events
 # are not counted (a lower bound on the work)
 SAT_OPS_PER_TEXEL_BUCKET = 48
+# and per candidate bump of a (tile, bucket): its 9 corner weights (A p_i q_j)
+# and 4 corner adds of each (corners outside the tile are dropped, so this is
+# an upper bound on that part; the whole count stays algorithmic, independent
+# of how the kernel aggregates or orders the adds)
+SAT_OPS_PER_CANDIDATE = 45
 
 
 def tensor_peak():
@@ -97,13 +102,19 @@ def reduce_over_ranks(total_s, total_evals, world, device):
 
 def describe(cfg):
     s = cfg["spectrum"]
-    p = cfg["patches"][0]
+    ps = cfg["patches"]
+    p = ps[0]
+    nbs = sorted({int(q["n_buckets"]) if int(q["n_buckets"]) > 0 else int(s["n_buckets"]) for q in ps})
+    sides = sorted({(int(q["width"]), int(q["height"])) for q in ps})
+    shape = (f"{sides[0][0]}x{sides[0][1]}" if len(sides) == 1 else
+             f"{min(a * b for a, b in sides)}..{max(a * b for a, b in sides)} texels each")
     return {
         "workload": (f"{cfg['name']}: {'JONSWAP' if s['spectrum'] == 0 else 'Phillips'} "
                      f"U10={s['wind_speed']} m/s, {s['fft_n']}^2 FFT over {s['fft_L']} m, "
-                     f"{len(cfg['patches'])} patch(es) {p['width']}x{p['height']} at {p['cell']} m, "
-                     f"{s['n_buckets']} buckets x {s['n_theta']} directions, "
-                     f"{p['prefill']} prefilled particles, wake={'on' if p['emitter'] else 'off'}"),
+                     f"{len(ps)} patch(es) {shape} at {p['cell']} m, "
+                     f"{nbs[0] if len(nbs) == 1 else f'{nbs[0]}-{nbs[-1]}'} buckets x {s['n_theta']} directions, "
+                     f"{sum(int(q['prefill']) for q in ps)} prefilled particles in all, "
+                     f"wake={'on' if any(q['emitter'] for q in ps) else 'off'}"),
         "patches": len(cfg["patches"]),
         "fft_n": s["fft_n"],
         "patch_texels": sum(q["width"] * q["height"] for q in cfg["patches"]),
@@ -408,7 +419,15 @@ def run_sweep(args):
 
 # ---- ours ----------------------------------------------------------------------------
 def host_cpu():
-    """The host CPU's model name (from /proc/cpuinfo where it has one)."""
+    """The host CPU's model name (lscpu, else /proc/cpuinfo where it has one)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                return v.strip()
+    except Exception:
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
@@ -443,16 +462,21 @@ def sat_roofline(sc, cfg, synth_ms, stage_info):
     bucket-group blend), timed by the library's events around the synthesis
     stage.  Algorithmic work: SAT_OPS_PER_TEXEL_BUCKET operations per (texel,
     bucket) of every patch, against the instruction-issue peak."""
-    tb = 0
+    tb = cand = 0
     for p in range(len(cfg["patches"])):
         H, W = sc.patch_shape(p)
         tb += W * H * sc.info(p).n_buckets
-    ops = tb * SAT_OPS_PER_TEXEL_BUCKET
+        cand += sc.stats(p).sat_candidates
+    ops = tb * SAT_OPS_PER_TEXEL_BUCKET + cand * SAT_OPS_PER_CANDIDATE
     achieved = ops / (synth_ms / 1000.0) / 1e12
     return {"bound": "alu", "kernel": "k_synth_sat", "achieved": achieved, "peak": ALU_PEAK_TOPS,
             "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS, "traffic": profiled_traffic(cfg, "k_synth_sat"),
             "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (thread instructions)",
-            "ops_per_launch": ops, "texel_buckets_per_launch": tb, "avg_launch_ms": synth_ms,
+            "ops_per_launch": ops, "texel_buckets_per_launch": tb, "candidates_per_launch": cand,
+            "ops_note": f"{SAT_OPS_PER_TEXEL_BUCKET} per (texel, bucket): 9 components x (2 prefix adds + "
+                        f"1 conversion) + 21 contraction multiply-adds; {SAT_OPS_PER_CANDIDATE} per (candidate "
+                        f"bump, tile): 9 corner weights + 4 x 9 corner adds",
+            "avg_launch_ms": synth_ms,
             "stage_ms": stage_info}
 
 

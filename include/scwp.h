@@ -166,6 +166,9 @@ typedef struct scwp_stats {
     int64_t mma_stages;        /* operand stages (6 MMAs of 128x128x16 each) the last
                                   tensor-core synthesis committed; 0 for the other modes */
     int64_t eval_total;        /* eval_count summed over every frame stepped */
+    int64_t sat_candidates;    /* candidate bumps the last summed-area synthesis took, summed
+                                  over its (tile, bucket) pairs (each candidate: 4 corner
+                                  events of 9 components); 0 for the other modes */
 } scwp_stats;
 
 /* Scalar description of a patch's tables and bins. */

@@ -394,7 +394,10 @@ std::vector<double> tile_bucket_sat(const PatchHost& P, int& tiles) {
             const double y0 = (t / ntx) * ts - r, y1 = (t / ntx + 1) * ts + r;
             const double ax = std::max(0.0, std::min(x1 + c, T.W + r) - std::max(x0, -r));
             const double ay = std::max(0.0, std::min(y1 + c, T.H + r) - std::max(y0, -r));
-            est[(size_t)t * T.nb + i] = (kSatBucketUs + dens * ax * ay * kSatBumpUs) / kStageUs;
+            // dense pairs go in several passes, each with the fixed part
+            const double n = dens * ax * ay;
+            const double passes = std::max(1.0, std::ceil(n * std::sqrt(n) / (double)P.bk[i].sat_c));
+            est[(size_t)t * T.nb + i] = (passes * kSatBucketUs + n * kSatBumpUs) / kStageUs;
         }
     }
     return est;
@@ -553,6 +556,7 @@ SynthParams synth_params(scwp_ctx* ctx, const PatchHost& P) {
 scwp_status reset_frame_stats(scwp_ctx* ctx, PatchHost& P, cudaStream_t st) {
     CU(cudaMemsetAsync(P.dev.stats, 0, 2 * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(P.dev.stats + 3, 0, ((size_t)P.T.nb + 1) * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(P.dev.stats + 5 + P.T.nb, 0, sizeof(unsigned long long), st));
     return SCWP_OK;
 }
 
@@ -783,6 +787,27 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     D.emitter = desc->emitter ? 1 : 0;
     D.wake_amp = (float)desc->wake_amp;
     bin_geometry(*P);
+    // |A| bound per bucket: its directions' amplitudes and, with an emitter,
+    // the wake amplitude (wake directions may sit in any bucket)
+    std::vector<float> amax(T.nb, 0.f);
+    for (int i = 0; i < T.nb; ++i) {
+        for (int j = 0; j < T.nth; ++j) amax[i] = std::max(amax[i], std::fabs((float)T.amp[(size_t)i * T.nth + j]));
+        if (D.emitter) amax[i] = std::max(amax[i], std::fabs(D.wake_amp));
+    }
+    // Summed-area passes.  The kernel rounds each corner weight once to an
+    // integer unit of 2^-30 * 1.001 m A_max for a pass of m candidates; the
+    // rounding errors of the n candidates that reach a texel add up to about
+    // sqrt(n) m A_max 2^-31 per S_ij, of which 3/4 reach h (worst texel of a
+    // tile: ~2 sigma).  A (tile, bucket) of n candidates therefore goes in
+    // k = ceil(n^1.5 / c) passes of n / k candidates, c = eps Hs 2^31 /
+    // (0.6 A_max), which keeps that error under eps = 1e-5 Hs per bucket
+    // (one pass for every tile of the realistic and mixed_large scenes; up to
+    // tens on patches holding tens of particles per texel).
+    {
+        const double hs = 4.0 * std::sqrt(ctx->sm.m0());
+        for (int i = 0; i < T.nb; ++i)
+            P->bk[i].sat_c = amax[i] > 0 ? (float)(1e-5 * hs * 2147483648.0 / (0.6 * (double)amax[i])) : 3.0e38f;
+    }
     const size_t cap = (size_t)D.cap;
     D.nblk_c = (int)((cap + 1023) / 1024);
     D.nblk_s = (int)((2 * cap + kSortTile - 1) / kSortTile);
@@ -848,7 +873,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
             ok = ok && D.partial;
         }
     }
-    D.stats = (unsigned long long*)dalloc(ctx, (5 + (size_t)T.nb) * sizeof(unsigned long long));
+    D.stats = (unsigned long long*)dalloc(ctx, (6 + (size_t)T.nb) * sizeof(unsigned long long));
     ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.phase && D.amax && D.hist &&
          D.offsets && D.rec && D.out && D.stats;
     if (!ok) {
@@ -922,16 +947,9 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         }
     }
     CU(cudaMemcpyAsync(D.phase, phase.data(), phase.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
-    // |A| bound per bucket: its directions' amplitudes and, with an emitter,
-    // the wake amplitude (wake directions may sit in any bucket)
-    std::vector<float> amax(T.nb, 0.f);
-    for (int i = 0; i < T.nb; ++i) {
-        for (int j = 0; j < T.nth; ++j) amax[i] = std::max(amax[i], std::fabs(ampf[(size_t)i * T.nth + j]));
-        if (D.emitter) amax[i] = std::max(amax[i], std::fabs(D.wake_amp));
-    }
     CU(cudaMemcpyAsync(D.amax, amax.data(), amax.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
-    CU(cudaMemsetAsync(D.stats, 0, (5 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
+    CU(cudaMemsetAsync(D.stats, 0, (6 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));
     CU(cudaMemsetAsync(D.out, 0, (size_t)3 * T.W * T.H * sizeof(float), ctx->st));
     if (n0 > 0) {
@@ -1474,7 +1492,7 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
     if (s != SCWP_OK) return s;
     if (!out || patch_id < 0 || patch_id >= (int)ctx->patches.size()) return fail(ctx, SCWP_E_INVALID, "args");
     PatchHost* P = ctx->patches[patch_id];
-    std::vector<unsigned long long> st(5 + P->T.nb);
+    std::vector<unsigned long long> st(6 + P->T.nb);
     int32_t cnt[2];
     CU(cudaMemcpyAsync(st.data(), P->dev.stats, st.size() * 8, cudaMemcpyDeviceToHost, ctx->st));
     CU(cudaMemcpyAsync(cnt, P->dev.count, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
@@ -1489,6 +1507,7 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
     out->injected_total = P->injected;
     out->mma_stages = (int64_t)st[3 + P->T.nb];
     out->eval_total = (int64_t)st[4 + P->T.nb];
+    out->sat_candidates = (int64_t)st[5 + P->T.nb];
     out->n_buckets = P->T.nb;
     for (int i = 0; i < P->T.nb; ++i) {
         out->live_per_bucket[i] = (int64_t)st[3 + i];

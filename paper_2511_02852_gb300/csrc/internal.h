@@ -23,7 +23,9 @@ struct BucketDev {
     float invR;     // 1 / R (float)
     int32_t C;      // bin side, Q16.16 cells
     int32_t nbx, nby, base;  // bin grid and first key
-    int32_t pad0, pad1;
+    float sat_c;    // summed-area pass bound: a (tile, bucket) of n candidates goes in
+                    // ceil(n^1.5 / sat_c) passes of at most as many candidates each
+    int32_t pad1;
 };
 
 // A bump in bin order, as the synthesis kernels stage it (32 bytes).
@@ -75,7 +77,9 @@ struct PatchDev {
     int patch = 0;                        // index of the patch in its context
     unsigned long long* stats = nullptr;  // [0] evals, [1] binned, [2] flags, [3..3+nb) live per bucket,
                                           // [3+nb] operand stages of the last tensor-core synthesis,
-                                          // [4+nb] evals summed over all frames
+                                          // [4+nb] evals summed over all frames,
+                                          // [5+nb] candidates of the last summed-area synthesis
+                                          // (summed over its (tile, bucket) pairs)
     float* layers = nullptr;              // layered variant scratch (lazy)
     size_t layers_bytes = 0;
 };

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
         // bucket, operand stages; the error flags stay)
         if (threadIdx.x < 2) p.stats[threadIdx.x] = 0ull;
         if (threadIdx.x <= p.nb) p.stats[3 + threadIdx.x] = 0ull;
+        if (threadIdx.x == 0) p.stats[5 + p.nb] = 0ull;
     }
     const int base = blockIdx.x * kTileC;
     int32_t* X = p.x[p.cur];

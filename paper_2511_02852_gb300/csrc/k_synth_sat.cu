@@ -22,14 +22,17 @@
 // no longer grows with the number of bumps covering a texel.
 //
 // Exactness of the prefix sums: the corner weights are rounded once to
-// 32-bit integers with a per-(tile, bucket) scale 2^30 / (1.001 n A_max),
-// n the tile's candidate bumps and A_max the bucket's bound on |A| (its
+// 32-bit integers with a per-pass scale 2^30 / (1.001 m A_max), m the
+// candidate bumps of the pass and A_max the bucket's bound on |A| (its
 // direction amplitudes, and the wake's).  Every S_ij then fits in 31 bits, the
 // events accumulate exactly in any order (integer shared-memory atomics:
 // deterministic results), and the prefix sums are exact modulo 2^32 (their
 // intermediate values may wrap; the final ones do not).  The contraction is
-// FP32.  The rounding error of a weight is at most 2^-31 n A_max, far below
-// the FP32 map tolerance.
+// FP32.  The rounding error of a weight is at most 2^-31 m A_max; those of the
+// n candidates covering a texel add up to about sqrt(n) m A_max 2^-31, so a
+// (tile, bucket) whose n is large against the bound the host sets per bucket
+// (BucketDev::sat_c) is split into passes of fewer candidates, each with its
+// own scale, prefix sums and contraction (the FP32 accumulators carry over).
 //
 // One CTA per (tile, bucket group) item, 512 threads, two CTAs per SM.  The
 // nine S components are processed in three groups of three (fixed p_i), so
@@ -199,6 +202,7 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
             }
             const BucketDev bk = S.bk[bi];
             const int q0 = S.rb[t], q1 = S.rb[t + 1];
+            if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)ncand);
             for (int k = tid; k < 2 * kT; k += kSatThreads)
                 S.ph[k] = p.phase[(size_t)(b_begin + bi) * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
             // stage the first kSatStage candidates: warp w takes rows w, w + 16, ...
@@ -223,9 +227,16 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                     S.c2[f_row + k] = make_float2(ry.z, __uint_as_float(box));
                 }
             }
-            const float bound = 1.001f * (float)ncand * amax;   // >= every |S_ij|
-            const float scale = 1073741824.f / bound;         // 2^30 / bound
-            const float inv = bound * (1.f / 1073741824.f);   // 1 / scale
+            // passes of at most mch candidates, so that the integer rounding
+            // of the corner weights stays within the bound set on the host
+            const float nf = (float)ncand;
+            const int kch = max(1, (int)ceilf(nf * sqrtf(nf) / bk.sat_c));
+            const int mch = (ncand + kch - 1) / kch;
+            for (int c0 = 0; c0 < ncand; c0 += mch) {
+            const int c1 = min(ncand, c0 + mch);
+            const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
+            const float scale = 1073741824.f / bound;              // 2^30 / bound
+            const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
 
             for (int i = 0; i < 3; ++i) {   // component group p_i: S_i0, S_i1, S_i2
                 for (int k = tid; k < 3 * kT * kT / 4; k += kSatThreads)
@@ -236,11 +247,11 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                 // every bump that covers the tile's first texel: its weights
                 // are summed per thread here and per warp after the loop.
                 uint32_t z0 = 0u, z1 = 0u, z2 = 0u;
-                for (int f0 = warp * 32; f0 < ncand; f0 += kSatThreads) {
+                for (int f0 = c0 + warp * 32; f0 < c1; f0 += kSatThreads) {
                     const int f = f0 + lane;
                     float A = 0.f, pc = 0.f, ps = 0.f, qc = 0.f, qs = 0.f;
                     uint32_t box = 0u;   // empty box: no events
-                    if (f < ncand) {
+                    if (f < c1) {
                         if (f < kSatStage) {
                             const float4 c = S.c4[f];
                             const float2 e = S.c2[f];
@@ -367,6 +378,7 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                 }
                 __syncthreads();   // E and seg are rewritten by the next group
             }
+            }   // passes
         }
         bb = be;
     }

@@ -65,7 +65,7 @@ class scwp_stats(C.Structure):
                 ("injected_total", C.c_int64), ("n_buckets", C.c_int32),
                 ("error_flags", C.c_int32), ("live_per_bucket", C.c_int64 * MAX_BUCKETS),
                 ("injected_energy", C.c_double * MAX_BUCKETS), ("mma_stages", C.c_int64),
-                ("eval_total", C.c_int64)]
+                ("eval_total", C.c_int64), ("sat_candidates", C.c_int64)]
 
 
 class scwp_patch_info(C.Structure):

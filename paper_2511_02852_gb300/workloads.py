@@ -262,6 +262,14 @@ def scaled(sc, **patch_overrides):
     return out
 
 
+def mixed_large_1():
+    """The first patch of mixed_large alone (its 2048^2 background, one
+    1024^2 patch of 2M particles): the size for one-launch kernel profiles."""
+    sc = mixed_large(n_patches=1)
+    sc["name"] = "mixed_large_1"
+    return sc
+
+
 ALL = {"tiny": tiny, "realistic": realistic, "small_jonswap": small_jonswap,
        "small_two_patches": small_two_patches, "small_batch": small_batch, "batched": batched,
-       "mixed_large": mixed_large}
+       "mixed_large": mixed_large, "mixed_large_1": mixed_large_1}
