@@ -800,13 +800,17 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     // sqrt(n) m A_max 2^-31 per S_ij, of which 3/4 reach h (worst texel of a
     // tile: ~2 sigma).  A (tile, bucket) of n candidates therefore goes in
     // k = ceil(n^1.5 / c) passes of n / k candidates, c = eps Hs 2^31 /
-    // (0.6 A_max), which keeps that error under eps = 1e-5 Hs per bucket
-    // (one pass for every tile of the realistic and mixed_large scenes; up to
-    // tens on patches holding tens of particles per texel).
+    // (0.6 A_max), which keeps that error under eps = 2e-5 Hs / sqrt(nb) per
+    // bucket, so that the nb buckets of a texel stay within about 2e-5 Hs
+    // together (measured worst texel of the 32-patch batched workload before
+    // this bound: 1.7e-4 Hs).  That is one pass for nearly every tile of the
+    // realistic and mixed_large scenes and up to a few tens on patches holding
+    // tens of particles per texel.
     {
         const double hs = 4.0 * std::sqrt(ctx->sm.m0());
+        const double eps = 2e-5 * hs / std::sqrt((double)T.nb);
         for (int i = 0; i < T.nb; ++i)
-            P->bk[i].sat_c = amax[i] > 0 ? (float)(1e-5 * hs * 2147483648.0 / (0.6 * (double)amax[i])) : 3.0e38f;
+            P->bk[i].sat_c = amax[i] > 0 ? (float)(eps * 2147483648.0 / (0.6 * (double)amax[i])) : 3.0e38f;
     }
     const size_t cap = (size_t)D.cap;
     D.nblk_c = (int)((cap + 1023) / 1024);
