@@ -48,9 +48,7 @@ typedef enum {
     SCWP_E_CAPACITY = 3,  /* particle pool full: injection was truncated   */
     SCWP_E_CUDA = 4,      /* CUDA error (sticky)                           */
     SCWP_E_TIMEOUT = 5,   /* a bounded device wait gave up (sticky)        */
-    SCWP_E_STATE = 6,     /* call not valid in the current state           */
-    SCWP_E_INCOMPLETE = 7 /* a synthesis limit was reached: a bucket's share
-                             is missing from some tile of the last maps     */
+    SCWP_E_STATE = 6      /* call not valid in the current state           */
 } scwp_status;
 
 enum { SCWP_SPECTRUM_JONSWAP = 0, SCWP_SPECTRUM_PHILLIPS = 1 };
@@ -158,9 +156,7 @@ typedef struct scwp_stats {
     int64_t injected_total;    /* particles injected since creation        */
     int32_t n_buckets;
     int32_t error_flags;       /* bit 0: particle pool full (injection truncated);
-                                  bit 1: a bounded device wait timed out;
-                                  bit 2: a synthesis limit was reached (a bucket
-                                  of some tile was left out of the maps)   */
+                                  bit 1: a bounded device wait timed out   */
     int64_t live_per_bucket[SCWP_MAX_BUCKETS];
     double injected_energy[SCWP_MAX_BUCKETS]; /* sum 1/8 A^2 pi r^2 (Eq. 12 / rho g) */
     int64_t mma_stages;        /* operand stages (6 MMAs of 128x128x16 each) the last
@@ -257,8 +253,8 @@ scwp_status scwp_normal_map(scwp_ctx* ctx, int32_t patch_id, float* dst, size_t 
 
 /* Statistics of a patch after the last frame (synchronises the stream).
  * The statistics are filled in every case; the status reports the frame's
- * error flags: SCWP_E_TIMEOUT (sticky) for bit 1, SCWP_E_INCOMPLETE for
- * bit 2, SCWP_E_CAPACITY for bit 0, SCWP_OK when none is set. */
+ * error flags: SCWP_E_TIMEOUT (sticky) for bit 1, SCWP_E_CAPACITY for bit 0,
+ * SCWP_OK when none is set. */
 scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out);
 
 /* Table and bin geometry of a patch. */

@@ -147,6 +147,7 @@ struct scwp_ctx {
     cudaStream_t gst = nullptr;       // capture origin (the caller's stream may be the legacy one)
     std::vector<InjectParams> ips;    // this frame's injection plans
     size_t alloc_bytes = 0;           // device memory held by the context
+    unsigned int* queue = nullptr;    // work queue of the persistent summed-area synthesis (2 words)
     float* normal_scratch = nullptr;  // normals for host destinations
     size_t normal_bytes = 0;
     std::vector<double> b_work;       // estimated stages of each batched item
@@ -647,11 +648,11 @@ scwp_status synthesize(scwp_ctx* ctx, int mode) {
         if (s != SCWP_OK) return s;
         if (ctx->batched) {
             CU(launch_synth_sat(ctx->d_sitems, (int)ctx->s_items.size(), ctx->d_pdevs, ctx->d_sps, ctx->d_sspans,
-                                (int)ctx->s_spans.size(), ctx->st));
+                                (int)ctx->s_spans.size(), ctx->queue, ctx->st));
         } else {
             for (PatchHost* P : ctx->patches)
                 CU(launch_synth_sat(P->d_sat_items, (int)P->sat_items.size(), ctx->d_pdevs, ctx->d_sps,
-                                    P->d_sat_spans, (int)P->sat_spans.size(), ctx->st));
+                                    P->d_sat_spans, (int)P->sat_spans.size(), ctx->queue, ctx->st));
         }
         return SCWP_OK;
     }
@@ -742,11 +743,13 @@ scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
     ctx->tw = (float2*)dalloc(ctx, N * sizeof(float2));
     ctx->G = (float2*)dalloc(ctx, 2 * NN * sizeof(float2));
     ctx->bgout = (float*)dalloc(ctx, 3 * NN * sizeof(float));
-    if (!ctx->h0 || !ctx->omega || !ctx->tw || !ctx->G || !ctx->bgout) return bail(SCWP_E_NOMEM);
+    ctx->queue = (unsigned int*)dalloc(ctx, 2 * sizeof(unsigned int));
+    if (!ctx->h0 || !ctx->omega || !ctx->tw || !ctx->G || !ctx->bgout || !ctx->queue) return bail(SCWP_E_NOMEM);
     if (cudaMemcpy(ctx->h0, h0.data(), NN * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->omega, om.data(), NN * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(ctx->bgout, 0, 3 * NN * sizeof(float)) != cudaSuccess) {
+        cudaMemset(ctx->bgout, 0, 3 * NN * sizeof(float)) != cudaSuccess ||
+        cudaMemset(ctx->queue, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         return bail(SCWP_E_CUDA);
     }
@@ -1518,8 +1521,6 @@ scwp_status scwp_stats_get(scwp_ctx* ctx, int32_t patch_id, scwp_stats* out) {
         out->injected_energy[i] = P->energy[i];
     }
     if (st[2] & kErrTimeout) return fail(ctx, SCWP_E_TIMEOUT, "a device wait timed out");
-    if (st[2] & kErrSynthLimit)
-        return fail(ctx, SCWP_E_INCOMPLETE, "a bucket's bin rows exceeded the synthesis row table; its share of some tile is missing");
     if (st[2] & kErrCapacity) return fail(ctx, SCWP_E_CAPACITY, "particle pool full: injection was truncated");
     return SCWP_OK;
 }
@@ -1786,6 +1787,7 @@ struct scwp_server {
     std::vector<void*> hstage, dstage;
     std::vector<size_t> stage_cap;
     std::vector<bool> slot_busy;
+    unsigned int* queue = nullptr;    // work queue of the summed-area synthesis launches (2 words)
     size_t used = 0;
     int rr = 0;
     int64_t ticks_launched = 0, requests_done = 0;
@@ -1851,6 +1853,10 @@ scwp_status scwp_server_create(const scwp_server_desc* desc, scwp_server** out) 
              cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
         if (s) sv->pst.push_back(s);
         if (e) sv->pev.push_back(e);
+    }
+    if (ok) {
+        sv->queue = (unsigned int*)sv_alloc(sv, 2 * sizeof(unsigned int));
+        ok = sv->queue && cudaMemset(sv->queue, 0, 2 * sizeof(unsigned int)) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
@@ -2034,7 +2040,8 @@ scwp_status scwp_server_tick(scwp_server* sv, int32_t* started) {
                             reinterpret_cast<const BlendSpan*>(dv + o_bs[0]), (int)spans[0].size(), sv->st));
     if (!items[1].empty())
         SCU(launch_synth_sat(reinterpret_cast<const TcItem*>(dv + o_it[1]), (int)items[1].size(), dpd, dsp,
-                             reinterpret_cast<const BlendSpan*>(dv + o_bs[1]), (int)spans[1].size(), sv->st));
+                             reinterpret_cast<const BlendSpan*>(dv + o_bs[1]), (int)spans[1].size(), sv->queue,
+                             sv->st));
     SCU(cudaEventRecord(tk.done, sv->st));
     sv->slot_busy[slot] = true;
     *started = (int32_t)tk.reqs.size();
@@ -2103,6 +2110,7 @@ void scwp_server_destroy(scwp_server* sv) {
     }
     for (cudaEvent_t e : sv->tick_events)
         if (e) cudaEventDestroy(e);
+    sv_free(sv, sv->queue);
     for (cudaStream_t s : sv->pst) cudaStreamDestroy(s);
     for (cudaEvent_t e : sv->pev) cudaEventDestroy(e);
     cudaGetLastError();

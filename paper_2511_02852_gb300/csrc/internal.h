@@ -15,7 +15,6 @@ constexpr int kMaxWakeRate = 64;    // wake particles per Kelvin arm per frame a
 constexpr int kMaxGiven = kMaxRing + 2 * kMaxWakeRate;   // host-placed particles per frame
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
-constexpr uint32_t kErrSynthLimit = 4u;   // a synthesis table limit left a bucket of a tile out
 
 // Per-bucket constants read by the binning and synthesis kernels.
 struct BucketDev {
@@ -188,10 +187,12 @@ cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaSt
 cudaError_t launch_synth_tc(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
                             const BlendSpan* spans, int n_spans, cudaStream_t st, bool split = true);
 // Summed-area synthesis (the same sums through 2-D difference arrays of the
-// kernel's rank-3 factors) of `n_items` items in one launch, then the
-// group-sum blend, like launch_synth_tc.
+// kernel's rank-3 factors) of `n_items` items in one persistent launch, then
+// the group-sum blend, like launch_synth_tc.  `queue` is the launch's work
+// queue, two zeroed device words that the kernel leaves zeroed again; the
+// launches that share one must be ordered on a stream.
 cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
-                             const BlendSpan* spans, int n_spans, cudaStream_t st);
+                             const BlendSpan* spans, int n_spans, unsigned int* queue, cudaStream_t st);
 int synth_sat_tile();
 int synth_sat_ctas_per_sm();
 // tensor-core synthesis geometry: tile side (texels), bumps per operand stage,

@@ -34,9 +34,20 @@
 // (BucketDev::sat_c) is split into passes of fewer candidates, each with its
 // own scale, prefix sums and contraction (the FP32 accumulators carry over).
 //
-// One CTA per (tile, bucket group) item, 512 threads, two CTAs per SM.  The
-// nine S components are processed in three groups of three (fixed p_i), so
-// the difference array takes 48 KB of shared memory.
+// Organisation: a persistent grid, one 1024-thread CTA per SM, pulls (tile,
+// bucket group) items from a work queue (an atomic ticket over the plan's
+// heaviest-first order; the last CTA to finish resets the queue for the next
+// launch, so no CTA ever waits on another).  All nine S_ij planes of a
+// bucket live in shared memory at once (144 KB), so each candidate bump is
+// staged and turned into corner events exactly once per pass: the bin rows
+// that reach the tile are read into a row table, the candidates are staged in
+// chunks of 2048 (each thread finds its candidate's row by a binary search of
+// the row table and reads the 32-byte record from L2), and each staged
+// candidate adds its nine weights at up to four corners.  Bumps whose box
+// starts at the tile's first texel in both axes (every bump covering the
+// whole tile among them) sum their (0, 0) corner in registers, which one
+// warp reduction adds.  A bucket whose bin rows exceed the row table is taken
+// in row chunks, each a pass of its own.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -48,31 +59,35 @@ namespace scwp {
 namespace {
 
 constexpr int kT = 64;                       // tile side in texels
-constexpr int kSatThreads = 512;
-constexpr int kSatWarps = kSatThreads / 32;
+constexpr int kSatThreads = 1024;
 constexpr int kSegs = kSatThreads / kT;      // row segments of the column pass
 constexpr int kSegRows = kT / kSegs;         // rows per segment
-constexpr int kSatRowCap = 512;              // bin rows of the item's buckets held at once
-constexpr int kSatStage = 1984;              // candidates of a bucket staged in shared memory
+constexpr int kPlanes = 9;                   // S_ij, plane 3 i + j
+constexpr int kRowCap = 512;                 // bin rows of a bucket held at once
+constexpr int kStage = 2048;                 // candidates staged at once
 constexpr int32_t kQs = 65536, kHalfs = 32768;
-static_assert(kSegs * kSegRows == kT && kSegs == 8, "column-pass mapping");
+static_assert(kSegs * kSegRows == kT && kSegs == 16, "column-pass mapping");
+static_assert(kPlanes * kT <= kSatThreads, "one row scan per thread");
+
+struct Staged {
+    float4 c4[kStage];                    // A, cos, sin (x), cos (y)
+    float2 c2[kStage];                    // sin (y), support box (bits)
+};
 
 struct SatSmem {
-    uint32_t E[3][kT * kT];               // difference array, then prefix sums (one component group)
-    uint32_t seg[kSegs][3][kT];           // column sums of each row segment
+    uint32_t E[kPlanes][kT * kT];         // difference arrays, then prefix sums
+    union {
+        Staged st;                        // the staged candidates (events phase)
+        uint32_t seg[kSegs][kPlanes][kT]; // column sums of each row segment (column pass)
+    } u;
     float2 ph[2 * kT];                    // the bucket's texel phases (cos, sin) a: rows, then columns
-    float4 c4[kSatStage];                 // staged candidates: A, cos, sin (x), cos (y)
-    float2 c2[kSatStage];                 //                    sin (y), support box (bits)
-    int32_t rs[kSatRowCap];               // first record of each bin row (all buckets of a batch)
-    int32_t cum[kSatRowCap];              // candidates of the bucket before the row
-    BucketDev bk[kMaxBuckets];            // the item's buckets
-    int32_t bx_lo[kMaxBuckets], bx_hi[kMaxBuckets], by_lo[kMaxBuckets], nrows[kMaxBuckets];
-    int32_t rb[kMaxBuckets + 1];          // first row of each bucket of the batch
-    int32_t ncand[kMaxBuckets];           // candidates of each bucket
-    int32_t batch_end;                    // one past the last bucket of the batch
+    int32_t rs[kRowCap];                  // first record of each bin row
+    int32_t cum[kRowCap];                 // candidates of the bucket before the row
+    int32_t item, ncand, pad0, pad1;
     alignas(16) unsigned char pd[sizeof(PatchDev)];
     alignas(16) unsigned char spd[sizeof(SynthParams)];
 };
+static_assert(sizeof(SatSmem) <= 227 * 1024, "shared memory of one CTA");
 
 // element (row y, column x) of a 64 x 64 plane: columns XOR-swizzled by the
 // row so that a warp walking a row (one row per lane) or a column (one
@@ -81,12 +96,11 @@ __device__ __forceinline__ int sw(int y, int x) { return y * kT + (x ^ (y & 31))
 
 __device__ __forceinline__ int clamp_t(int t) { return min(max(t, 0), kT); }
 
-// the three components of one corner event
-__device__ __forceinline__ void event3(SatSmem& S, int x, int y, uint32_t w0, uint32_t w1, uint32_t w2) {
+// the nine components of one corner event
+__device__ __forceinline__ void event9(SatSmem& S, int x, int y, const uint32_t (&w)[kPlanes], bool neg) {
     const int o = sw(y, x);
-    atomicAdd(&S.E[0][o], w0);
-    atomicAdd(&S.E[1][o], w1);
-    atomicAdd(&S.E[2][o], w2);
+#pragma unroll
+    for (int k = 0; k < kPlanes; ++k) atomicAdd(&S.E[k][o], neg ? 0u - w[k] : w[k]);
 }
 
 // inclusive warp scan of v
@@ -99,167 +113,111 @@ __device__ __forceinline__ uint32_t warp_scan(uint32_t v, int lane) {
     return v;
 }
 
-__global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* items, const PatchDev* pdevs,
-                                                            const SynthParams* sps) {
+__global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* items, int n_items,
+                                                            const PatchDev* pdevs, const SynthParams* sps,
+                                                            unsigned int* queue) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SatSmem& S = *reinterpret_cast<SatSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    pdl_enter();
-    const TcItem it = items[blockIdx.x];
-    {
-        static_assert(sizeof(PatchDev) % 4 == 0 && sizeof(SynthParams) % 4 == 0, "descriptor copy");
-        const uint32_t* a = reinterpret_cast<const uint32_t*>(pdevs + it.patch);
-        const uint32_t* b = reinterpret_cast<const uint32_t*>(sps + it.patch);
-        for (int k = tid; k < (int)(sizeof(PatchDev) / 4); k += kSatThreads) reinterpret_cast<uint32_t*>(S.pd)[k] = a[k];
-        for (int k = tid; k < (int)(sizeof(SynthParams) / 4); k += kSatThreads)
-            reinterpret_cast<uint32_t*>(S.spd)[k] = b[k];
-    }
-    __syncthreads();
-    const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
-    const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
-    const int G = it.groups, g = it.group;
-    const int ntx = (sp.W + kT - 1) / kT;
-    const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
-    const int b_begin = max((g * sp.nb) / G, sp.b_lo);
-    const int b_end = min(((g + 1) * sp.nb) / G, sp.b_hi);
-    const int nbk = max(0, b_end - b_begin);
-    // Q16.16 centres of the tile's first and last texel columns and rows
-    const int32_t X0 = tx0 * kQs + kHalfs, X1 = X0 + (kT - 1) * kQs;
-    const int32_t Y0 = ty0 * kQs + kHalfs, Y1 = Y0 + (kT - 1) * kQs;
-    const float lamq = 0.5f * sp.lam_half;   // lam / 4
-
-    // ---- the item's buckets and the bin rows that reach the tile
-    // (bins hold x_b + R in [bx C, (bx + 1) C))
-    for (int t = tid; t < nbk; t += kSatThreads) {
-        const BucketDev bk = p.bk[b_begin + t];
-        S.bk[t] = bk;
-        const int bx_lo = (int)((int64_t)X0 / bk.C);
-        const int bx_hi = min((int)(((int64_t)X1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nbx - 1);
-        const int by_lo = (int)((int64_t)Y0 / bk.C);
-        const int by_hi = min((int)(((int64_t)Y1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nby - 1);
-        S.bx_lo[t] = bx_lo;
-        S.bx_hi[t] = bx_hi;
-        S.by_lo[t] = by_lo;
-        S.nrows[t] = (bx_lo > bx_hi || by_lo > by_hi) ? 0 : by_hi - by_lo + 1;
-    }
-
-    // column pass: this thread owns texel column cx of rows sg*8 .. sg*8 + 7
+    // column pass: this thread owns texel column cx of rows sg*4 .. sg*4 + 3
     const int cx = tid & (kT - 1), sg = tid / kT;
-    float ah[kSegRows], adx[kSegRows], ady[kSegRows];
+    pdl_enter();
+    for (;;) {
+        if (tid == 0) S.item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int ti = S.item;
+        if (ti >= n_items) break;
+        const TcItem it = items[ti];
+        {
+            static_assert(sizeof(PatchDev) % 4 == 0 && sizeof(SynthParams) % 4 == 0, "descriptor copy");
+            const uint32_t* a = reinterpret_cast<const uint32_t*>(pdevs + it.patch);
+            const uint32_t* b = reinterpret_cast<const uint32_t*>(sps + it.patch);
+            for (int k = tid; k < (int)(sizeof(PatchDev) / 4); k += kSatThreads)
+                reinterpret_cast<uint32_t*>(S.pd)[k] = a[k];
+            for (int k = tid; k < (int)(sizeof(SynthParams) / 4); k += kSatThreads)
+                reinterpret_cast<uint32_t*>(S.spd)[k] = b[k];
+        }
+        __syncthreads();
+        const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
+        const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
+        const int G = it.groups, g = it.group;
+        const int ntx = (sp.W + kT - 1) / kT;
+        const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
+        const int b_begin = max((g * sp.nb) / G, sp.b_lo);
+        const int b_end = min(((g + 1) * sp.nb) / G, sp.b_hi);
+        // Q16.16 centres of the tile's first and last texel columns and rows
+        const int32_t X0 = tx0 * kQs + kHalfs, X1 = X0 + (kT - 1) * kQs;
+        const int32_t Y0 = ty0 * kQs + kHalfs, Y1 = Y0 + (kT - 1) * kQs;
+        const float lamq = 0.5f * sp.lam_half;   // lam / 4
+        float ah[kSegRows], adx[kSegRows], ady[kSegRows];
 #pragma unroll
-    for (int r = 0; r < kSegRows; ++r) ah[r] = adx[r] = ady[r] = 0.f;
+        for (int r = 0; r < kSegRows; ++r) ah[r] = adx[r] = ady[r] = 0.f;
 
-    // buckets in batches whose bin rows fit the row tables
-    for (int bb = 0; bb < nbk;) {
-        __syncthreads();   // bucket geometry written; the previous batch is done with the tables
-        if (tid == 0) {
-            int n = 0, be = bb;
-            while (be < nbk && (be == bb || n + S.nrows[be] <= kSatRowCap)) {
-                S.rb[be - bb] = n;
-                n += min(S.nrows[be], kSatRowCap);
-                ++be;
-            }
-            S.rb[be - bb] = n;
-            S.batch_end = be;
-        }
-        __syncthreads();
-        const int be = S.batch_end;
-        const int nq = S.rb[be - bb];
-        // every row of the batch: record range from the bin offsets
-        for (int q = tid; q < nq; q += kSatThreads) {
-            int t = 0;
-            while (S.rb[t + 1] <= q) ++t;
-            const int bi = bb + t, r = q - S.rb[t];
-            const BucketDev& bk = S.bk[bi];
-            const int key0 = bk.base + (S.by_lo[bi] + r) * bk.nbx;
-            const int s0 = (int)p.offsets[key0 + S.bx_lo[bi]];
-            S.rs[q] = s0;
-            S.cum[q] = (int)p.offsets[key0 + S.bx_hi[bi] + 1] - s0;   // row length for now
-        }
-        __syncthreads();
-        // per bucket: exclusive prefix of the row lengths (warp w takes buckets w, w + 16, ...)
-        for (int t = warp; t < be - bb; t += kSatWarps) {
-            const int q0 = S.rb[t], q1 = S.rb[t + 1];
-            uint32_t carry = 0u;
-            for (int q = q0; q < q1; q += 32) {
-                const uint32_t l = q + lane < q1 ? (uint32_t)S.cum[q + lane] : 0u;
-                const uint32_t inc = warp_scan(l, lane);
-                if (q + lane < q1) S.cum[q + lane] = (int32_t)(carry + inc - l);
-                carry += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            if (lane == 0) S.ncand[bb + t] = (int32_t)carry;
-        }
-        __syncthreads();
-
-        for (int bi = bb; bi < be; ++bi) {
-            const int t = bi - bb;
-            const int ncand = S.ncand[bi];
-            const float amax = p.amax[b_begin + bi];
-            if (ncand == 0 || !(amax > 0.f)) continue;   // no bump of this bucket reaches the tile
-            if (S.nrows[bi] > kSatRowCap) {              // rows beyond the tables: not synthesised
-                if (tid == 0) atomicOr(p.stats + 2, (unsigned long long)kErrSynthLimit);
-                continue;
-            }
-            const BucketDev bk = S.bk[bi];
-            const int q0 = S.rb[t], q1 = S.rb[t + 1];
-            if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)ncand);
+        for (int b = b_begin; b < b_end; ++b) {
+            const BucketDev bk = p.bk[b];
+            const float amax = p.amax[b];
+            // bins hold x_b + R in [bx C, (bx + 1) C): the bin rows and columns
+            // that reach the tile
+            const int bx_lo = (int)((int64_t)X0 / bk.C);
+            const int bx_hi = min((int)(((int64_t)X1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nbx - 1);
+            const int by_lo = (int)((int64_t)Y0 / bk.C);
+            const int by_hi = min((int)(((int64_t)Y1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nby - 1);
+            const int nrows = (bx_lo > bx_hi || by_lo > by_hi) ? 0 : by_hi - by_lo + 1;
+            if (nrows == 0 || !(amax > 0.f)) continue;   // (uniform over the CTA)
+            // the bucket's texel phases (every read of the previous bucket's
+            // ended before its last barrier)
             for (int k = tid; k < 2 * kT; k += kSatThreads)
-                S.ph[k] = p.phase[(size_t)(b_begin + bi) * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
-            // stage the first kSatStage candidates: warp w takes rows w, w + 16, ...
-            for (int q = q0 + warp; q < q1; q += kSatWarps) {
-                const int f_row = S.cum[q];
-                const int l = (q + 1 < q1 ? S.cum[q + 1] : ncand) - f_row;
-                const int r0 = S.rs[q];
-                for (int k = lane; k < l && f_row + k < kSatStage; k += 32) {
-                    const float4* rp = reinterpret_cast<const float4*>(p.rec + r0 + k);
-                    const float4 rx = rp[0];   // x, cos, sin, id
-                    const float4 ry = rp[1];   // y, cos, sin, A
-                    const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
-                    // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
-                    const int a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
-                    const int b = clamp_t(-((X0 - xb - bk.R) >> 16));
-                    const int c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
-                    const int d = clamp_t(-((Y0 - yb - bk.R) >> 16));
-                    const uint32_t box = (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) |
-                                                                ((uint32_t)d << 21)
-                                                          : 0u;
-                    S.c4[f_row + k] = make_float4(ry.w, rx.y, rx.z, ry.y);
-                    S.c2[f_row + k] = make_float2(ry.z, __uint_as_float(box));
+                S.ph[k] = p.phase[(size_t)b * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
+            for (int r0 = 0; r0 < nrows; r0 += kRowCap) {
+                const int nr = min(kRowCap, nrows - r0);
+                for (int q = tid; q < nr; q += kSatThreads) {
+                    const int key0 = bk.base + (by_lo + r0 + q) * bk.nbx;
+                    const int s0 = (int)p.offsets[key0 + bx_lo];
+                    S.rs[q] = s0;
+                    S.cum[q] = (int)p.offsets[key0 + bx_hi + 1] - s0;   // row length for now
                 }
-            }
-            // passes of at most mch candidates, so that the integer rounding
-            // of the corner weights stays within the bound set on the host
-            const float nf = (float)ncand;
-            const int kch = max(1, (int)ceilf(nf * sqrtf(nf) / bk.sat_c));
-            const int mch = (ncand + kch - 1) / kch;
-            for (int c0 = 0; c0 < ncand; c0 += mch) {
-            const int c1 = min(ncand, c0 + mch);
-            const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
-            const float scale = 1073741824.f / bound;              // 2^30 / bound
-            const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
-
-            for (int i = 0; i < 3; ++i) {   // component group p_i: S_i0, S_i1, S_i2
-                for (int k = tid; k < 3 * kT * kT / 4; k += kSatThreads)
-                    reinterpret_cast<uint4*>(&S.E[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
                 __syncthreads();
-                // ---- corner events; candidate f of the bucket, all lanes of a
-                // warp in the same trips.  The corner (0, 0) is shared by
-                // every bump that covers the tile's first texel: its weights
-                // are summed per thread here and per warp after the loop.
-                uint32_t z0 = 0u, z1 = 0u, z2 = 0u;
-                for (int f0 = c0 + warp * 32; f0 < c1; f0 += kSatThreads) {
-                    const int f = f0 + lane;
-                    float A = 0.f, pc = 0.f, ps = 0.f, qc = 0.f, qs = 0.f;
-                    uint32_t box = 0u;   // empty box: no events
-                    if (f < c1) {
-                        if (f < kSatStage) {
-                            const float4 c = S.c4[f];
-                            const float2 e = S.c2[f];
-                            A = c.x; pc = c.y; ps = c.z; qc = c.w; qs = e.x;
-                            box = __float_as_uint(e.y);
-                        } else {
-                            // the row holding candidate f, and its record
-                            int lo = q0, hi = q1 - 1;
+                if (warp == 0) {   // exclusive prefix of the row lengths
+                    uint32_t carry = 0u;
+                    for (int q = 0; q < nr; q += 32) {
+                        const uint32_t l = q + lane < nr ? (uint32_t)S.cum[q + lane] : 0u;
+                        const uint32_t inc = warp_scan(l, lane);
+                        if (q + lane < nr) S.cum[q + lane] = (int32_t)(carry + inc - l);
+                        carry += __shfl_sync(0xffffffffu, inc, 31);
+                    }
+                    if (lane == 0) S.ncand = (int32_t)carry;
+                }
+                __syncthreads();
+                const int ncand = S.ncand;
+                if (ncand == 0) continue;
+                if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)ncand);
+                // passes of at most mch candidates, so that the integer rounding
+                // of the corner weights stays within the bound set on the host
+                const float nf = (float)ncand;
+                const int kch = max(1, (int)ceilf(nf * sqrtf(nf) / bk.sat_c));
+                const int mch = (ncand + kch - 1) / kch;
+                for (int c0 = 0; c0 < ncand; c0 += mch) {
+                    const int c1 = min(ncand, c0 + mch);
+                    const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
+                    const float scale = 1073741824.f / bound;              // 2^30 / bound
+                    const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
+                    {
+                        uint4* e4 = reinterpret_cast<uint4*>(&S.E[0][0]);
+                        for (int k = tid; k < kPlanes * kT * kT / 4; k += kSatThreads)
+                            e4[k] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                    // the (0, 0) corner, shared by every bump whose box starts at
+                    // the tile's first texel in both axes: per-thread sums
+                    uint32_t z[kPlanes];
+#pragma unroll
+                    for (int k = 0; k < kPlanes; ++k) z[k] = 0u;
+                    for (int s0 = c0; s0 < c1; s0 += kStage) {
+                        const int ns = min(kStage, c1 - s0);
+                        __syncthreads();   // E cleared; the previous chunk's events done
+                        // ---- stage candidates s0 .. s0 + ns - 1 of the row chunk
+                        for (int k = tid; k < ns; k += kSatThreads) {
+                            const int f = s0 + k;
+                            int lo = 0, hi = nr - 1;   // the last row with cum <= f holds f
                             while (lo < hi) {
                                 const int mid = (lo + hi + 1) >> 1;
                                 if (S.cum[mid] <= f) lo = mid; else hi = mid - 1;
@@ -270,131 +228,160 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat(const TcItem* item
                             const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
                             // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
                             const int a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
-                            const int b = clamp_t(-((X0 - xb - bk.R) >> 16));
+                            const int bb = clamp_t(-((X0 - xb - bk.R) >> 16));
                             const int c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
                             const int d = clamp_t(-((Y0 - yb - bk.R) >> 16));
-                            box = (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) |
-                                                         ((uint32_t)d << 21)
-                                                   : 0u;
-                            A = ry.w; pc = rx.y; ps = rx.z; qc = ry.y; qs = ry.z;
+                            const uint32_t box = (a < bb && c < d)
+                                                     ? (uint32_t)a | ((uint32_t)bb << 7) | ((uint32_t)c << 14) |
+                                                           ((uint32_t)d << 21)
+                                                     : 0u;
+                            S.u.st.c4[k] = make_float4(ry.w, rx.y, rx.z, ry.y);
+                            S.u.st.c2[k] = make_float2(ry.z, __uint_as_float(box));
+                        }
+                        __syncthreads();
+                        // ---- corner events of the staged candidates
+                        for (int k = tid; k < ns; k += kSatThreads) {
+                            const float2 e = S.u.st.c2[k];
+                            const uint32_t box = __float_as_uint(e.y);
+                            if (box == 0u) continue;   // no texel of the tile in the support
+                            const float4 cc = S.u.st.c4[k];
+                            const int a = box & 127, bb = (box >> 7) & 127, c = (box >> 14) & 127,
+                                      d = (box >> 21) & 127;
+                            const float A = cc.x, qc = cc.w, qs = e.x;
+                            const float m0 = A * scale, m1 = A * cc.y * scale, m2 = A * cc.z * scale;
+                            uint32_t w[kPlanes];
+                            w[0] = (uint32_t)__float2int_rn(m0);
+                            w[1] = (uint32_t)__float2int_rn(m0 * qc);
+                            w[2] = (uint32_t)__float2int_rn(m0 * qs);
+                            w[3] = (uint32_t)__float2int_rn(m1);
+                            w[4] = (uint32_t)__float2int_rn(m1 * qc);
+                            w[5] = (uint32_t)__float2int_rn(m1 * qs);
+                            w[6] = (uint32_t)__float2int_rn(m2);
+                            w[7] = (uint32_t)__float2int_rn(m2 * qc);
+                            w[8] = (uint32_t)__float2int_rn(m2 * qs);
+                            if (a == 0 && c == 0) {
+#pragma unroll
+                                for (int q = 0; q < kPlanes; ++q) z[q] += w[q];
+                            } else {
+                                event9(S, a, c, w, false);
+                            }
+                            if (bb < kT) event9(S, bb, c, w, true);
+                            if (d < kT) event9(S, a, d, w, true);
+                            if (bb < kT && d < kT) event9(S, bb, d, w, false);
                         }
                     }
-                    const int a = box & 127, b = (box >> 7) & 127, c = (box >> 14) & 127, d = (box >> 21) & 127;
-                    const bool ov = a < b;   // (an empty box has a = b = 0)
-                    uint32_t w0 = 0u, w1 = 0u, w2 = 0u;
-                    if (ov) {
-                        const float pi = i == 0 ? 1.f : (i == 1 ? pc : ps);
-                        const float m = A * pi * scale;
-                        w0 = (uint32_t)__float2int_rn(m);
-                        w1 = (uint32_t)__float2int_rn(m * qc);
-                        w2 = (uint32_t)__float2int_rn(m * qs);
-                    }
-                    const bool z = ov && a == 0 && c == 0;
-                    if (z) {
-                        z0 += w0;
-                        z1 += w1;
-                        z2 += w2;
-                    }
-                    if (ov) {
-                        if (!z) event3(S, a, c, w0, w1, w2);
-                        if (b < kT) event3(S, b, c, 0u - w0, 0u - w1, 0u - w2);
-                        if (d < kT) event3(S, a, d, 0u - w0, 0u - w1, 0u - w2);
-                        if (b < kT && d < kT) event3(S, b, d, w0, w1, w2);
-                    }
-                }
-                {
-                    const uint32_t v0 = __reduce_add_sync(0xffffffffu, z0);
-                    const uint32_t v1 = __reduce_add_sync(0xffffffffu, z1);
-                    const uint32_t v2 = __reduce_add_sync(0xffffffffu, z2);
-                    if (lane == 0 && (v0 | v1 | v2)) event3(S, 0, 0, v0, v1, v2);
-                }
-                __syncthreads();
-                // ---- prefix along x: one row of one plane per thread, in
-                // chunks of 4 with the next chunk loaded before this one is
-                // stored (the loads need not wait for the stores)
-                if (tid < 3 * kT) {
-                    uint32_t* E = S.E[tid / kT];
-                    const int y = tid % kT;
-                    uint32_t cur[4], nxt[4], run = 0u;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) cur[k] = E[sw(y, k)];
+                    for (int k = 0; k < kPlanes; ++k) z[k] = __reduce_add_sync(0xffffffffu, z[k]);
+                    if (lane == 0) {
 #pragma unroll
-                    for (int x0 = 0; x0 < kT; x0 += 4) {
-                        if (x0 + 4 < kT) {
+                        for (int k = 0; k < kPlanes; ++k)
+                            if (z[k]) atomicAdd(&S.E[k][0], z[k]);
+                    }
+                    __syncthreads();
+                    // ---- prefix along x: one row of one plane per thread, in
+                    // chunks of 4 with the next chunk loaded before this one is
+                    // stored (the loads need not wait for the stores)
+                    if (tid < kPlanes * kT) {
+                        uint32_t* E = S.E[tid / kT];
+                        const int y = tid % kT;
+                        uint32_t cur[4], nxt[4], run = 0u;
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) nxt[k] = E[sw(y, x0 + 4 + k)];
+                        for (int k = 0; k < 4; ++k) cur[k] = E[sw(y, k)];
+#pragma unroll
+                        for (int x0 = 0; x0 < kT; x0 += 4) {
+                            if (x0 + 4 < kT) {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) nxt[k] = E[sw(y, x0 + 4 + k)];
+                            }
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                run += cur[k];
+                                E[sw(y, x0 + k)] = run;
+                            }
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
                         }
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            run += cur[k];
-                            E[sw(y, x0 + k)] = run;
-                        }
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
                     }
-                }
-                __syncthreads();
-                // ---- prefix along y, in two steps: segment column sums ...
-                {
-                    uint32_t s0 = 0u, s1 = 0u, s2 = 0u;
+                    __syncthreads();
+                    // ---- prefix along y in three steps: the column sums of each
+                    // row segment ...
+#pragma unroll
+                    for (int k = 0; k < kPlanes; ++k) {
+                        uint32_t s = 0u;
+#pragma unroll
+                        for (int r = 0; r < kSegRows; ++r) s += S.E[k][sw(sg * kSegRows + r, cx)];
+                        S.u.seg[sg][k][cx] = s;
+                    }
+                    __syncthreads();
+                    // ... their exclusive prefix over the segments ...
+                    if (tid < kPlanes * kT) {
+                        const int k = tid / kT, c = tid % kT;
+                        uint32_t run = 0u;
+#pragma unroll
+                        for (int s = 0; s < kSegs; ++s) {
+                            const uint32_t v = S.u.seg[s][k][c];
+                            S.u.seg[s][k][c] = run;
+                            run += v;
+                        }
+                    }
+                    __syncthreads();
+                    // ... then this segment's rows, contracted as they come
+                    uint32_t run[kPlanes];
+#pragma unroll
+                    for (int k = 0; k < kPlanes; ++k) run[k] = S.u.seg[sg][k][cx];
+                    const float2 ux = S.ph[kT + cx];   // (cos a_X, sin a_X) of this column
+                    const float kh = 0.25f * inv, kd = lamq * inv;
 #pragma unroll
                     for (int r = 0; r < kSegRows; ++r) {
-                        const int o = sw(sg * kSegRows + r, cx);
-                        s0 += S.E[0][o];
-                        s1 += S.E[1][o];
-                        s2 += S.E[2][o];
+                        const int y = sg * kSegRows + r;
+                        const int o = sw(y, cx);
+                        float f[kPlanes];
+#pragma unroll
+                        for (int k = 0; k < kPlanes; ++k) {
+                            run[k] += S.E[k][o];
+                            f[k] = (float)(int32_t)run[k];
+                        }
+                        const float2 vy = S.ph[y];   // (cos a_Y, sin a_Y)
+                        float t[3], tp[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            t[i] = fmaf(-vy.y, f[3 * i + 2], fmaf(vy.x, f[3 * i + 1], f[3 * i]));   // v . S_i.
+                            tp[i] = fmaf(vy.y, f[3 * i + 1], vy.x * f[3 * i + 2]);                // v' . S_i.
+                        }
+                        ah[r] = fmaf(kh, fmaf(-ux.y, t[2], fmaf(ux.x, t[1], t[0])), ah[r]);
+                        adx[r] = fmaf(kd, fmaf(ux.y, t[1], ux.x * t[2]), adx[r]);
+                        ady[r] = fmaf(kd, fmaf(-ux.y, tp[2], fmaf(ux.x, tp[1], tp[0])), ady[r]);
                     }
-                    S.seg[sg][0][cx] = s0;
-                    S.seg[sg][1][cx] = s1;
-                    S.seg[sg][2][cx] = s2;
+                    __syncthreads();   // E, the segment sums and the phases are rewritten next
                 }
-                __syncthreads();
-                // ... then this segment's rows from the sums of the segments above
-                uint32_t run0 = 0u, run1 = 0u, run2 = 0u;
-                for (int s = 0; s < sg; ++s) {
-                    run0 += S.seg[s][0][cx];
-                    run1 += S.seg[s][1][cx];
-                    run2 += S.seg[s][2][cx];
-                }
-                // u_i(X), u'_i(X) with the constant factors and 1 / scale
-                const float2 ux = S.ph[kT + cx];   // (cos a_X, sin a_X) of this column
-                const float u = i == 0 ? 1.f : (i == 1 ? ux.x : -ux.y);
-                const float up = i == 0 ? 0.f : (i == 1 ? ux.y : ux.x);
-                const float ku = 0.25f * u * inv, kup = lamq * up * inv, kud = lamq * u * inv;
+            }
+        }
+
+        // ---- store: the group's partial planes, or (one group) the blended maps
+        const int x = tx0 + cx;
+        if (x < sp.W) {
+            const size_t plane = (size_t)sp.W * sp.H;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                float* const dst = (G > 1 ? p.partial + ((size_t)g * 3 + f) * plane : p.out + (size_t)f * plane) + x;
 #pragma unroll
                 for (int r = 0; r < kSegRows; ++r) {
-                    const int y = sg * kSegRows + r;
-                    const int o = sw(y, cx);
-                    run0 += S.E[0][o];
-                    run1 += S.E[1][o];
-                    run2 += S.E[2][o];
-                    const float2 vy = S.ph[y];   // (cos a_Y, sin a_Y)
-                    const float f0 = (float)(int32_t)run0, f1 = (float)(int32_t)run1, f2 = (float)(int32_t)run2;
-                    const float t = fmaf(-vy.y, f2, fmaf(vy.x, f1, f0));   // v . S_i.
-                    const float tp = fmaf(vy.y, f1, vy.x * f2);            // v' . S_i.
-                    ah[r] = fmaf(ku, t, ah[r]);
-                    adx[r] = fmaf(kup, t, adx[r]);
-                    ady[r] = fmaf(kud, tp, ady[r]);
+                    const int y = ty0 + sg * kSegRows + r;
+                    const float v = f == 0 ? ah[r] : (f == 1 ? adx[r] : ady[r]);
+                    if (y < sp.H) dst[(size_t)y * sp.W] = G > 1 ? v : blend1(sp, x, y, f, v);
                 }
-                __syncthreads();   // E and seg are rewritten by the next group
             }
-            }   // passes
         }
-        bb = be;
+        __syncthreads();   // the item slot and the descriptors are rewritten next
     }
-
-    // ---- store: the group's partial planes, or (one group) the blended maps
-    const int x = tx0 + cx;
-    if (x >= sp.W) return;
-    const size_t plane = (size_t)sp.W * sp.H;
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-        float* const dst = (G > 1 ? p.partial + ((size_t)g * 3 + f) * plane : p.out + (size_t)f * plane) + x;
-#pragma unroll
-        for (int r = 0; r < kSegRows; ++r) {
-            const int y = ty0 + sg * kSegRows + r;
-            const float v = f == 0 ? ah[r] : (f == 1 ? adx[r] : ady[r]);
-            if (y < sp.H) dst[(size_t)y * sp.W] = G > 1 ? v : blend1(sp, x, y, f, v);
+    // the last CTA out resets the queue for the next launch: every CTA takes
+    // its last ticket before it counts itself out
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+            queue[0] = 0u;
+            queue[1] = 0u;
+            __threadfence();
         }
     }
 }
@@ -427,11 +414,17 @@ int synth_sat_ctas_per_sm() {
 }
 
 cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
-                             const BlendSpan* spans, int n_spans, cudaStream_t st) {
+                             const BlendSpan* spans, int n_spans, unsigned int* queue, cudaStream_t st) {
     cudaError_t e = sat_attributes();
     if (e != cudaSuccess) return e;
     if (n_items > 0) {
-        e = launch_pdl(k_synth_sat, n_items, kSatThreads, sizeof(SatSmem), st, items, pdevs, sps);
+        // persistent grid: one CTA per resident slot, no more than the items
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return cudaGetLastError();
+        const int grid = min(n_items, sms * max(1, synth_sat_ctas_per_sm()));
+        e = launch_pdl(k_synth_sat, grid, kSatThreads, sizeof(SatSmem), st, items, n_items, pdevs, sps, queue);
         count_launches(1);
         if (e != cudaSuccess) return e;
     }

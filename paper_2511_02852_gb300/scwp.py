@@ -26,10 +26,10 @@ SYNTH_GATHER, SYNTH_LAYERED, SYNTH_GATHER_FP32, SYNTH_GATHER_FP16, SYNTH_SAT = 0
 (TAB_OMEGA, TAB_K, TAB_C, TAB_R, TAB_E, TAB_EDGES, TAB_AMP, TAB_RQ, TAB_VX, TAB_VY, TAB_QX,
  TAB_QY, TAB_WAKE_VX, TAB_WAKE_VY, TAB_WAKE_QX, TAB_WAKE_QY, TAB_CARRY) = range(17)
 STATUS = {0: "SCWP_OK", 1: "SCWP_E_INVALID", 2: "SCWP_E_NOMEM", 3: "SCWP_E_CAPACITY",
-          4: "SCWP_E_CUDA", 5: "SCWP_E_TIMEOUT", 6: "SCWP_E_STATE", 7: "SCWP_E_INCOMPLETE"}
-# statuses of scwp_stats_get that still fill the statistics: the frame's
-# error flags say what happened (bit 0 pool full, bit 2 synthesis limit)
-_STATS_FLAGGED = (3, 7)
+          4: "SCWP_E_CUDA", 5: "SCWP_E_TIMEOUT", 6: "SCWP_E_STATE"}
+# the status of scwp_stats_get that still fills the statistics: the frame's
+# error flags say what happened (bit 0: pool full, injection truncated)
+_STATS_FLAGGED = (3,)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

@@ -205,19 +205,22 @@ def test_sat_fine_bins_many_rows_and_three_radix_passes():
     sc.close()
 
 
-def test_sat_row_table_limit_is_reported_apart_from_pool_overflow():
+def test_sat_bucket_rows_beyond_the_row_table():
     """One-cell bins on a 0.1 m patch whose longest bucket has R = 290
     cells: 64 + 2R = 645 bin rows of that bucket reach a tile, more than the
-    summed-area kernel's 512-row table.  The kernel leaves that bucket out
-    of those tiles and says so: error flag bit 2 and SCWP_E_INCOMPLETE from
-    scwp_stats_get, not the pool-overflow flag."""
-    import ctypes as C
-    from paper_2511_02852_gb300 import scwp
+    summed-area kernel's 512-row table, so the kernel takes the bucket in two
+    row chunks.  Bins bit-exact, maps within the contract, no error flag."""
     cfg = wl.scaled(wl.small_jonswap(), bin_cells=1, cell=0.1)
     sc = sat_scene(cfg)
+    orc = OracleScene(cfg)
     sc.step(cfg["dt"])
-    st = scwp.scwp_stats()
-    rc = scwp.lib().scwp_stats_get(sc.ctx, 0, C.byref(st))
-    assert rc == 7, scwp.STATUS.get(rc, rc)          # SCWP_E_INCOMPLETE
-    assert st.error_flags & 4 and not st.error_flags & 1
+    orc.step(cfg["dt"])
+    info = sc.info(0)
+    R = orc.patches[0].T.R
+    assert 64 + 2 * int(R.max()) // 65536 > 512 and info.bin_cells[0] == 1
+    compare_state(sc, orc, 0)
+    compare_bins(sc, orc, 0)
+    ref, _ = orc.patch_maps(0)
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), "sat rows beyond the table")
+    assert sc.stats(0).error_flags == 0
     sc.close()
