@@ -39,15 +39,20 @@
 // heaviest-first order; the last CTA to finish resets the queue for the next
 // launch, so no CTA ever waits on another).  All nine S_ij planes of a
 // bucket live in shared memory at once (144 KB), so each candidate bump is
-// staged and turned into corner events exactly once per pass: the bin rows
-// that reach the tile are read into a row table, the candidates are staged in
-// chunks of 2048 (each thread finds its candidate's row by a binary search of
-// the row table and reads the 32-byte record from L2), and each staged
-// candidate adds its nine weights at up to four corners.  Bumps whose box
-// starts at the tile's first texel in both axes (every bump covering the
-// whole tile among them) sum their (0, 0) corner in registers, which one
-// warp reduction adds.  A bucket whose bin rows exceed the row table is taken
-// in row chunks, each a pass of its own.
+// staged and turned into corner events exactly once per pass.  Per item, the
+// buckets' bin geometry and the bin rows that reach the tile are read once
+// into a row table (a bucket with more rows than the table spans several
+// segments, each a pass of its own).  Candidates are staged in chunks of
+// 1536: each thread finds its candidate's row by a binary search of the row
+// table and reads the 32-byte record from L2.  Each staged candidate adds its
+// nine weights at up to four corners; bumps whose box starts at the tile's
+// first texel in both axes (every bump covering the whole tile among them)
+// sum their (0, 0) corner in registers, which one warp reduction adds.  The
+// x prefix takes 18 of the 32 warps; meanwhile the other 14 fetch the
+// bucket's texel phases and stage the next segment's first chunk, so that
+// the L2 latency of the staging overlaps the prefix passes.  The last
+// column pass zeroes each difference-array element it reads, so no pass
+// needs a clearing phase.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -63,27 +68,29 @@ constexpr int kSatThreads = 1024;
 constexpr int kSegs = kSatThreads / kT;      // row segments of the column pass
 constexpr int kSegRows = kT / kSegs;         // rows per segment
 constexpr int kPlanes = 9;                   // S_ij, plane 3 i + j
-constexpr int kRowCap = 512;                 // bin rows of a bucket held at once
-constexpr int kStage = 2048;                 // candidates staged at once
+constexpr int kScanThreads = kPlanes * kT;   // one row (or column) scan per thread
+constexpr int kRowCap = 256;                 // bin rows held at once (all segments of a batch)
+constexpr int kMaxSeg = 64;                  // segments per batch
+constexpr int kStage = 1536;                 // candidates staged at once
 constexpr int32_t kQs = 65536, kHalfs = 32768;
 static_assert(kSegs * kSegRows == kT && kSegs == 16, "column-pass mapping");
-static_assert(kPlanes * kT <= kSatThreads, "one row scan per thread");
-
-struct Staged {
-    float4 c4[kStage];                    // A, cos, sin (x), cos (y)
-    float2 c2[kStage];                    // sin (y), support box (bits)
-};
+static_assert(kScanThreads % 32 == 0 && kScanThreads + 128 <= kSatThreads, "scan warps and helper warps");
 
 struct SatSmem {
-    uint32_t E[kPlanes][kT * kT];         // difference arrays, then prefix sums
-    union {
-        Staged st;                        // the staged candidates (events phase)
-        uint32_t seg[kSegs][kPlanes][kT]; // column sums of each row segment (column pass)
-    } u;
-    float2 ph[2 * kT];                    // the bucket's texel phases (cos, sin) a: rows, then columns
-    int32_t rs[kRowCap];                  // first record of each bin row
-    int32_t cum[kRowCap];                 // candidates of the bucket before the row
-    int32_t item, ncand, pad0, pad1;
+    uint32_t E[kPlanes][kT * kT];         // difference arrays, then prefix sums; zero between passes
+    uint32_t seg[kSegs][kPlanes][kT];     // column sums of each row segment
+    float4 c4[kStage];                    // staged candidates: A, cos, sin (x), cos (y)
+    float2 c2[kStage];                    //                    sin (y), support box (bits)
+    float2 ph[2][2 * kT];                 // texel phases (cos, sin) a of a segment's bucket: rows, then columns
+    int32_t rs[kRowCap];                  // first record of each bin row of the batch
+    int32_t cum[kRowCap];                 // candidates of the segment before the row
+    // the item's buckets
+    int32_t mR[kMaxBuckets], mC[kMaxBuckets], mnbx[kMaxBuckets], mbase[kMaxBuckets];
+    int32_t mbx_lo[kMaxBuckets], mbx_hi[kMaxBuckets], mby_lo[kMaxBuckets], mnrows[kMaxBuckets];
+    float mamax[kMaxBuckets], msatc[kMaxBuckets];
+    // the batch's segments: bucket (item-relative), first row, first table row, candidates
+    int32_t sgb[kMaxSeg], sgr0[kMaxSeg], sgrb[kMaxSeg + 1], sgnc[kMaxSeg];
+    int32_t item, patch, nseg, bt_next, bt_r0, staged;
     alignas(16) unsigned char pd[sizeof(PatchDev)];
     alignas(16) unsigned char spd[sizeof(SynthParams)];
 };
@@ -113,6 +120,46 @@ __device__ __forceinline__ uint32_t warp_scan(uint32_t v, int lane) {
     return v;
 }
 
+// passes of segment candidates: a (tile, bucket) of n candidates goes in
+// ceil(n^1.5 / sat_c) passes, so that the integer rounding of its corner
+// weights stays within the bound the host set
+__device__ __forceinline__ int pass_size(int ncand, float satc) {
+    const float nf = (float)ncand;
+    const int kch = max(1, (int)ceilf(nf * sqrtf(nf) / satc));
+    return (ncand + kch - 1) / kch;
+}
+
+// Stage candidates s0 .. s0 + ns - 1 of segment s (thread t of nt): find the
+// candidate's bin row in the segment's part of the row table (the last row
+// whose exclusive candidate prefix is <= f), read its 32-byte record and
+// store its amplitude, phase pairs and support box clipped to the tile.
+__device__ __forceinline__ void stage(SatSmem& S, const BumpRec* rec, int s, int s0, int ns, int32_t X0,
+                                      int32_t Y0, int t, int nt) {
+    const int q0 = S.sgrb[s], q1 = S.sgrb[s + 1];
+    const int R = S.mR[S.sgb[s]];
+    for (int k = t; k < ns; k += nt) {
+        const int f = s0 + k;
+        int lo = q0, hi = q1 - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.cum[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const float4* rp = reinterpret_cast<const float4*>(rec + S.rs[lo] + (f - S.cum[lo]));
+        const float4 rx = rp[0];   // x, cos, sin, id
+        const float4 ry = rp[1];   // y, cos, sin, A
+        const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
+        // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
+        const int a = clamp_t(((xb - R - X0) >> 16) + 1);
+        const int b = clamp_t(-((X0 - xb - R) >> 16));
+        const int c = clamp_t(((yb - R - Y0) >> 16) + 1);
+        const int d = clamp_t(-((Y0 - yb - R) >> 16));
+        const uint32_t box =
+            (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) | ((uint32_t)d << 21) : 0u;
+        S.c4[k] = make_float4(ry.w, rx.y, rx.z, ry.y);
+        S.c2[k] = make_float2(ry.z, __uint_as_float(box));
+    }
+}
+
 __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* items, int n_items,
                                                             const PatchDev* pdevs, const SynthParams* sps,
                                                             unsigned int* queue) {
@@ -122,13 +169,21 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
     // column pass: this thread owns texel column cx of rows sg*4 .. sg*4 + 3
     const int cx = tid & (kT - 1), sg = tid / kT;
     pdl_enter();
+    // E starts zeroed, and every pass leaves it zeroed again
+    {
+        uint4* e4 = reinterpret_cast<uint4*>(&S.E[0][0]);
+        for (int k = tid; k < kPlanes * kT * kT / 4; k += kSatThreads) e4[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        S.item = (int)atomicAdd(queue, 1u);
+        S.patch = -1;
+    }
+    __syncthreads();
     for (;;) {
-        if (tid == 0) S.item = (int)atomicAdd(queue, 1u);
-        __syncthreads();
         const int ti = S.item;
         if (ti >= n_items) break;
         const TcItem it = items[ti];
-        {
+        if (it.patch != S.patch) {   // (uniform) items of one patch share its descriptors
             static_assert(sizeof(PatchDev) % 4 == 0 && sizeof(SynthParams) % 4 == 0, "descriptor copy");
             const uint32_t* a = reinterpret_cast<const uint32_t*>(pdevs + it.patch);
             const uint32_t* b = reinterpret_cast<const uint32_t*>(sps + it.patch);
@@ -136,8 +191,9 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                 reinterpret_cast<uint32_t*>(S.pd)[k] = a[k];
             for (int k = tid; k < (int)(sizeof(SynthParams) / 4); k += kSatThreads)
                 reinterpret_cast<uint32_t*>(S.spd)[k] = b[k];
+            __syncthreads();
+            if (tid == 0) S.patch = it.patch;
         }
-        __syncthreads();
         const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
         const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
         const int G = it.groups, g = it.group;
@@ -145,67 +201,114 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
         const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
         const int b_begin = max((g * sp.nb) / G, sp.b_lo);
         const int b_end = min(((g + 1) * sp.nb) / G, sp.b_hi);
+        const int nbk = max(0, b_end - b_begin);
         // Q16.16 centres of the tile's first and last texel columns and rows
         const int32_t X0 = tx0 * kQs + kHalfs, X1 = X0 + (kT - 1) * kQs;
         const int32_t Y0 = ty0 * kQs + kHalfs, Y1 = Y0 + (kT - 1) * kQs;
         const float lamq = 0.5f * sp.lam_half;   // lam / 4
-        float ah[kSegRows], adx[kSegRows], ady[kSegRows];
-#pragma unroll
-        for (int r = 0; r < kSegRows; ++r) ah[r] = adx[r] = ady[r] = 0.f;
-
-        for (int b = b_begin; b < b_end; ++b) {
-            const BucketDev bk = p.bk[b];
-            const float amax = p.amax[b];
-            // bins hold x_b + R in [bx C, (bx + 1) C): the bin rows and columns
-            // that reach the tile
+        // ---- the item's buckets, one thread each: bins hold x_b + R in
+        // [bx C, (bx + 1) C); the bin rows and columns that reach the tile
+        for (int t = tid; t < nbk; t += kSatThreads) {
+            const BucketDev bk = p.bk[b_begin + t];
+            const float amax = p.amax[b_begin + t];
             const int bx_lo = (int)((int64_t)X0 / bk.C);
             const int bx_hi = min((int)(((int64_t)X1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nbx - 1);
             const int by_lo = (int)((int64_t)Y0 / bk.C);
             const int by_hi = min((int)(((int64_t)Y1 + 2 * (int64_t)bk.R - 1) / bk.C), bk.nby - 1);
-            const int nrows = (bx_lo > bx_hi || by_lo > by_hi) ? 0 : by_hi - by_lo + 1;
-            if (nrows == 0 || !(amax > 0.f)) continue;   // (uniform over the CTA)
-            // the bucket's texel phases (every read of the previous bucket's
-            // ended before its last barrier)
-            for (int k = tid; k < 2 * kT; k += kSatThreads)
-                S.ph[k] = p.phase[(size_t)b * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
-            for (int r0 = 0; r0 < nrows; r0 += kRowCap) {
-                const int nr = min(kRowCap, nrows - r0);
-                for (int q = tid; q < nr; q += kSatThreads) {
-                    const int key0 = bk.base + (by_lo + r0 + q) * bk.nbx;
-                    const int s0 = (int)p.offsets[key0 + bx_lo];
-                    S.rs[q] = s0;
-                    S.cum[q] = (int)p.offsets[key0 + bx_hi + 1] - s0;   // row length for now
-                }
-                __syncthreads();
-                if (warp == 0) {   // exclusive prefix of the row lengths
-                    uint32_t carry = 0u;
-                    for (int q = 0; q < nr; q += 32) {
-                        const uint32_t l = q + lane < nr ? (uint32_t)S.cum[q + lane] : 0u;
-                        const uint32_t inc = warp_scan(l, lane);
-                        if (q + lane < nr) S.cum[q + lane] = (int32_t)(carry + inc - l);
-                        carry += __shfl_sync(0xffffffffu, inc, 31);
+            S.mR[t] = bk.R;
+            S.mC[t] = bk.C;
+            S.mnbx[t] = bk.nbx;
+            S.mbase[t] = bk.base;
+            S.mbx_lo[t] = bx_lo;
+            S.mbx_hi[t] = bx_hi;
+            S.mby_lo[t] = by_lo;
+            S.mnrows[t] = (bx_lo > bx_hi || by_lo > by_hi || !(amax > 0.f)) ? 0 : by_hi - by_lo + 1;
+            S.mamax[t] = amax;
+            S.msatc[t] = bk.sat_c;
+        }
+        float ah[kSegRows], adx[kSegRows], ady[kSegRows];
+#pragma unroll
+        for (int r = 0; r < kSegRows; ++r) ah[r] = adx[r] = ady[r] = 0.f;
+        int t_next = 0, sub_r0 = 0;   // the first bucket (and its row) not yet batched
+        for (;;) {
+            __syncthreads();   // bucket table written; the previous batch is done with the row table
+            // ---- a batch: segments (bucket, row range) whose bin rows fit the row table
+            // (a bucket with more rows than the table spans several segments)
+            if (tid == 0) {
+                int n = 0, rows = 0, t = t_next, r0 = sub_r0;
+                while (t < nbk && n < kMaxSeg) {
+                    const int left = S.mnrows[t] - r0;
+                    if (left <= 0) {
+                        ++t;
+                        r0 = 0;
+                        continue;
                     }
-                    if (lane == 0) S.ncand = (int32_t)carry;
+                    const int take = min(left, kRowCap - rows);
+                    if (take <= 0) break;
+                    S.sgb[n] = t;
+                    S.sgr0[n] = r0;
+                    S.sgrb[n] = rows;
+                    rows += take;
+                    ++n;
+                    r0 += take;
+                    if (r0 >= S.mnrows[t]) {
+                        ++t;
+                        r0 = 0;
+                    }
                 }
-                __syncthreads();
-                const int ncand = S.ncand;
-                if (ncand == 0) continue;
+                S.sgrb[n] = rows;
+                S.nseg = n;
+                S.bt_next = t;
+                S.bt_r0 = r0;
+                S.staged = -1;
+            }
+            __syncthreads();
+            const int nseg = S.nseg;
+            t_next = S.bt_next;
+            sub_r0 = S.bt_r0;
+            if (nseg == 0) break;
+            // ---- the batch's row table: first record and length of every row
+            const int nq = S.sgrb[nseg];
+            for (int q = tid; q < nq; q += kSatThreads) {
+                int s = 0;
+                while (S.sgrb[s + 1] <= q) ++s;
+                const int t = S.sgb[s];
+                const int r = S.sgr0[s] + (q - S.sgrb[s]);
+                const int key0 = S.mbase[t] + (S.mby_lo[t] + r) * S.mnbx[t];
+                const int s0 = (int)p.offsets[key0 + S.mbx_lo[t]];
+                S.rs[q] = s0;
+                S.cum[q] = (int)p.offsets[key0 + S.mbx_hi[t] + 1] - s0;   // row length for now
+            }
+            __syncthreads();
+            // exclusive prefix of the row lengths within each segment (warp w:
+            // segments w, w + 32)
+            for (int s = warp; s < nseg; s += kSatThreads / 32) {
+                const int q0 = S.sgrb[s], q1 = S.sgrb[s + 1];
+                uint32_t carry = 0u;
+                for (int q = q0; q < q1; q += 32) {
+                    const uint32_t l = q + lane < q1 ? (uint32_t)S.cum[q + lane] : 0u;
+                    const uint32_t inc = warp_scan(l, lane);
+                    if (q + lane < q1) S.cum[q + lane] = (int32_t)(carry + inc - l);
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                if (lane == 0) S.sgnc[s] = (int32_t)carry;
+            }
+            __syncthreads();
+
+            for (int s = 0; s < nseg; ++s) {
+                const int ncand = S.sgnc[s];
+                if (ncand == 0) continue;   // (uniform)
+                const int t = S.sgb[s];
+                const int b = b_begin + t;
+                const float amax = S.mamax[t];
                 if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)ncand);
-                // passes of at most mch candidates, so that the integer rounding
-                // of the corner weights stays within the bound set on the host
-                const float nf = (float)ncand;
-                const int kch = max(1, (int)ceilf(nf * sqrtf(nf) / bk.sat_c));
-                const int mch = (ncand + kch - 1) / kch;
+                const int mch = pass_size(ncand, S.msatc[t]);
+                float2* const ph = S.ph[s & 1];
                 for (int c0 = 0; c0 < ncand; c0 += mch) {
                     const int c1 = min(ncand, c0 + mch);
                     const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
                     const float scale = 1073741824.f / bound;              // 2^30 / bound
                     const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
-                    {
-                        uint4* e4 = reinterpret_cast<uint4*>(&S.E[0][0]);
-                        for (int k = tid; k < kPlanes * kT * kT / 4; k += kSatThreads)
-                            e4[k] = make_uint4(0u, 0u, 0u, 0u);
-                    }
                     // the (0, 0) corner, shared by every bump whose box starts at
                     // the tile's first texel in both axes: per-thread sums
                     uint32_t z[kPlanes];
@@ -213,38 +316,16 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                     for (int k = 0; k < kPlanes; ++k) z[k] = 0u;
                     for (int s0 = c0; s0 < c1; s0 += kStage) {
                         const int ns = min(kStage, c1 - s0);
-                        __syncthreads();   // E cleared; the previous chunk's events done
-                        // ---- stage candidates s0 .. s0 + ns - 1 of the row chunk
-                        for (int k = tid; k < ns; k += kSatThreads) {
-                            const int f = s0 + k;
-                            int lo = 0, hi = nr - 1;   // the last row with cum <= f holds f
-                            while (lo < hi) {
-                                const int mid = (lo + hi + 1) >> 1;
-                                if (S.cum[mid] <= f) lo = mid; else hi = mid - 1;
-                            }
-                            const float4* rp = reinterpret_cast<const float4*>(p.rec + S.rs[lo] + (f - S.cum[lo]));
-                            const float4 rx = rp[0];   // x, cos, sin, id
-                            const float4 ry = rp[1];   // y, cos, sin, A
-                            const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
-                            // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
-                            const int a = clamp_t(((xb - bk.R - X0) >> 16) + 1);
-                            const int bb = clamp_t(-((X0 - xb - bk.R) >> 16));
-                            const int c = clamp_t(((yb - bk.R - Y0) >> 16) + 1);
-                            const int d = clamp_t(-((Y0 - yb - bk.R) >> 16));
-                            const uint32_t box = (a < bb && c < d)
-                                                     ? (uint32_t)a | ((uint32_t)bb << 7) | ((uint32_t)c << 14) |
-                                                           ((uint32_t)d << 21)
-                                                     : 0u;
-                            S.u.st.c4[k] = make_float4(ry.w, rx.y, rx.z, ry.y);
-                            S.u.st.c2[k] = make_float2(ry.z, __uint_as_float(box));
+                        if (!(S.staged == s && s0 == 0)) {   // (uniform) else staged ahead
+                            stage(S, p.rec, s, s0, ns, X0, Y0, tid, kSatThreads);
+                            __syncthreads();
                         }
-                        __syncthreads();
                         // ---- corner events of the staged candidates
                         for (int k = tid; k < ns; k += kSatThreads) {
-                            const float2 e = S.u.st.c2[k];
+                            const float2 e = S.c2[k];
                             const uint32_t box = __float_as_uint(e.y);
                             if (box == 0u) continue;   // no texel of the tile in the support
-                            const float4 cc = S.u.st.c4[k];
+                            const float4 cc = S.c4[k];
                             const int a = box & 127, bb = (box >> 7) & 127, c = (box >> 14) & 127,
                                       d = (box >> 21) & 127;
                             const float A = cc.x, qc = cc.w, qs = e.x;
@@ -269,19 +350,21 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                             if (d < kT) event9(S, a, d, w, true);
                             if (bb < kT && d < kT) event9(S, bb, d, w, false);
                         }
-                    }
+                        if (s0 + kStage >= c1) {   // the pass's last chunk: the (0, 0) corner
 #pragma unroll
-                    for (int k = 0; k < kPlanes; ++k) z[k] = __reduce_add_sync(0xffffffffu, z[k]);
-                    if (lane == 0) {
+                            for (int k = 0; k < kPlanes; ++k) z[k] = __reduce_add_sync(0xffffffffu, z[k]);
+                            if (lane == 0) {
 #pragma unroll
-                        for (int k = 0; k < kPlanes; ++k)
-                            if (z[k]) atomicAdd(&S.E[k][0], z[k]);
+                                for (int k = 0; k < kPlanes; ++k)
+                                    if (z[k]) atomicAdd(&S.E[k][0], z[k]);
+                            }
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
-                    // ---- prefix along x: one row of one plane per thread, in
-                    // chunks of 4 with the next chunk loaded before this one is
-                    // stored (the loads need not wait for the stores)
-                    if (tid < kPlanes * kT) {
+                    if (tid < kScanThreads) {
+                        // ---- prefix along x: one row of one plane per thread, in
+                        // chunks of 4 with the next chunk loaded before this one
+                        // is stored (the loads need not wait for the stores)
                         uint32_t* E = S.E[tid / kT];
                         const int y = tid % kT;
                         uint32_t cur[4], nxt[4], run = 0u;
@@ -301,35 +384,53 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
 #pragma unroll
                             for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
                         }
+                    } else {
+                        // ---- meanwhile the other warps fetch this bucket's texel
+                        // phases and, after the segment's last pass, stage the first
+                        // chunk of the next segment that has candidates
+                        const int h = tid - kScanThreads, nh = kSatThreads - kScanThreads;
+                        if (h < 2 * kT)
+                            ph[h] = p.phase[(size_t)b * p.phase_len + (h < kT ? ty0 + h : tx0 + (h - kT))];
+                        if (c1 == ncand) {
+                            int sn = s + 1;
+                            while (sn < nseg && S.sgnc[sn] == 0) ++sn;
+                            if (sn < nseg) {
+                                const int mn = pass_size(S.sgnc[sn], S.msatc[S.sgb[sn]]);
+                                stage(S, p.rec, sn, 0, min(kStage, mn), X0, Y0, h, nh);
+                                if (h == 0) S.staged = sn;
+                            }
+                        }
                     }
                     __syncthreads();
                     // ---- prefix along y in three steps: the column sums of each
                     // row segment ...
 #pragma unroll
                     for (int k = 0; k < kPlanes; ++k) {
-                        uint32_t s = 0u;
+                        uint32_t v = 0u;
 #pragma unroll
-                        for (int r = 0; r < kSegRows; ++r) s += S.E[k][sw(sg * kSegRows + r, cx)];
-                        S.u.seg[sg][k][cx] = s;
+                        for (int r = 0; r < kSegRows; ++r) v += S.E[k][sw(sg * kSegRows + r, cx)];
+                        S.seg[sg][k][cx] = v;
                     }
                     __syncthreads();
                     // ... their exclusive prefix over the segments ...
-                    if (tid < kPlanes * kT) {
+                    if (tid < kScanThreads) {
                         const int k = tid / kT, c = tid % kT;
                         uint32_t run = 0u;
 #pragma unroll
-                        for (int s = 0; s < kSegs; ++s) {
-                            const uint32_t v = S.u.seg[s][k][c];
-                            S.u.seg[s][k][c] = run;
+                        for (int q = 0; q < kSegs; ++q) {
+                            const uint32_t v = S.seg[q][k][c];
+                            S.seg[q][k][c] = run;
                             run += v;
                         }
                     }
                     __syncthreads();
-                    // ... then this segment's rows, contracted as they come
+                    // ... then this segment's rows, contracted as they come; each
+                    // element of E is zeroed once read (the next pass starts from
+                    // a cleared difference array)
                     uint32_t run[kPlanes];
 #pragma unroll
-                    for (int k = 0; k < kPlanes; ++k) run[k] = S.u.seg[sg][k][cx];
-                    const float2 ux = S.ph[kT + cx];   // (cos a_X, sin a_X) of this column
+                    for (int k = 0; k < kPlanes; ++k) run[k] = S.seg[sg][k][cx];
+                    const float2 ux = ph[kT + cx];   // (cos a_X, sin a_X) of this column
                     const float kh = 0.25f * inv, kd = lamq * inv;
 #pragma unroll
                     for (int r = 0; r < kSegRows; ++r) {
@@ -339,20 +440,21 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
 #pragma unroll
                         for (int k = 0; k < kPlanes; ++k) {
                             run[k] += S.E[k][o];
+                            S.E[k][o] = 0u;
                             f[k] = (float)(int32_t)run[k];
                         }
-                        const float2 vy = S.ph[y];   // (cos a_Y, sin a_Y)
-                        float t[3], tp[3];
+                        const float2 vy = ph[y];   // (cos a_Y, sin a_Y)
+                        float tt[3], tp[3];
 #pragma unroll
                         for (int i = 0; i < 3; ++i) {
-                            t[i] = fmaf(-vy.y, f[3 * i + 2], fmaf(vy.x, f[3 * i + 1], f[3 * i]));   // v . S_i.
-                            tp[i] = fmaf(vy.y, f[3 * i + 1], vy.x * f[3 * i + 2]);                // v' . S_i.
+                            tt[i] = fmaf(-vy.y, f[3 * i + 2], fmaf(vy.x, f[3 * i + 1], f[3 * i]));   // v . S_i.
+                            tp[i] = fmaf(vy.y, f[3 * i + 1], vy.x * f[3 * i + 2]);                 // v' . S_i.
                         }
-                        ah[r] = fmaf(kh, fmaf(-ux.y, t[2], fmaf(ux.x, t[1], t[0])), ah[r]);
-                        adx[r] = fmaf(kd, fmaf(ux.y, t[1], ux.x * t[2]), adx[r]);
+                        ah[r] = fmaf(kh, fmaf(-ux.y, tt[2], fmaf(ux.x, tt[1], tt[0])), ah[r]);
+                        adx[r] = fmaf(kd, fmaf(ux.y, tt[1], ux.x * tt[2]), adx[r]);
                         ady[r] = fmaf(kd, fmaf(-ux.y, tp[2], fmaf(ux.x, tp[1], tp[0])), ady[r]);
                     }
-                    __syncthreads();   // E, the segment sums and the phases are rewritten next
+                    __syncthreads();   // E cleared; the segment sums and the staging area are free
                 }
             }
         }
@@ -372,7 +474,8 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                 }
             }
         }
-        __syncthreads();   // the item slot and the descriptors are rewritten next
+        if (tid == 0) S.item = (int)atomicAdd(queue, 1u);
+        __syncthreads();   // the next item's ticket
     }
     // the last CTA out resets the queue for the next launch: every CTA takes
     // its last ticket before it counts itself out
