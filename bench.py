@@ -538,6 +538,21 @@ def timed_frames(sc, cfg, n, flush, stream):
     return sorted(a.elapsed_time(b) for a, b in zip(st_ev, en_ev)), ev
 
 
+def tune(sc, args, flush, dt):
+    """The summed-area autotuner on the scene's live frame (timed on the
+    device), then warm-up frames for the re-captured frame graphs."""
+    if args.no_tune or args.synth != "sat":
+        return None
+    rows, chosen, cached = sc.autotune(reps=3)
+    for _ in range(3):
+        flush.zero_()
+        sc.step(dt)
+    names = {0: "persistent nine-plane", 1: "three-group"}
+    return {"chosen": {"kernel": names[rows[chosen][0]], "group_multiplier": rows[chosen][1]},
+            "from_cache": cached,
+            "timed": [{"kernel": names[v], "group_multiplier": g, "synthesis_ms": m} for v, g, m in rows]}
+
+
 def frame_summary(ms, ev, mode):
     return {"mode": mode, "frames": len(ms), "value": ev / (sum(ms) / 1000.0), "unit": UNIT,
             "ms_per_step": sum(ms) / len(ms), "frames_per_s": 1000.0 * len(ms) / sum(ms),
@@ -560,10 +575,12 @@ def batched_vs_plain(args, flush, stream, frames):
         for _ in range(5):
             flush.zero_()
             sc.step(cfg["dt"])
+        tuned = tune(sc, args, flush, cfg["dt"])
         torch.cuda.synchronize()
         ms, ev = timed_frames(sc, cfg, frames, flush, stream)
         out[mode] = frame_summary(ms, ev, "one synthesis launch over all 32 patches, captured frame graph"
                                   if on else "one synthesis launch per patch, eager launches")
+        out[mode]["autotune"] = tuned
     out["speedup_frames_per_s"] = out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]
     sc.close()
     return out
@@ -600,6 +617,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         flush.zero_()
         sc.step(dt)
+    tuned = tune(sc, args, flush, dt)
     barrier()
     launches0 = sc.launch_count()
     props = torch.cuda.get_device_properties(local)
@@ -652,9 +670,11 @@ def run_ours(args):
         for _ in range(3):
             flush.zero_()
             sc.step(dt)
+        plain_tune = tune(sc, args, flush, dt)
         ms, ev = timed_frames(sc, cfg, max(10, min(args.steps, 50)), flush, stream)
         sc.set_batched(True)
         plain = frame_summary(ms, ev, "plain: one synthesis launch per patch, eager launches")
+        plain["autotune"] = plain_tune
 
     # the other synthesis on the same scene: the tensor-core gather beside the
     # summed-area default (its own roofline), for comparison
@@ -745,7 +765,7 @@ def run_ours(args):
             "live_particles": sum(sc.stats(p).live_particles for p in range(npatch)),
             "roofline": roofline, "roofline_fft": roof_fft, "cpu_baseline": cpu, "e2e": e2e,
             "plain": plain, "batched_vs_plain": bvp, "gather_tc": other,
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "autotune": tuned,
             "synth_groups": [sc.info(p).sat_groups if args.synth == "sat" else sc.info(p).synth_groups
                              for p in range(npatch)],
         }
@@ -782,6 +802,8 @@ def main():
     ap.add_argument("--plain", action="store_true",
                     help="one synthesis launch per patch, frames launched eagerly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the summed-area autotuner (scwp_autotune) before the timed frames")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="reference: strip seconds per step at most")
     ap.add_argument("--ref-total-seconds", type=float, default=60.0, help="reference: strip seconds in all")

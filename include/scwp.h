@@ -184,6 +184,8 @@ typedef struct scwp_patch_info {
     int32_t sat_slots;         /* resident CTA slots its plan assumed */
     int32_t frame_param_bytes; /* host-computed plan of one frame of this patch (injection
                                   counts, host-placed spawn points) copied to the device */
+    int32_t sat_variant;       /* summed-area kernel of this patch: 0 the persistent
+                                  nine-plane kernel, 1 the three-group kernel */
 } scwp_patch_info;
 
 /* Table identifiers for scwp_get_table (element type, count). */
@@ -311,6 +313,40 @@ scwp_status scwp_set_bucket_range(scwp_ctx* ctx, int32_t b_lo, int32_t b_hi);
  * paper has no counterpart (its frame is one scene on one GPU).  Returns
  * SCWP_E_INVALID for a null context; takes effect at the next synthesis. */
 scwp_status scwp_set_batched(scwp_ctx* ctx, int32_t on);
+
+/* Autotuner of the summed-area synthesis (SCWP_SYNTH_SAT), the frame's
+ * dominant stage.  The paper has no counterpart (its synthesis is one
+ * fixed-function pass).  Two kernel variants compute the same sums: the
+ * persistent nine-plane kernel (one 1024-thread CTA per SM pulling (tile,
+ * bucket group) items from a work queue) and the three-group kernel (two
+ * 512-thread CTAs per SM, one per item; offered only where every bucket
+ * reaches at most 512 bin rows of a tile).  For each variant and each
+ * bucket-group multiplier of the host plan (1, 1/2, 2) the tuner
+ * re-synthesises the last frame `reps` times on the context's stream (one
+ * warm-up, then CUDA events), keeps the configuration of the smallest median
+ * time, re-synthesises the last frame with it and caches it per device and
+ * workload signature (every patch's size, buckets, prefill, capacity, bin
+ * size, and the batching mode) for the life of the process; a later call
+ * with the same signature applies the cached choice without timing unless
+ * force != 0.  Needs at least one stepped frame; synchronises.  reps in
+ * 1..100.  SCWP_E_STATE if the context's mode is not SCWP_SYNTH_SAT. */
+#define SCWP_TUNE_MAX 8
+typedef struct scwp_tune_result {
+    int32_t n_configs;           /* configurations timed (1 with from_cache)      */
+    int32_t chosen;              /* index of the one kept                           */
+    int32_t from_cache;          /* 1: the cached choice was applied, nothing timed */
+    int32_t pad;
+    int32_t variant[SCWP_TUNE_MAX];   /* 0 nine-plane persistent, 1 three-group    */
+    double gmul[SCWP_TUNE_MAX];       /* bucket-group multiplier of the plan       */
+    double ms[SCWP_TUNE_MAX];         /* median synthesis + blend time, ms          */
+} scwp_tune_result;
+scwp_status scwp_autotune(scwp_ctx* ctx, int32_t reps, int32_t force, scwp_tune_result* out);
+
+/* Set the autotuner's choice by hand: summed-area kernel variant (0 or 1, as
+ * above) and bucket-group multiplier gmul (0.125..8) of the host plans.
+ * SCWP_E_INVALID for variant 1 when a patch's buckets exceed the three-group
+ * kernel's row table.  Synchronises; takes effect at the next synthesis. */
+scwp_status scwp_set_sat_plan(scwp_ctx* ctx, int32_t variant, double gmul);
 
 /* Stage timing with CUDA events on the context's stream: enable (1) or
  * disable (0).  scwp_timing_read sums, over the frames stepped since the

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libscwp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 CU_SOURCES = ["api.cu", "k_particles.cu", "k_fft.cu", "k_synth.cu", "k_synth_tc.cu", "k_layered.cu",
-              "noalloc.cu", "k_normals.cu", "k_synth_sat.cu"]
+              "noalloc.cu", "k_normals.cu", "k_synth_sat.cu", "k_synth_sat3.cu"]
 CXX_SOURCES = ["host_spectrum.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

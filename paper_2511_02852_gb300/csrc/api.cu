@@ -12,6 +12,8 @@
 #include <deque>
 #include <cmath>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <queue>
 #include <new>
 #include <string>
@@ -65,6 +67,8 @@ struct PatchHost {
     BlendSpan* d_sat_spans = nullptr;
     int sat_groups = 1;
     int sat_slots = 0;
+    int sat_item_cap = 0;             // capacity of d_sat_items (items of the largest G)
+    bool sat3_ok = false;             // every bucket fits the three-group kernel's row table
 };
 
 // A frame (or a scene's part of a frame) captured as CUDA graphs, one per
@@ -134,6 +138,8 @@ struct scwp_ctx {
     BlendSpan* d_bspans = nullptr;
     // the batched plan of the summed-area synthesis
     int sat_slots = 0;
+    int sat_variant = 0;              // 0: persistent nine-plane kernel, 1: three-group kernel
+    double sat_gmul = 1.0;            // bucket-group multiplier of the plans (the autotuner's)
     std::vector<TcItem> s_items;
     std::vector<BlendSpan> s_spans;
     TcItem* d_sitems = nullptr;
@@ -435,19 +441,16 @@ std::vector<BlendSpan> blend_spans(const PatchHost& P, int G) {
 
 // Plan of one patch launched alone: G minimises the simulated makespan over
 // the device's resident CTA slots plus the traffic of the group-sum blend.
-void plan_patch(PatchHost& P, int slots, bool sat = false) {
+// For the summed-area synthesis, gmul scales the chosen G (the autotuner's
+// search axis), within [1, gcap].
+void plan_patch(PatchHost& P, int slots, bool sat = false, double gmul = 1.0, int gcap = 16) {
     int tiles = 0;
     const std::vector<double> est = sat ? tile_bucket_sat(P, tiles) : tile_bucket_stages(P, tiles);
     const int nb = P.T.nb;
     double best_cost = 0.0;
     int& groups = sat ? P.sat_groups : P.dev.groups_tc;
     std::vector<TcItem>& plan = sat ? P.sat_items : P.tc_items;
-    // the summed-area items cost about the same per bucket; the smallest G
-    // that gives three waves over the slots, as far as the buckets allow
-    int g_lo = 1;
-    if (sat)
-        while (g_lo < std::min(nb, 16) && (double)tiles * g_lo < 3.0 * slots) ++g_lo;
-    for (int G = g_lo; G <= std::min(nb, 16); ++G) {
+    auto build = [&](int G) {   // the heaviest-first plan with G groups, and its modelled cost
         std::vector<double> work((size_t)tiles * G);
         for (int t = 0; t < tiles; ++t)
             for (int g = 0; g < G; ++g) work[(size_t)t * G + g] = item_work(est, nb, t, g, G);
@@ -455,15 +458,52 @@ void plan_patch(PatchHost& P, int slots, bool sat = false) {
         for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
         const double blend = G > 1 ? (G + 1) * 12.0 * P.T.W * P.T.H / kHbmBytesPerUs : 0.0;
-        const double cost = makespan(work, order, slots) * kStageUs + blend;
-        if (G == g_lo || cost < best_cost) {
-            best_cost = cost;
+        std::vector<TcItem> items;
+        for (int k : order) items.push_back(TcItem{P.index, k / G, k % G, G});
+        return std::make_pair(makespan(work, order, slots) * kStageUs + blend, items);
+    };
+    // the summed-area items cost about the same per bucket; the smallest G
+    // that gives three waves over the slots, as far as the buckets allow
+    const int gmax = std::max(1, std::min(std::min(nb, 16), gcap));
+    int g_lo = 1;
+    if (sat)
+        while (g_lo < gmax && (double)tiles * g_lo < 3.0 * slots) ++g_lo;
+    for (int G = g_lo; G <= gmax; ++G) {
+        auto r = build(G);
+        if (G == g_lo || r.first < best_cost) {
+            best_cost = r.first;
             groups = G;
-            plan.clear();
-            for (int k : order) plan.push_back(TcItem{P.index, k / G, k % G, G});
+            plan.swap(r.second);
+        }
+    }
+    if (sat && gmul != 1.0) {
+        const int G = std::max(1, std::min(gmax, (int)std::lround(groups * gmul)));
+        if (G != groups) {
+            groups = G;
+            plan = build(G).second;
         }
     }
     (sat ? P.sat_spans : P.tc_spans) = blend_spans(P, groups);
+}
+
+// Resident CTA slots of a summed-area kernel variant on the current device
+// (0: the persistent nine-plane kernel, 1: the three-group kernel).
+int sat_slots_of(int variant) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = variant == 1 ? synth_sat3_ctas_per_sm() : synth_sat_ctas_per_sm();
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+// Whether every bucket of the patch reaches at most the three-group kernel's
+// row table of bin rows per tile: rows = floor((Y1 + 2R - 1) / C) -
+// floor(Y0 / C) + 1 <= (63 Q + 2R - 1) / C + 2.
+bool sat3_fits(const PatchHost& P) {
+    const int cap = synth_sat3_row_cap();
+    for (const BucketDev& b : P.bk)
+        if ((63 * (int64_t)kQ + 2 * (int64_t)b.R - 1) / b.C + 2 > cap) return false;
+    return true;
 }
 
 // Plan of all patches in one launch: each patch's G is the smallest that
@@ -646,13 +686,15 @@ scwp_status synthesize(scwp_ctx* ctx, int mode) {
     if (mode == SCWP_SYNTH_SAT) {
         scwp_status s = sync_synth(ctx);
         if (s != SCWP_OK) return s;
+        auto launch = [&](const TcItem* it, int n, const BlendSpan* sp, int ns) {
+            return ctx->sat_variant == 1 ? launch_synth_sat3(it, n, ctx->d_pdevs, ctx->d_sps, sp, ns, ctx->st)
+                                         : launch_synth_sat(it, n, ctx->d_pdevs, ctx->d_sps, sp, ns, ctx->queue, ctx->st);
+        };
         if (ctx->batched) {
-            CU(launch_synth_sat(ctx->d_sitems, (int)ctx->s_items.size(), ctx->d_pdevs, ctx->d_sps, ctx->d_sspans,
-                                (int)ctx->s_spans.size(), ctx->queue, ctx->st));
+            CU(launch(ctx->d_sitems, (int)ctx->s_items.size(), ctx->d_sspans, (int)ctx->s_spans.size()));
         } else {
             for (PatchHost* P : ctx->patches)
-                CU(launch_synth_sat(P->d_sat_items, (int)P->sat_items.size(), ctx->d_pdevs, ctx->d_sps,
-                                    P->d_sat_spans, (int)P->sat_spans.size(), ctx->queue, ctx->st));
+                CU(launch(P->d_sat_items, (int)P->sat_items.size(), P->d_sat_spans, (int)P->sat_spans.size()));
         }
         return SCWP_OK;
     }
@@ -864,16 +906,29 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         ctx->slots = P->tc_slots;
         D.patch = P->index;
         plan_patch(*P, P->tc_slots);
-        const int sat_per_sm = synth_sat_ctas_per_sm();
-        P->sat_slots = sms * (sat_per_sm > 0 ? sat_per_sm : 1);
+        P->sat3_ok = sat3_fits(*P);
+        // partial planes for any plan the autotuner may choose: up to twice
+        // the groups either summed-area variant plans on its own
+        int gsat = 1;
+        for (int v = 0; v < 2; ++v) {
+            plan_patch(*P, sat_slots_of(v), true);
+            gsat = std::max(gsat, P->sat_groups);
+        }
+        const int nbmax = std::min(T.nb, 16);
+        const int gpart = std::min(nbmax, 2 * gsat);
+        const int variant = (ctx->sat_variant == 1 && P->sat3_ok) ? 1 : 0;
+        P->sat_slots = sat_slots_of(variant);
         ctx->sat_slots = P->sat_slots;
-        plan_patch(*P, P->sat_slots, true);
+        plan_patch(*P, P->sat_slots, true, ctx->sat_gmul, gpart);
         P->d_items = (TcItem*)dalloc(ctx, P->tc_items.size() * sizeof(TcItem));
         P->d_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, P->tc_spans.size()) * sizeof(BlendSpan));
-        P->d_sat_items = (TcItem*)dalloc(ctx, P->sat_items.size() * sizeof(TcItem));
-        P->d_sat_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, P->sat_spans.size()) * sizeof(BlendSpan));
+        int tiles_sat = 0;
+        tile_bucket_sat(*P, tiles_sat);
+        P->sat_item_cap = tiles_sat * gpart;
+        P->d_sat_items = (TcItem*)dalloc(ctx, (size_t)P->sat_item_cap * sizeof(TcItem));
+        P->d_sat_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, blend_spans(*P, 2).size()) * sizeof(BlendSpan));
         ok = ok && P->d_items && P->d_spans && P->d_sat_items && P->d_sat_spans;
-        const int G = std::max(std::max(D.groups, D.groups_tc), P->sat_groups);
+        const int G = std::max(std::max(D.groups, D.groups_tc), gpart);
         P->partial_planes = G;
         if (G > 1) {
             D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
@@ -1419,6 +1474,141 @@ scwp_status scwp_set_synth_mode(scwp_ctx* ctx, int32_t mode) {
     return SCWP_OK;
 }
 
+// Re-plan every patch's summed-area synthesis for the context's variant and
+// bucket-group multiplier (the autotuner's choices) and upload the plans;
+// the batched plan and the captured frames follow at the next synthesis.
+static scwp_status replan_sat(scwp_ctx* ctx) {
+    for (PatchHost* P : ctx->patches) {
+        const int variant = (ctx->sat_variant == 1 && P->sat3_ok) ? 1 : 0;
+        P->sat_slots = sat_slots_of(variant);
+        plan_patch(*P, P->sat_slots, true, ctx->sat_gmul, P->partial_planes);
+        if ((int)P->sat_items.size() > P->sat_item_cap) return fail(ctx, SCWP_E_STATE, "summed-area plan capacity");
+        CU(cudaMemcpyAsync(P->d_sat_items, P->sat_items.data(), P->sat_items.size() * sizeof(TcItem),
+                           cudaMemcpyHostToDevice, ctx->st));
+        if (!P->sat_spans.empty())
+            CU(cudaMemcpyAsync(P->d_sat_spans, P->sat_spans.data(), P->sat_spans.size() * sizeof(BlendSpan),
+                               cudaMemcpyHostToDevice, ctx->st));
+        ctx->sat_slots = P->sat_slots;
+    }
+    CU(cudaStreamSynchronize(ctx->st));
+    graph_reset(ctx);
+    ctx->synth_dirty = true;
+    return SCWP_OK;
+}
+
+namespace {
+// Choices of the autotuner per device and workload signature (process-wide).
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, double>> g_tune_cache;
+
+// the workload signature the autotuner's choice is cached under: device,
+// batching, and every patch's size, buckets, prefill, capacity and bin size
+std::string tune_signature(const scwp_ctx* ctx) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string s = "dev" + std::to_string(dev) + (ctx->batched ? "/b" : "/p");
+    for (const PatchHost* P : ctx->patches) {
+        s += "/" + std::to_string(P->T.W) + "x" + std::to_string(P->T.H) + ":" + std::to_string(P->T.nb) + ":" +
+             std::to_string(P->d.prefill) + ":" + std::to_string(P->dev.cap) + ":" +
+             std::to_string(P->bin_cells.empty() ? 0 : P->bin_cells[0]);
+    }
+    return s;
+}
+}  // namespace
+
+scwp_status scwp_set_sat_plan(scwp_ctx* ctx, int32_t variant, double gmul) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if ((variant != 0 && variant != 1) || !(gmul >= 0.125 && gmul <= 8.0)) return fail(ctx, SCWP_E_INVALID, "plan");
+    if (variant == 1)
+        for (const PatchHost* P : ctx->patches)
+            if (!P->sat3_ok) return fail(ctx, SCWP_E_INVALID, "a patch's buckets exceed the three-group row table");
+    ctx->sat_variant = variant;
+    ctx->sat_gmul = gmul;
+    return replan_sat(ctx);
+}
+
+scwp_status scwp_autotune(scwp_ctx* ctx, int32_t reps, int32_t force, scwp_tune_result* out) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (!out || reps < 1 || reps > 100) return fail(ctx, SCWP_E_INVALID, "autotune arguments");
+    if (ctx->synth_mode != SCWP_SYNTH_SAT) return fail(ctx, SCWP_E_STATE, "the autotuner tunes the summed-area synthesis");
+    if (ctx->frame < 1 || ctx->patches.empty()) return fail(ctx, SCWP_E_STATE, "autotune needs a stepped frame");
+    memset(out, 0, sizeof(*out));
+    const long long before = launches_total();
+    const std::string key = tune_signature(ctx);
+    bool all3 = true;
+    for (const PatchHost* P : ctx->patches) all3 = all3 && P->sat3_ok;
+    if (!force) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            ctx->sat_variant = it->second.first;
+            ctx->sat_gmul = it->second.second;
+            out->n_configs = 1;
+            out->chosen = 0;
+            out->variant[0] = ctx->sat_variant;
+            out->gmul[0] = ctx->sat_gmul;
+            out->ms[0] = -1.0;
+            out->from_cache = 1;
+            return replan_sat(ctx);
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return fail(ctx, SCWP_E_CUDA, "autotune events");
+    }
+    const double gmuls[3] = {1.0, 0.5, 2.0};
+    int n = 0;
+    for (int v = 0; v < 2 && s == SCWP_OK; ++v) {
+        if (v == 1 && !all3) continue;
+        for (double gm : gmuls) {
+            if (n >= SCWP_TUNE_MAX) break;
+            ctx->sat_variant = v;
+            ctx->sat_gmul = gm;
+            if ((s = replan_sat(ctx)) != SCWP_OK || (s = sync_synth(ctx)) != SCWP_OK) break;
+            if ((s = synthesize(ctx, SCWP_SYNTH_SAT)) != SCWP_OK) break;   // warm-up
+            std::vector<float> ms;
+            for (int r = 0; r < reps && s == SCWP_OK; ++r) {
+                float t = 0.f;
+                if (cudaEventRecord(e0, ctx->st) != cudaSuccess) { s = fail(ctx, SCWP_E_CUDA, "autotune"); break; }
+                if ((s = synthesize(ctx, SCWP_SYNTH_SAT)) != SCWP_OK) break;
+                if (cudaEventRecord(e1, ctx->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                    s = fail(ctx, SCWP_E_CUDA, "autotune timing");
+                    break;
+                }
+                ms.push_back(t);
+            }
+            if (s != SCWP_OK) break;
+            std::sort(ms.begin(), ms.end());
+            out->variant[n] = v;
+            out->gmul[n] = gm;
+            out->ms[n] = ms[ms.size() / 2];
+            if (out->ms[n] < out->ms[out->chosen]) out->chosen = n;
+            ++n;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out->n_configs = n;
+    if (s != SCWP_OK) return s;
+    ctx->sat_variant = out->variant[out->chosen];
+    ctx->sat_gmul = out->gmul[out->chosen];
+    if ((s = replan_sat(ctx)) != SCWP_OK || (s = sync_synth(ctx)) != SCWP_OK) return s;
+    // the maps of the last frame, synthesised with the chosen plan
+    if ((s = synthesize(ctx, SCWP_SYNTH_SAT)) != SCWP_OK) return s;
+    CU(cudaStreamSynchronize(ctx->st));
+    ctx->launches += launches_total() - before;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = std::make_pair(ctx->sat_variant, ctx->sat_gmul);
+    }
+    return SCWP_OK;
+}
+
 scwp_status scwp_height_map(scwp_ctx* ctx, int32_t patch_id, int32_t field, float* dst, size_t dst_elems,
                             int32_t dst_on_device) {
     scwp_status s = ready(ctx);
@@ -1545,6 +1735,7 @@ scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info
     out->sat_groups = P->sat_groups;
     out->sat_items = (int32_t)P->sat_items.size();
     out->sat_slots = P->sat_slots;
+    out->sat_variant = (ctx->sat_variant == 1 && P->sat3_ok) ? 1 : 0;
     out->frame_param_bytes = (int32_t)sizeof(InjectParams);
     for (int i = 0; i < P->T.nb; ++i) {
         out->bin_cells[i] = P->bin_cells[i];

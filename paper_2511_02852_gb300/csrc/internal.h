@@ -195,6 +195,13 @@ cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* p
                              const BlendSpan* spans, int n_spans, unsigned int* queue, cudaStream_t st);
 int synth_sat_tile();
 int synth_sat_ctas_per_sm();
+// The three-group variant of the same synthesis (two 512-thread CTAs per SM,
+// one CTA per item): faster where per-texel work dominates; every bucket of
+// its patches must reach at most synth_sat3_row_cap() bin rows per tile.
+cudaError_t launch_synth_sat3(const TcItem* items, int n_items, const PatchDev* pdevs, const SynthParams* sps,
+                              const BlendSpan* spans, int n_spans, cudaStream_t st);
+int synth_sat3_ctas_per_sm();
+int synth_sat3_row_cap();
 // tensor-core synthesis geometry: tile side (texels), bumps per operand stage,
 // and resident CTAs per SM (0 on error)
 int synth_tc_tile();

@@ -76,7 +76,16 @@ class scwp_patch_info(C.Structure):
                 ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS),
                 ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32),
                 ("sat_groups", C.c_int32), ("sat_items", C.c_int32), ("sat_slots", C.c_int32),
-                ("frame_param_bytes", C.c_int32)]
+                ("frame_param_bytes", C.c_int32), ("sat_variant", C.c_int32)]
+
+
+TUNE_MAX = 8
+
+
+class scwp_tune_result(C.Structure):
+    _fields_ = [("n_configs", C.c_int32), ("chosen", C.c_int32), ("from_cache", C.c_int32),
+                ("pad", C.c_int32), ("variant", C.c_int32 * TUNE_MAX), ("gmul", C.c_double * TUNE_MAX),
+                ("ms", C.c_double * TUNE_MAX)]
 
 
 class scwp_server_desc(C.Structure):
@@ -111,6 +120,8 @@ EXPORTS = {
     "scwp_resynthesize": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_synth_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_batched": (C.c_int, [C.c_void_p, C.c_int32]),
+    "scwp_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(scwp_tune_result)]),
+    "scwp_set_sat_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
     "scwp_set_bucket_range": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "scwp_normal_map": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]),
     "scwp_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -388,6 +399,19 @@ class Scene:
 
     def set_synth_mode(self, mode):
         _check(lib().scwp_set_synth_mode(self.ctx, mode), self.ctx)
+
+    def set_sat_plan(self, variant, gmul=1.0):
+        _check(lib().scwp_set_sat_plan(self.ctx, int(variant), float(gmul)), self.ctx)
+
+    def autotune(self, reps=3, force=False):
+        """scwp_autotune: time the summed-area variants and bucket-group
+        multipliers on the last frame and keep the fastest; returns the
+        table [(variant, gmul, ms)], the chosen index and whether the choice
+        came from the per-device cache."""
+        r = scwp_tune_result()
+        _check(lib().scwp_autotune(self.ctx, int(reps), 1 if force else 0, C.byref(r)), self.ctx)
+        rows = [(int(r.variant[k]), float(r.gmul[k]), float(r.ms[k])) for k in range(r.n_configs)]
+        return rows, int(r.chosen), bool(r.from_cache)
 
     def set_batched(self, on):
         _check(lib().scwp_set_batched(self.ctx, 1 if on else 0), self.ctx)

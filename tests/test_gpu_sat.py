@@ -224,3 +224,56 @@ def test_sat_bucket_rows_beyond_the_row_table():
     compare_maps(sc.maps(0), ref, orc.spec.Hs(), "sat rows beyond the table")
     assert sc.stats(0).error_flags == 0
     sc.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("gmul", [0.5, 1.0, 2.0])
+def test_sat_variants_and_group_plans_match_oracle(variant, gmul):
+    """Both summed-area kernels (0: persistent nine-plane, 1: three-group)
+    under each bucket-group multiplier the autotuner searches, in batched
+    mode on the five-patch scene: maps within the contract of the oracle."""
+    cfg = wl.small_batch()
+    sc = sat_scene(cfg, batched=True)
+    orc = OracleScene(cfg)
+    for _ in range(2):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+    sc.set_sat_plan(variant, gmul)
+    sc.step(cfg["dt"])
+    orc.step(cfg["dt"])
+    bg = orc.background()
+    for p in range(len(cfg["patches"])):
+        assert sc.info(p).sat_variant == variant
+        ref, ev = orc.patch_maps(p, bg)
+        assert sc.stats(p).eval_count == ev
+        compare_maps(sc.maps(p), ref, orc.spec.Hs(), f"sat variant {variant} gmul {gmul} patch {p}")
+    sc.close()
+
+
+def test_autotune_chooses_caches_and_keeps_parity():
+    """scwp_autotune times the variants and multipliers, keeps one, and a
+    second context with the same workload signature takes the cached choice
+    without timing; the maps stay within the contract of the oracle."""
+    from paper_2511_02852_gb300 import scwp
+    cfg = wl.small_batch()
+    a = sat_scene(cfg, batched=True)
+    orc = OracleScene(cfg)
+    a.step(cfg["dt"])
+    orc.step(cfg["dt"])
+    rows, chosen, cached = a.autotune(reps=2, force=True)
+    assert not cached and len(rows) == 6 and 0 <= chosen < len(rows)
+    assert rows[chosen][2] == min(r[2] for r in rows)
+    print("[autotune] small_batch: " + ", ".join(f"v{v} x{g:g}: {m:.4f} ms" for v, g, m in rows))
+    a.step(cfg["dt"])
+    orc.step(cfg["dt"])
+    bg = orc.background()
+    for p in range(len(cfg["patches"])):
+        assert a.info(p).sat_variant == rows[chosen][0]
+        ref, _ = orc.patch_maps(p, bg)
+        compare_maps(a.maps(p), ref, orc.spec.Hs(), f"tuned patch {p}")
+    b = sat_scene(cfg, batched=True)
+    b.step(cfg["dt"])
+    rows_b, _, cached_b = b.autotune(reps=2)
+    assert cached_b and rows_b[0][:2] == rows[chosen][:2]
+    a.close()
+    b.close()
