@@ -371,13 +371,16 @@ scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_de
  * update of scwp_step (spectrum evolution + inverse 2-D FFT).
  *   h0     device, float32 complex interleaved [n][n] (FFT-natural order),
  *          8-byte aligned
- *   omega  device, float64 [n][n] dispersion w(k), 8-byte aligned
+ *   omega  device, float32 [n][n][2] dispersion w(k) as a float pair
+ *          (hi, lo) with w = hi + lo (hi = (float)w, lo = (float)(w - hi)),
+ *          8-byte aligned
  *   n      grid size: power of two, 8 <= n <= 512; larger grids are refused
  *          with SCWP_E_INVALID (the scratch is sized for 512 x 512)
  *   out    device, float32 [3][n][n]: h, Dx, Dy at x_j = j fft_L / n,
  *          4-byte aligned
  *   stream cudaStream_t (NULL: the legacy stream); asynchronous
- * The scratch (4 MiB + 4 KiB) is one static __device__ array of the library:
+ * The scratch (3 x 257 x 512 + 512 complex floats, about 3.0 MiB) is one
+ * static __device__ array of the library:
  * every GPU that loads the library holds it until the process exits, and
  * every call shares it, so calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  The first call
@@ -386,7 +389,7 @@ scwp_status scwp_host_table(const scwp_spectrum_desc* sdesc, const scwp_patch_de
  * call before any stream capture.  Returns SCWP_E_INVALID on bad arguments
  * (a null or misaligned pointer, a grid size out of range; nothing is
  * launched), SCWP_E_CUDA if the set-up or a launch fails. */
-scwp_status scwp_background_noalloc(const float* h0, const double* omega, int32_t n, double fft_L,
+scwp_status scwp_background_noalloc(const float* h0, const float* omega, int32_t n, double fft_L,
                                     double choppiness, double t, float* out, void* stream);
 
 /* Number of kernels this context has enqueued since creation (every

@@ -107,9 +107,9 @@ struct scwp_ctx {
     SpectrumModel sm;
     BgDev bg;
     float2* h0 = nullptr;
-    double* omega = nullptr;
+    float2* omega = nullptr;          // w(k) as float pairs (hi, lo)
     float2* tw = nullptr;
-    float2* G = nullptr;
+    float2* I = nullptr;              // row-pass intermediate of the background
     float* bgout = nullptr;
     int64_t frame = 0;
     double t = 0.0;
@@ -781,14 +781,20 @@ scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
     }
     const size_t NN = (size_t)N * N;
     ctx->h0 = (float2*)dalloc(ctx, NN * sizeof(float2));
-    ctx->omega = (double*)dalloc(ctx, NN * sizeof(double));
+    ctx->omega = (float2*)dalloc(ctx, NN * sizeof(float2));
     ctx->tw = (float2*)dalloc(ctx, N * sizeof(float2));
-    ctx->G = (float2*)dalloc(ctx, 2 * NN * sizeof(float2));
+    ctx->I = (float2*)dalloc(ctx, background_scratch_elems(N) * sizeof(float2));
     ctx->bgout = (float*)dalloc(ctx, 3 * NN * sizeof(float));
     ctx->queue = (unsigned int*)dalloc(ctx, 2 * sizeof(unsigned int));
-    if (!ctx->h0 || !ctx->omega || !ctx->tw || !ctx->G || !ctx->bgout || !ctx->queue) return bail(SCWP_E_NOMEM);
+    if (!ctx->h0 || !ctx->omega || !ctx->tw || !ctx->I || !ctx->bgout || !ctx->queue) return bail(SCWP_E_NOMEM);
+    // w(k) split into float pairs on the host: hi = (float)w, lo = (float)(w - hi)
+    std::vector<float2> omhl(NN);
+    for (size_t k = 0; k < NN; ++k) {
+        const float hi = (float)om[k];
+        omhl[k] = make_float2(hi, (float)(om[k] - (double)hi));
+    }
     if (cudaMemcpy(ctx->h0, h0.data(), NN * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(ctx->omega, om.data(), NN * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->omega, omhl.data(), NN * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ctx->bgout, 0, 3 * NN * sizeof(float)) != cudaSuccess ||
         cudaMemset(ctx->queue, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
@@ -799,7 +805,7 @@ scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
     ctx->bg.h0 = ctx->h0;
     ctx->bg.omega = ctx->omega;
     ctx->bg.tw = ctx->tw;
-    ctx->bg.G = ctx->G;
+    ctx->bg.I = ctx->I;
     ctx->bg.out = ctx->bgout;
     ctx->bg.lam = (float)desc->choppiness;
     ctx->bg.dk = (float)(2.0 * M_PI / desc->fft_L);
@@ -1209,7 +1215,7 @@ scwp_status scwp_step(scwp_ctx* ctx, double dt) {
 // them by value); ip_dev / t_dev: their device copies (captured frames read
 // the frame's parameters from device memory).
 static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>& ips, const InjectParams* ip_dev,
-                          const double* t_dev, FrameEvents* fe) {
+                          const float2* t_dev, FrameEvents* fe) {
     scwp_status s = SCWP_OK;
     // background on the side stream, concurrent with the particle stages
     CU(cudaEventRecord(ctx->ev_fork, ctx->st));
@@ -1258,7 +1264,7 @@ static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>&
 // context stream (the server's ticks).  ips / ip_dev / t_dev as in
 // enqueue_frame.
 static scwp_status enqueue_prepare(scwp_ctx* ctx, const std::vector<InjectParams>& ips, const InjectParams* ip_dev,
-                                   const double* t_dev) {
+                                   const float2* t_dev) {
     scwp_status s = SCWP_OK;
     CU(launch_background(ctx->bg, ctx->t, ctx->st, t_dev));
     ctx->bg_valid = true;
@@ -1312,7 +1318,12 @@ static scwp_status run_graph(scwp_ctx* ctx, FrameGraph& G, const std::vector<Inj
     }
     if (G.pending[g]) CU(cudaEventSynchronize(G.done[g]));
     unsigned char* h = (unsigned char*)G.hstage[g];
-    memcpy(h, &ctx->t, sizeof(double));
+    {
+        // the frame's time as a float pair (t_hi, t_lo), split here in float64
+        const float th = (float)ctx->t;
+        const float2 tt = make_float2(th, (float)(ctx->t - (double)th));
+        memcpy(h, &tt, sizeof(tt));
+    }
     memcpy(h + 16, ips.data(), ips.size() * sizeof(InjectParams));
     if (!G.valid[g]) {
         // everything that synchronises or allocates happens before the capture
@@ -1334,7 +1345,7 @@ static scwp_status run_graph(scwp_ctx* ctx, FrameGraph& G, const std::vector<Inj
         if (e == cudaSuccess) {
             e = cudaMemcpyAsync(G.dparams, h, bytes, cudaMemcpyHostToDevice, ctx->st);
             const InjectParams* ipd = reinterpret_cast<const InjectParams*>(G.dparams + 16);
-            const double* td = reinterpret_cast<const double*>(G.dparams);
+            const float2* td = reinterpret_cast<const float2*>(G.dparams);
             if (e == cudaSuccess)
                 s = full ? enqueue_frame(ctx, ips, ipd, td, nullptr) : enqueue_prepare(ctx, ips, ipd, td);
             e2 = cudaStreamEndCapture(ctx->st, &graph);

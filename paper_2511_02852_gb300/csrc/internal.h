@@ -223,14 +223,17 @@ cudaError_t launch_layered(const PatchDev& p, const SynthParams& sp, const int32
 
 struct BgDev {
     int N = 0;
-    const float2* h0 = nullptr;   // [N][N]
-    const double* omega = nullptr;// [N][N]
+    const float2* h0 = nullptr;   // [N][N] FFT-natural order
+    const float2* omega = nullptr;// [N][N] w(k) as a float pair (hi, lo), w = hi + lo
     const float2* tw = nullptr;   // [N] e^{2 pi i m / N}
-    float2* G = nullptr;          // [2][N][N] row-pass output
+    float2* I = nullptr;          // [3][N/2 + 1][N] row-pass output (H1, Dx1, Dy1 of rows k_y <= N/2)
     float* out = nullptr;         // [3][N][N] h, Dx, Dy
     float lam = 1.f, dk = 0.f;
 };
-// t_dev: if not null, the time is read from device memory (graph replay)
-cudaError_t launch_background(const BgDev& b, double t, cudaStream_t st, const double* t_dev = nullptr);
+// t_dev: if not null, the time is read from device memory (graph replay) as
+// a float pair (t_hi, t_lo), t = t_hi + t_lo, split on the host
+cudaError_t launch_background(const BgDev& b, double t, cudaStream_t st, const float2* t_dev = nullptr);
+// complex elements of the row-pass intermediate of an N x N background
+size_t background_scratch_elems(int N);
 
 }  // namespace scwp

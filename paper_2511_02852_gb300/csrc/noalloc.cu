@@ -9,7 +9,8 @@
 // already hold in device memory.  Its scratch (the row-pass intermediate and
 // the twiddle table) lives in one file-scope __device__ array below, sized
 // for grids up to kNoAllocMaxN x kNoAllocMaxN; every GPU that loads this
-// library holds that array (4 MiB + 4 KiB) until the process exits.
+// library holds that array (3 x 257 x 512 + 512 complex floats, about
+// 3.0 MiB) until the process exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,10 +23,11 @@
 namespace {
 
 constexpr int kNoAllocMaxN = 512;
-constexpr size_t kScratchElems = 2 * (size_t)kNoAllocMaxN * kNoAllocMaxN + kNoAllocMaxN;
+constexpr size_t kInterElems = 3 * (size_t)(kNoAllocMaxN / 2 + 1) * kNoAllocMaxN;
+constexpr size_t kScratchElems = kInterElems + kNoAllocMaxN;
 
-// [0, 2 N^2): row-pass output of the two transformed planes;
-// [2 N^2, 2 N^2 + N): e^{2 pi i m / N} for N = kNoAllocMaxN.
+// [0, kInterElems): row-pass output (H1, Dx1, Dy1 of the rows k_y <= N/2);
+// [kInterElems, kInterElems + N): e^{2 pi i m / N} for N = kNoAllocMaxN.
 static __device__ __align__(256) float2 g_noalloc_scratch[kScratchElems];
 
 constexpr int kMaxDevices = 64;
@@ -50,8 +52,7 @@ cudaError_t setup_device(int dev, float2** out) {
         const double a = 2.0 * M_PI * m / kNoAllocMaxN;
         tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
-    e = cudaMemcpy(ptr + 2 * (size_t)kNoAllocMaxN * kNoAllocMaxN, tw,
-                   kNoAllocMaxN * sizeof(float2), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(ptr + kInterElems, tw, kNoAllocMaxN * sizeof(float2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = ptr;
     *out = ptr;
@@ -66,7 +67,7 @@ __global__ void k_gather_twiddles(const float2* full, float2* dst, int n, int st
 
 }  // namespace
 
-extern "C" scwp_status scwp_background_noalloc(const float* h0, const double* omega, int32_t n,
+extern "C" scwp_status scwp_background_noalloc(const float* h0, const float* omega, int32_t n,
                                                double fft_L, double choppiness, double t, float* out,
                                                void* stream) {
     if (!h0 || !omega || !out || !(fft_L > 0)) return SCWP_E_INVALID;
@@ -85,13 +86,12 @@ extern "C" scwp_status scwp_background_noalloc(const float* h0, const double* om
         return SCWP_E_CUDA;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t nn = (size_t)kNoAllocMaxN * kNoAllocMaxN;
-    const float2* full_tw = scratch + 2 * nn;
-    // the row-pass buffer holds 2 n^2 values; for n < N_max its tail keeps
-    // this grid's twiddles (written before, read by, the FFT of this call)
+    const float2* full_tw = scratch + kInterElems;
+    // the row-pass buffer holds 3 (n/2 + 1) n values; for n < N_max its tail
+    // keeps this grid's twiddles (written before, read by, the FFT of this call)
     const float2* tw = full_tw;
     if (n < kNoAllocMaxN) {
-        float2* small = scratch + 2 * (size_t)n * n;
+        float2* small = scratch + scwp::background_scratch_elems(n);
         k_gather_twiddles<<<1, 256, 0, st>>>(full_tw, small, n, kNoAllocMaxN / n);
         scwp::count_launches(1);
         tw = small;
@@ -99,9 +99,9 @@ extern "C" scwp_status scwp_background_noalloc(const float* h0, const double* om
     scwp::BgDev bg;
     bg.N = n;
     bg.h0 = reinterpret_cast<const float2*>(h0);
-    bg.omega = omega;
+    bg.omega = reinterpret_cast<const float2*>(omega);
     bg.tw = tw;
-    bg.G = scratch;
+    bg.I = scratch;
     bg.out = out;
     bg.lam = (float)choppiness;
     bg.dk = (float)(2.0 * M_PI / fft_L);

@@ -40,7 +40,10 @@ def _inputs(cfg):
     omega = spec.omega_of_k(np.hypot(kx, ky))
     h0_t = torch.from_numpy(np.ascontiguousarray(
         np.stack([h0.real, h0.imag], -1).astype(np.float32))).cuda()
-    om_t = torch.from_numpy(np.ascontiguousarray(omega, dtype=np.float64)).cuda()
+    # w(k) as float pairs (hi, lo), w = hi + lo, split in float64 on the host
+    hi = omega.astype(np.float32)
+    lo = (omega - hi.astype(np.float64)).astype(np.float32)
+    om_t = torch.from_numpy(np.ascontiguousarray(np.stack([hi, lo], -1))).cuda()
     return spec, h0_t, om_t
 
 
@@ -93,7 +96,7 @@ def test_noalloc_background_refuses_bad_sizes_and_misaligned_pointers():
     from paper_2511_02852_gb300 import scwp
     L = scwp.lib()
     buf = torch.zeros(16, dtype=torch.float32, device="cuda")
-    om = torch.zeros(16, dtype=torch.float64, device="cuda")
+    om = torch.zeros(32, dtype=torch.float32, device="cuda")
     for n in (1024, 300, 4):
         rc = L.scwp_background_noalloc(_ptr(buf), _ptr(om), n, 100.0, 1.0, 0.0, _ptr(buf), None)
         assert rc == 1      # SCWP_E_INVALID, nothing launched
