@@ -352,7 +352,10 @@ scwp_status scwp_set_sat_plan(scwp_ctx* ctx, int32_t variant, double gmul);
  * disable (0).  scwp_timing_read sums, over the frames stepped since the
  * last read, the device time of [0] background FFT, [1] particle stages
  * (advect .. bin), [2] synthesis + blend, [3] whole frame, in ms, and the
- * number of frames; it synchronises and resets the sums. */
+ * number of frames; it synchronises and resets the sums.  With timing on,
+ * frames launch one stage at a time and the background runs alone on the
+ * context stream before the particle stages (instead of beside them on a
+ * second stream), so that each sum times its stage by itself. */
 scwp_status scwp_set_timing(scwp_ctx* ctx, int32_t enable);
 scwp_status scwp_timing_read(scwp_ctx* ctx, double ms_sum[4], int64_t* frames);
 

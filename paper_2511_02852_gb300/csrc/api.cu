@@ -1217,13 +1217,16 @@ scwp_status scwp_step(scwp_ctx* ctx, double dt) {
 static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>& ips, const InjectParams* ip_dev,
                           const float2* t_dev, FrameEvents* fe) {
     scwp_status s = SCWP_OK;
-    // background on the side stream, concurrent with the particle stages
+    // background on the side stream, concurrent with the particle stages;
+    // with stage timing on, alone on the context stream ahead of them, so
+    // that each stage's events time that stage by itself
     CU(cudaEventRecord(ctx->ev_fork, ctx->st));
-    CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-    if (fe && (s = record(ctx, fe->e[4], ctx->side)) != SCWP_OK) return s;
-    CU(launch_background(ctx->bg, ctx->t, ctx->side, t_dev));
-    if (fe && (s = record(ctx, fe->e[5], ctx->side)) != SCWP_OK) return s;
-    CU(cudaEventRecord(ctx->ev_join, ctx->side));
+    cudaStream_t bgs = fe ? ctx->st : ctx->side;
+    if (!fe) CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    if (fe && (s = record(ctx, fe->e[4], bgs)) != SCWP_OK) return s;
+    CU(launch_background(ctx->bg, ctx->t, bgs, t_dev));
+    if (fe && (s = record(ctx, fe->e[5], bgs)) != SCWP_OK) return s;
+    CU(cudaEventRecord(ctx->ev_join, bgs));
     ctx->bg_valid = true;
 
     // one patch: the context stream; several: up to kParticleStreams

@@ -53,6 +53,11 @@ template <int N>
 __host__ __device__ constexpr int threads_per_transform() { return N >= 16 ? N / 16 : 1; }
 template <int N>
 __host__ __device__ constexpr int padded() { return N + N / 16; }
+// stride of one transform in shared memory: the padded length, rounded to
+// 2 mod 16 complex values so that consecutive transforms start 4 banks apart
+// (the column pass's loads and stores walk across transforms)
+template <int N>
+__host__ __device__ constexpr int tstride() { return padded<N>() + ((18 - padded<N>() % 16) % 16); }
 // columns per column-pass CTA for h + i Dx (twice as many for Dy, in pairs)
 template <int N>
 __host__ __device__ constexpr int col_group() { return N >= 4096 ? 4 : N >= 1024 ? 8 : N >= 32 ? 16 : N / 2; }
@@ -175,9 +180,10 @@ __device__ __forceinline__ float phase(float2 w, float th, float tl) {
 // f = tid / P.  h0 is [N][N] (FFT-natural order), omega [N][N] float pairs
 // (hi, lo); I is [3][N/2 + 1][N].
 template <int N>
-__global__ void __launch_bounds__(3 * threads_per_transform<N>()) k_spectrum_rows(BgDev bg, float th, float tl,
-                                                                                 const float2* t_dev) {
-    constexpr int P = threads_per_transform<N>(), Np = padded<N>();
+__global__ void __launch_bounds__(3 * threads_per_transform<N>(), N >= 1024 ? 3 : 1)
+    k_spectrum_rows(BgDev bg, float th, float tl, const float2* t_dev) {
+    constexpr int P = threads_per_transform<N>(), Np = tstride<N>();
+    constexpr int NT = 3 * P, E = (N + NT - 1) / NT;   // grid points per thread
     extern __shared__ float2 smem_rows[];
     float2 (*buf)[Np] = reinterpret_cast<float2 (*)[Np]>(smem_rows);   // [3][Np]
     pdl_enter();
@@ -190,12 +196,25 @@ __global__ void __launch_bounds__(3 * threads_per_transform<N>()) k_spectrum_row
     const int mym = (N - my) & (N - 1);
     const int ny = my < N / 2 ? my : my - N;
     const float ky = bg.dk * (float)ny;
-    for (int mx = threadIdx.x; mx < N; mx += 3 * P) {
-        const int mxm = (N - mx) & (N - 1);
+    // every load of the thread's grid points first
+    float2 av[E], bv[E], wv[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int mx = threadIdx.x + i * NT;
+        if (mx < N) {
+            av[i] = bg.h0[(size_t)my * N + mx];
+            bv[i] = bg.h0[(size_t)mym * N + ((N - mx) & (N - 1))];
+            wv[i] = bg.omega[(size_t)my * N + mx];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int mx = threadIdx.x + i * NT;
+        if (mx >= N) continue;
         const int nx = mx < N / 2 ? mx : mx - N;
-        const float2 a = bg.h0[(size_t)my * N + mx], b = bg.h0[(size_t)mym * N + mxm];
+        const float2 a = av[i], b = bv[i];
         float s, c;
-        sincosf(phase(bg.omega[(size_t)my * N + mx], th, tl), &s, &c);
+        sincosf(phase(wv[i], th, tl), &s, &c);
         // h~ = h0(k) e^{i w t} + conj(h0(-k) e^{i w t})
         const float2 q = make_float2(b.x * c - b.y * s, b.x * s + b.y * c);
         const float2 ht = make_float2(a.x * c - a.y * s + q.x, a.x * s + a.y * c - q.y);
@@ -228,7 +247,7 @@ __global__ void __launch_bounds__(3 * threads_per_transform<N>()) k_spectrum_row
 // the rows N - k_y.  out is [3][N][N] (h, Dx, Dy), row-major.
 template <int N>
 __global__ void __launch_bounds__(col_group<N>() * threads_per_transform<N>()) k_fft_cols(BgDev bg) {
-    constexpr int P = threads_per_transform<N>(), Np = padded<N>(), CZ = col_group<N>();
+    constexpr int P = threads_per_transform<N>(), Np = tstride<N>(), CZ = col_group<N>();
     constexpr int NT = CZ * P;
     extern __shared__ float2 smem_cols[];
     float2 (*buf)[Np] = reinterpret_cast<float2 (*)[Np]>(smem_cols);   // [CZ][Np]
@@ -236,21 +255,33 @@ __global__ void __launch_bounds__(col_group<N>() * threads_per_transform<N>()) k
     const size_t rows = (size_t)(N / 2 + 1) * N;
     const bool dy = (int)blockIdx.x >= N / CZ;
     const int x0 = dy ? ((int)blockIdx.x - N / CZ) * 2 * CZ : (int)blockIdx.x * CZ;
-    // load: element (k_y, c) with c fastest (CZ consecutive columns of a row)
-    for (int w = threadIdx.x; w < (N / 2 + 1) * CZ; w += NT) {
-        const int m = w / CZ, c = w - m * CZ;
-        float2 v, vm;   // rows m and N - m of the transform
-        if (!dy) {
-            const float2 h = bg.I[(size_t)m * N + x0 + c], d = bg.I[rows + (size_t)m * N + x0 + c];
-            v = make_float2(h.x - d.y, h.y + d.x);    // H1 + i Dx1
-            vm = make_float2(h.x + d.y, d.x - h.y);   // conj(H1) + i conj(Dx1)
-        } else {
-            const float4 pr = *reinterpret_cast<const float4*>(&bg.I[2 * rows + (size_t)m * N + x0 + 2 * c]);
-            v = make_float2(pr.x - pr.w, pr.y + pr.z);    // Dy1(x) + i Dy1(x + 1)
-            vm = make_float2(pr.x + pr.w, pr.z - pr.y);   // conjugates
+    // load: element (k_y, c) with c fastest (CZ consecutive columns of a
+    // row), every load of the thread issued before the first store
+    constexpr int E = ((N / 2 + 1) * CZ + NT - 1) / NT;
+    float4 ld[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int w = threadIdx.x + i * NT;
+        if (w < (N / 2 + 1) * CZ) {
+            const int m = w / CZ, c = w - m * CZ;
+            if (!dy) {
+                const float2 h = bg.I[(size_t)m * N + x0 + c], d = bg.I[rows + (size_t)m * N + x0 + c];
+                ld[i] = make_float4(h.x, h.y, d.x, d.y);
+            } else {
+                ld[i] = *reinterpret_cast<const float4*>(&bg.I[2 * rows + (size_t)m * N + x0 + 2 * c]);
+            }
         }
-        buf[c][pad(m)] = v;
-        if (m > 0 && m < N / 2) buf[c][pad(N - m)] = vm;
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int w = threadIdx.x + i * NT;
+        if (w >= (N / 2 + 1) * CZ) continue;
+        const int m = w / CZ, c = w - m * CZ;
+        // (p, q) = (H1, Dx1) or (Dy1(x), Dy1(x + 1)): the transform's rows m
+        // and N - m are p + i q and conj(p) + i conj(q)
+        const float4 pq = ld[i];
+        buf[c][pad(m)] = make_float2(pq.x - pq.w, pq.y + pq.z);
+        if (m > 0 && m < N / 2) buf[c][pad(N - m)] = make_float2(pq.x + pq.w, pq.z - pq.y);
     }
     __syncthreads();
     const int t = threadIdx.x / P, jt = threadIdx.x % P;
@@ -275,7 +306,7 @@ __global__ void __launch_bounds__(col_group<N>() * threads_per_transform<N>()) k
 template <int N>
 cudaError_t launch_n(const BgDev& bg, float th, float tl, cudaStream_t st, const float2* t_dev) {
     constexpr int P = threads_per_transform<N>(), CZ = col_group<N>();
-    constexpr size_t smr = sizeof(float2) * 3 * padded<N>(), smc = sizeof(float2) * CZ * padded<N>();
+    constexpr size_t smr = sizeof(float2) * 3 * tstride<N>(), smc = sizeof(float2) * CZ * tstride<N>();
     static_assert(smc <= 227 * 1024 && smr <= 227 * 1024, "shared memory of one CTA");
     cudaError_t e = cudaFuncSetAttribute(k_spectrum_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
     if (e == cudaSuccess)
