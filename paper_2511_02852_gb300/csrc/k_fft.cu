@@ -60,7 +60,7 @@ template <int N>
 __host__ __device__ constexpr int tstride() { return padded<N>() + ((18 - padded<N>() % 16) % 16); }
 // columns per column-pass CTA for h + i Dx (twice as many for Dy, in pairs)
 template <int N>
-__host__ __device__ constexpr int col_group() { return N >= 4096 ? 4 : N >= 1024 ? 8 : N >= 32 ? 16 : N / 2; }
+__host__ __device__ constexpr int col_group() { return N >= 2048 ? 4 : N >= 1024 ? 8 : N >= 32 ? 16 : N / 2; }
 // the radix of the last stage: N = 16^a r, r in {1, 2, 4, 8}
 template <int N>
 __host__ __device__ constexpr int last_radix() { return N < 16 ? N : last_radix<N / 16>(); }
