@@ -170,6 +170,19 @@ inline cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_
 }
 long long launches_total();
 
+// A kernel's launch set-up (attributes, occupancy) done once per device:
+// slot d of a function-local cache holds the result for device d, set on
+// the first call with that device current.  Later calls skip the driver
+// queries that would otherwise stall every eager launch on the host.
+constexpr int kMaxCachedDevices = 64;
+template <typename F>
+inline int cached_per_device(int (&cache)[kMaxCachedDevices], F&& compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxCachedDevices) return compute();
+    if (cache[dev] == 0) cache[dev] = compute();
+    return cache[dev];
+}
+
 // ---- launchers (each enqueues on `st`) --------------------------------------
 cudaError_t launch_advect_flag(const PatchDev& p, cudaStream_t st);
 cudaError_t launch_compact(const PatchDev& p, cudaStream_t st);

@@ -308,10 +308,21 @@ cudaError_t launch_n(const BgDev& bg, float th, float tl, cudaStream_t st, const
     constexpr int P = threads_per_transform<N>(), CZ = col_group<N>();
     constexpr size_t smr = sizeof(float2) * 3 * tstride<N>(), smc = sizeof(float2) * CZ * tstride<N>();
     static_assert(smc <= 227 * 1024 && smr <= 227 * 1024, "shared memory of one CTA");
-    cudaError_t e = cudaFuncSetAttribute(k_spectrum_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-    if (e != cudaSuccess) return e;
+    static int attr[kMaxCachedDevices] = {};
+    const int ok = cached_per_device(attr, [] {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_spectrum_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        return (e == cudaSuccess &&
+                cudaFuncSetAttribute(k_fft_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc) ==
+                    cudaSuccess)
+                   ? 1
+                   : -1;
+    });
+    if (ok < 0) {
+        cudaGetLastError();
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e;
     e = launch_pdl(k_spectrum_rows<N>, N / 2 + 1, 3 * P, smr, st, bg, th, tl, t_dev);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_fft_cols<N>, N / CZ + N / (2 * CZ), CZ * P, smc, st, bg);

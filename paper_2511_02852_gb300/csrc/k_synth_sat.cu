@@ -490,7 +490,13 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
 }
 
 cudaError_t sat_attributes() {
-    return cudaFuncSetAttribute(k_synth_sat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SatSmem));
+    static int attr[kMaxCachedDevices] = {};
+    return cached_per_device(attr, [] {
+               return cudaFuncSetAttribute(k_synth_sat, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(SatSmem)) == cudaSuccess ? 1 : -1;
+           }) > 0
+               ? cudaSuccess
+               : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -498,7 +504,12 @@ cudaError_t sat_attributes() {
 int synth_sat_tile() { return kT; }
 
 // resident CTAs per SM from the SM's limits (shared memory, registers, threads)
+static int synth_sat_ctas_per_sm_query();
 int synth_sat_ctas_per_sm() {
+    static int cache[kMaxCachedDevices] = {};
+    return max(0, cached_per_device(cache, [] { return max(-1, synth_sat_ctas_per_sm_query()); }));
+}
+static int synth_sat_ctas_per_sm_query() {
     if (sat_attributes() != cudaSuccess) return 0;
     int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
     cudaFuncAttributes a;
@@ -522,11 +533,15 @@ cudaError_t launch_synth_sat(const TcItem* items, int n_items, const PatchDev* p
     if (e != cudaSuccess) return e;
     if (n_items > 0) {
         // persistent grid: one CTA per resident slot, no more than the items
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return cudaGetLastError();
-        const int grid = min(n_items, sms * max(1, synth_sat_ctas_per_sm()));
+        static int slots[kMaxCachedDevices] = {};
+        const int n_slots = cached_per_device(slots, [] {
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return 152;
+            return sms * max(1, synth_sat_ctas_per_sm());
+        });
+        const int grid = min(n_items, n_slots);
         e = launch_pdl(k_synth_sat, grid, kSatThreads, sizeof(SatSmem), st, items, n_items, pdevs, sps, queue);
         count_launches(1);
         if (e != cudaSuccess) return e;

@@ -375,7 +375,13 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat3(const TcItem* ite
 }
 
 cudaError_t sat3_attributes() {
-    return cudaFuncSetAttribute(k_synth_sat3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SatSmem));
+    static int attr[kMaxCachedDevices] = {};
+    return cached_per_device(attr, [] {
+               return cudaFuncSetAttribute(k_synth_sat3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(SatSmem)) == cudaSuccess ? 1 : -1;
+           }) > 0
+               ? cudaSuccess
+               : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -383,7 +389,12 @@ cudaError_t sat3_attributes() {
 int synth_sat3_row_cap() { return kSatRowCap; }
 
 // resident CTAs per SM from the SM's limits (shared memory, registers, threads)
+static int synth_sat3_ctas_per_sm_query();
 int synth_sat3_ctas_per_sm() {
+    static int cache[kMaxCachedDevices] = {};
+    return max(0, cached_per_device(cache, [] { return max(-1, synth_sat3_ctas_per_sm_query()); }));
+}
+static int synth_sat3_ctas_per_sm_query() {
     if (sat3_attributes() != cudaSuccess) return 0;
     int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
     cudaFuncAttributes a;
