@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(3 * threads_per_transform<N>(), N >= 1024 ? 3 
 // column pair).  The rows k_y > N/2 of H1, Dx1 and Dy1 are the conjugates of
 // the rows N - k_y.  out is [3][N][N] (h, Dx, Dy), row-major.
 template <int N>
-__global__ void __launch_bounds__(col_group<N>() * threads_per_transform<N>()) k_fft_cols(BgDev bg) {
+__global__ void __launch_bounds__(col_group<N>() * threads_per_transform<N>(),
+                                  col_group<N>() * threads_per_transform<N>() <= 512 ? 2 : 1) k_fft_cols(BgDev bg) {
     constexpr int P = threads_per_transform<N>(), Np = tstride<N>(), CZ = col_group<N>();
     constexpr int NT = CZ * P;
     extern __shared__ float2 smem_cols[];
