@@ -1220,13 +1220,18 @@ static scwp_status enqueue_frame(scwp_ctx* ctx, const std::vector<InjectParams>&
     // background on the side stream, concurrent with the particle stages;
     // with stage timing on, alone on the context stream ahead of them, so
     // that each stage's events time that stage by itself
-    CU(cudaEventRecord(ctx->ev_fork, ctx->st));
-    cudaStream_t bgs = fe ? ctx->st : ctx->side;
-    if (!fe) CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-    if (fe && (s = record(ctx, fe->e[4], bgs)) != SCWP_OK) return s;
-    CU(launch_background(ctx->bg, ctx->t, bgs, t_dev));
-    if (fe && (s = record(ctx, fe->e[5], bgs)) != SCWP_OK) return s;
-    CU(cudaEventRecord(ctx->ev_join, bgs));
+    if (fe) {
+        if ((s = record(ctx, fe->e[4], ctx->st)) != SCWP_OK) return s;
+        CU(launch_background(ctx->bg, ctx->t, ctx->st, t_dev));
+        if ((s = record(ctx, fe->e[5], ctx->st)) != SCWP_OK) return s;
+        CU(cudaEventRecord(ctx->ev_fork, ctx->st));   // the particle streams start after it
+        CU(cudaEventRecord(ctx->ev_join, ctx->st));
+    } else {
+        CU(cudaEventRecord(ctx->ev_fork, ctx->st));
+        CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        CU(launch_background(ctx->bg, ctx->t, ctx->side, t_dev));
+        CU(cudaEventRecord(ctx->ev_join, ctx->side));
+    }
     ctx->bg_valid = true;
 
     // one patch: the context stream; several: up to kParticleStreams
