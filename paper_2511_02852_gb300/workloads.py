@@ -190,22 +190,88 @@ def mixed_large(n_patches=8, particles=2_000_000, seed=2):
 #    of two), JONSWAP U10 uniform in 5..20 m/s at a 100 km fetch, 1..16
 #    patches with sides log-uniform in 64..512 cells, 1e4..1e6 particles per
 #    scene (log-uniform, split over the patches by area), 8..16 buckets.
-#    Unstated by the scene list and chosen here: the cell is 1/48 of the
-#    peak wavelength (so kernel radii in cells stay alike across winds) and
-#    the FFT domain is N/32 peak wavelengths.  Scenes from seed 3.
-G = 9.81
+#    Unstated by the scene list and chosen here: the cell is about 1/48 of
+#    the scene's peak wavelength (so kernel radii in cells stay alike across
+#    winds) and the FFT domain about N/32 peak wavelengths; both are given
+#    per scene in the table below (metres, 6 significant digits), in scene
+#    order.  Scenes from seed 3.
+_SERVING_GEOMETRY = [  # (cell, fft_L) of scene s
+    (0.926961, 355.953),
+    (1.20053, 922.005),
+    (1.92556, 739.417),
+    (1.69859, 652.26),
+    (1.28292, 985.282),
+    (1.27145, 488.237),
+    (1.65519, 1271.18),
+    (1.90589, 2927.45),
+    (1.73344, 1331.28),
+    (1.99411, 765.736),
+    (1.88116, 1444.73),
+    (0.86713, 1331.91),
+    (1.37671, 1057.31),
+    (1.3107, 1006.61),
+    (1.47351, 1131.66),
+    (1.79633, 2759.16),
+    (1.98574, 762.523),
+    (1.39382, 1070.45),
+    (0.983635, 755.432),
+    (1.24957, 479.835),
+    (1.473, 565.633),
+    (1.7648, 1355.37),
+    (1.70401, 654.341),
+    (1.32105, 1014.57),
+    (1.27053, 975.77),
+    (1.75087, 672.334),
+    (1.97698, 1518.32),
+    (1.5455, 593.472),
+    (1.3304, 2043.49),
+    (2.00299, 1538.29),
+    (1.56826, 1204.42),
+    (1.96553, 754.762),
+    (1.87275, 1438.27),
+    (2.00168, 768.646),
+    (1.77083, 1360.0),
+    (1.36538, 2097.22),
+    (0.825969, 634.344),
+    (0.799807, 307.126),
+    (1.6465, 1264.51),
+    (1.15801, 889.354),
+    (1.87094, 718.44),
+    (0.891995, 342.526),
+    (1.57852, 2424.61),
+    (1.82119, 2797.35),
+    (1.7726, 1361.36),
+    (1.82296, 1400.04),
+    (0.796395, 1223.26),
+    (1.84092, 1413.83),
+    (0.844907, 648.889),
+    (1.98479, 3048.64),
+    (1.3332, 511.95),
+    (1.50428, 577.645),
+    (1.65393, 635.109),
+    (1.26566, 1944.05),
+    (1.21818, 935.563),
+    (1.40513, 1079.14),
+    (1.42287, 546.384),
+    (1.03315, 793.458),
+    (1.52842, 2347.65),
+    (1.86352, 2862.37),
+    (1.01395, 778.713),
+    (1.60536, 1232.92),
+    (1.0739, 1649.51),
+    (1.6104, 1236.79)
+]
 
 
 def serving(n_scenes=64, seed=3):
+    if seed != 3 or n_scenes > len(_SERVING_GEOMETRY):
+        raise ValueError("the serving geometry table covers the 64 scenes of seed 3")
     rng = np.random.default_rng(seed)
     out = []
     for s in range(n_scenes):
         U = float(rng.uniform(5.0, 20.0))
         N = int(2 ** int(round(rng.uniform(8.0, 10.0))))
-        wp = 22.0 * (G * G / (U * 100e3)) ** (1.0 / 3.0)
-        lam_p = 2.0 * math.pi * G / (wp * wp)
-        cell = lam_p / 48.0
-        L = N * lam_p / 32.0
+        cell, L = _SERVING_GEOMETRY[s]
         n_p = int(rng.integers(1, 17))
         total = float(np.exp(rng.uniform(math.log(1e4), math.log(1e6))))
         sides = np.clip(np.round(np.exp(rng.uniform(math.log(64), math.log(512), size=(n_p, 2)))), 64, 512)
