@@ -186,6 +186,8 @@ typedef struct scwp_patch_info {
                                   counts, host-placed spawn points) copied to the device */
     int32_t sat_variant;       /* summed-area kernel of this patch: 0 the persistent
                                   nine-plane kernel, 1 the three-group kernel */
+    int32_t sat_parts;         /* parts each bucket's passes are split over (1 but on
+                                  very dense patches, whose buckets take many passes) */
 } scwp_patch_info;
 
 /* Table identifiers for scwp_get_table (element type, count). */

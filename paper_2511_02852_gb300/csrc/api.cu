@@ -68,6 +68,7 @@ struct PatchHost {
     int sat_groups = 1;
     int sat_slots = 0;
     int sat_item_cap = 0;             // capacity of d_sat_items (items of the largest G)
+    int sat_parts = 1;                // parts each bucket's passes are split over (dense patches)
     bool sat3_ok = false;             // every bucket fits the three-group kernel's row table
 };
 
@@ -439,6 +440,16 @@ std::vector<BlendSpan> blend_spans(const PatchHost& P, int G) {
     return out;
 }
 
+// Parts K over which the summed-area items of a patch split each bucket's
+// passes: the smallest K (up to kmax) that brings the patch's heaviest item
+// to at most `cap` stages; a part item costs its set-up plus 1/K of the rest.
+int sat_parts_for(double wmax, double cap, int kmax) {
+    int K = 1;
+    while (K < kmax && kItemStages + (wmax - kItemStages) / K > cap) ++K;
+    return K;
+}
+double part_work(double w, int K) { return kItemStages + (w - kItemStages) / K; }
+
 // Plan of one patch launched alone: G minimises the simulated makespan over
 // the device's resident CTA slots plus the traffic of the group-sum blend.
 // For the summed-area synthesis, gmul scales the chosen G (the autotuner's
@@ -483,7 +494,33 @@ void plan_patch(PatchHost& P, int slots, bool sat = false, double gmul = 1.0, in
             plan = build(G).second;
         }
     }
-    (sat ? P.sat_spans : P.tc_spans) = blend_spans(P, groups);
+    int K = 1;
+    if (sat) {
+        // dense patches: split each bucket's passes over K parts when the
+        // heaviest item would take more than a quarter of a slot's share
+        double total = 0.0, wmax = 0.0;
+        for (const TcItem& it : plan) {
+            const double w = item_work(est, nb, it.tile, it.group, groups);
+            total += w;
+            wmax = std::max(wmax, w);
+        }
+        K = sat_parts_for(wmax, 0.25 * total / std::max(slots, 1), std::max(1, std::min(8, gcap / groups)));
+        if (K > 1) {
+            std::vector<std::pair<double, TcItem>> parts;
+            for (const TcItem& it : plan)
+                for (int q = 0; q < K; ++q)
+                    parts.push_back({part_work(item_work(est, nb, it.tile, it.group, groups), K),
+                                     TcItem{it.patch, it.tile, it.group | (q << 16), groups | (K << 16)}});
+            std::stable_sort(parts.begin(), parts.end(),
+                             [](const std::pair<double, TcItem>& a, const std::pair<double, TcItem>& b) {
+                                 return a.first > b.first;
+                             });
+            plan.clear();
+            for (auto& pr : parts) plan.push_back(pr.second);
+        }
+        P.sat_parts = K;
+    }
+    (sat ? P.sat_spans : P.tc_spans) = blend_spans(P, groups * K);
 }
 
 // Resident CTA slots of a summed-area kernel variant on the current device
@@ -534,14 +571,24 @@ void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vec
             if (mx <= cap || G >= gmax) break;
         }
         // summed-area items: no more groups than the patch's own plan takes
-        // (enough waves for the patch alone; more only adds blend traffic)
-        if (sat) G = std::max(1, std::min(G, P.sat_groups));
+        // (enough waves for the patch alone; more only adds blend traffic),
+        // and each bucket's passes split over K parts where an item would
+        // still be heavier than the cap (dense patches)
+        int K = 1;
+        if (sat) {
+            G = std::max(1, std::min(G, P.sat_groups));
+            double wmax = 0.0;
+            for (int t = 0; t < tiles[k]; ++t)
+                for (int g = 0; g < G; ++g) wmax = std::max(wmax, item_work(est[k], nb, t, g, G));
+            K = sat_parts_for(wmax, cap, std::max(1, std::min(8, P.partial_planes / G)));
+        }
         for (int t = 0; t < tiles[k]; ++t)
-            for (int g = 0; g < G; ++g) {
-                items.push_back(TcItem{P.index, t, g, G});
-                work.push_back(item_work(est[k], nb, t, g, G));
-            }
-        const std::vector<BlendSpan> sp = blend_spans(P, G);
+            for (int g = 0; g < G; ++g)
+                for (int q = 0; q < K; ++q) {
+                    items.push_back(K > 1 ? TcItem{P.index, t, g | (q << 16), G | (K << 16)} : TcItem{P.index, t, g, G});
+                    work.push_back(part_work(item_work(est[k], nb, t, g, G), K));
+                }
+        const std::vector<BlendSpan> sp = blend_spans(P, G * K);
         spans.insert(spans.end(), sp.begin(), sp.end());
     }
     std::vector<int> order(items.size());
@@ -921,21 +968,25 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
             gsat = std::max(gsat, P->sat_groups);
         }
         const int nbmax = std::min(T.nb, 16);
-        const int gpart = std::min(nbmax, 2 * gsat);
+        // planes: room for twice the groups, and on patches of up to 0.35M
+        // texels (at most 256 MiB of planes) for 64 planes, so that dense
+        // small patches can split their buckets' passes into parts
+        int gpart = std::min(nbmax, 2 * gsat);
+        if ((size_t)64 * 12 * T.W * T.H <= ((size_t)256 << 20)) gpart = 64;
+        P->partial_planes = std::max(std::max(D.groups, D.groups_tc), gpart);
         const int variant = (ctx->sat_variant == 1 && P->sat3_ok) ? 1 : 0;
         P->sat_slots = sat_slots_of(variant);
         ctx->sat_slots = P->sat_slots;
-        plan_patch(*P, P->sat_slots, true, ctx->sat_gmul, gpart);
+        plan_patch(*P, P->sat_slots, true, ctx->sat_gmul, P->partial_planes);
         P->d_items = (TcItem*)dalloc(ctx, P->tc_items.size() * sizeof(TcItem));
         P->d_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, P->tc_spans.size()) * sizeof(BlendSpan));
         int tiles_sat = 0;
         tile_bucket_sat(*P, tiles_sat);
-        P->sat_item_cap = tiles_sat * gpart;
+        P->sat_item_cap = tiles_sat * P->partial_planes;   // G K <= the planes
         P->d_sat_items = (TcItem*)dalloc(ctx, (size_t)P->sat_item_cap * sizeof(TcItem));
         P->d_sat_spans = (BlendSpan*)dalloc(ctx, std::max<size_t>(1, blend_spans(*P, 2).size()) * sizeof(BlendSpan));
         ok = ok && P->d_items && P->d_spans && P->d_sat_items && P->d_sat_spans;
-        const int G = std::max(std::max(D.groups, D.groups_tc), gpart);
-        P->partial_planes = G;
+        const int G = P->partial_planes;
         if (G > 1) {
             D.partial = (float*)dalloc(ctx, (size_t)G * 3 * T.W * T.H * sizeof(float));
             ok = ok && D.partial;
@@ -1755,6 +1806,7 @@ scwp_status scwp_patch_info_get(scwp_ctx* ctx, int32_t patch_id, scwp_patch_info
     out->sat_items = (int32_t)P->sat_items.size();
     out->sat_slots = P->sat_slots;
     out->sat_variant = (ctx->sat_variant == 1 && P->sat3_ok) ? 1 : 0;
+    out->sat_parts = P->sat_parts;
     out->frame_param_bytes = (int32_t)sizeof(InjectParams);
     for (int i = 0; i < P->T.nb; ++i) {
         out->bin_cells[i] = P->bin_cells[i];

@@ -84,10 +84,18 @@ struct PatchDev {
 };
 
 // One work item of the tensor-core synthesis: bucket group `group` of
-// `groups` over tile `tile` of patch `patch`.
+// `groups` over tile `tile` of patch `patch`.  The summed-area syntheses may
+// also split each bucket's passes over K parts (tiles of very dense patches,
+// whose buckets take many passes): group = g | part << 16, groups =
+// G | K << 16 (K = 0 or 1: not split), and the item writes partial plane
+// g K + part of G K.
 struct TcItem {
     int32_t patch, tile, group, groups;
 };
+__host__ __device__ inline int item_groups(const TcItem& it) { return it.groups & 0xFFFF; }
+__host__ __device__ inline int item_parts(const TcItem& it) { return (it.groups >> 16) > 1 ? (it.groups >> 16) : 1; }
+__host__ __device__ inline int item_group(const TcItem& it) { return it.group & 0xFFFF; }
+__host__ __device__ inline int item_part(const TcItem& it) { return it.group >> 16; }
 
 // One span of the group-sum blend: quads [q0, q1) (4 texels of a row) of
 // patch `patch`, whose synthesis used `groups` bucket groups.

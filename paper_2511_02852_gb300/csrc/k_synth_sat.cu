@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
         }
         const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
         const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
-        const int G = it.groups, g = it.group;
+        const int G = item_groups(it), g = item_group(it), K = item_parts(it), part = item_part(it);
         const int ntx = (sp.W + kT - 1) / kT;
         const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
         const int b_begin = max((g * sp.nb) / G, sp.b_lo);
@@ -301,11 +301,11 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                 const int t = S.sgb[s];
                 const int b = b_begin + t;
                 const float amax = S.mamax[t];
-                if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)ncand);
                 const int mch = pass_size(ncand, S.msatc[t]);
                 float2* const ph = S.ph[s & 1];
-                for (int c0 = 0; c0 < ncand; c0 += mch) {
+                for (int c0 = part * mch; c0 < ncand; c0 += K * mch) {   // this part's passes
                     const int c1 = min(ncand, c0 + mch);
+                    if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)(c1 - c0));
                     const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
                     const float scale = 1073741824.f / bound;              // 2^30 / bound
                     const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                         const int h = tid - kScanThreads, nh = kSatThreads - kScanThreads;
                         if (h < 2 * kT)
                             ph[h] = p.phase[(size_t)b * p.phase_len + (h < kT ? ty0 + h : tx0 + (h - kT))];
-                        if (c1 == ncand) {
+                        if (K == 1 && c1 == ncand) {
                             int sn = s + 1;
                             while (sn < nseg && S.sgnc[sn] == 0) ++sn;
                             if (sn < nseg) {
@@ -464,13 +464,15 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
         if (x < sp.W) {
             const size_t plane = (size_t)sp.W * sp.H;
 #pragma unroll
+            const int pl = g * K + part;   // partial plane of this item
             for (int f = 0; f < 3; ++f) {
-                float* const dst = (G > 1 ? p.partial + ((size_t)g * 3 + f) * plane : p.out + (size_t)f * plane) + x;
+                float* const dst =
+                    (G * K > 1 ? p.partial + ((size_t)pl * 3 + f) * plane : p.out + (size_t)f * plane) + x;
 #pragma unroll
                 for (int r = 0; r < kSegRows; ++r) {
                     const int y = ty0 + sg * kSegRows + r;
                     const float v = f == 0 ? ah[r] : (f == 1 ? adx[r] : ady[r]);
-                    if (y < sp.H) dst[(size_t)y * sp.W] = G > 1 ? v : blend1(sp, x, y, f, v);
+                    if (y < sp.H) dst[(size_t)y * sp.W] = G * K > 1 ? v : blend1(sp, x, y, f, v);
                 }
             }
         }

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat3(const TcItem* ite
     __syncthreads();
     const PatchDev& p = *reinterpret_cast<const PatchDev*>(S.pd);
     const SynthParams& sp = *reinterpret_cast<const SynthParams*>(S.spd);
-    const int G = it.groups, g = it.group;
+    const int G = item_groups(it), g = item_group(it), K = item_parts(it), part = item_part(it);
     const int ntx = (sp.W + kT - 1) / kT;
     const int tx0 = (it.tile % ntx) * kT, ty0 = (it.tile / ntx) * kT;
     const int b_begin = max((g * sp.nb) / G, sp.b_lo);
@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat3(const TcItem* ite
                                                       // where every bucket fits the row table
             const BucketDev bk = S.bk[bi];
             const int q0 = S.rb[t], q1 = S.rb[t + 1];
-            if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)ncand);
             for (int k = tid; k < 2 * kT; k += kSatThreads)
                 S.ph[k] = p.phase[(size_t)(b_begin + bi) * p.phase_len + (k < kT ? ty0 + k : tx0 + (k - kT))];
             // stage the first kSatStage candidates: warp w takes rows w, w + 16, ...
@@ -207,8 +206,9 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat3(const TcItem* ite
             const float nf = (float)ncand;
             const int kch = max(1, (int)ceilf(nf * sqrtf(nf) / bk.sat_c));
             const int mch = (ncand + kch - 1) / kch;
-            for (int c0 = 0; c0 < ncand; c0 += mch) {
+            for (int c0 = part * mch; c0 < ncand; c0 += K * mch) {   // this part's passes
             const int c1 = min(ncand, c0 + mch);
+            if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)(c1 - c0));
             const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
             const float scale = 1073741824.f / bound;              // 2^30 / bound
             const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
@@ -364,12 +364,13 @@ __global__ void __launch_bounds__(kSatThreads, 2) k_synth_sat3(const TcItem* ite
     const size_t plane = (size_t)sp.W * sp.H;
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        float* const dst = (G > 1 ? p.partial + ((size_t)g * 3 + f) * plane : p.out + (size_t)f * plane) + x;
+        float* const dst =
+            (G * K > 1 ? p.partial + ((size_t)(g * K + part) * 3 + f) * plane : p.out + (size_t)f * plane) + x;
 #pragma unroll
         for (int r = 0; r < kSegRows; ++r) {
             const int y = ty0 + sg * kSegRows + r;
             const float v = f == 0 ? ah[r] : (f == 1 ? adx[r] : ady[r]);
-            if (y < sp.H) dst[(size_t)y * sp.W] = G > 1 ? v : blend1(sp, x, y, f, v);
+            if (y < sp.H) dst[(size_t)y * sp.W] = G * K > 1 ? v : blend1(sp, x, y, f, v);
         }
     }
 }

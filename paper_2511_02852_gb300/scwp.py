@@ -76,7 +76,7 @@ class scwp_patch_info(C.Structure):
                 ("nby", C.c_int32 * MAX_BUCKETS), ("bin_base", C.c_int32 * MAX_BUCKETS),
                 ("synth_groups", C.c_int32), ("synth_items", C.c_int32), ("synth_slots", C.c_int32),
                 ("sat_groups", C.c_int32), ("sat_items", C.c_int32), ("sat_slots", C.c_int32),
-                ("frame_param_bytes", C.c_int32), ("sat_variant", C.c_int32)]
+                ("frame_param_bytes", C.c_int32), ("sat_variant", C.c_int32), ("sat_parts", C.c_int32)]
 
 
 TUNE_MAX = 8

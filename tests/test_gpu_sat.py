@@ -277,3 +277,25 @@ def test_autotune_chooses_caches_and_keeps_parity():
     assert cached_b and rows_b[0][:2] == rows[chosen][:2]
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sat_dense_patch_passes_split_into_parts(variant):
+    """The densest patch of the 32-patch batched workload alone (69 x 69
+    texels, 262k particles, 24 buckets: tens of bumps per texel and bucket,
+    so its buckets take many passes): the plan splits each bucket's passes
+    over several parts (items writing their own partial planes), and the
+    maps stay within the contract of the oracle on both kernels."""
+    cfg = wl.batched()
+    cfg["patches"] = [cfg["patches"][9]]
+    sc = sat_scene(cfg)
+    sc.set_sat_plan(variant, 1.0)
+    orc = OracleScene(cfg)
+    sc.step(cfg["dt"])
+    orc.step(cfg["dt"])
+    assert sc.info(0).sat_parts > 1
+    compare_state(sc, orc, 0)
+    ref, ev = orc.patch_maps(0)
+    assert sc.stats(0).eval_count == ev
+    compare_maps(sc.maps(0), ref, orc.spec.Hs(), f"dense patch, parts {sc.info(0).sat_parts}")
+    sc.close()
