@@ -497,14 +497,16 @@ void plan_patch(PatchHost& P, int slots, bool sat = false, double gmul = 1.0, in
     int K = 1;
     if (sat) {
         // dense patches: split each bucket's passes over K parts when the
-        // heaviest item would take more than a quarter of a slot's share
+        // heaviest item alone would outlast the balanced share of a slot
+        // (the makespan's lower bound), with at most one wave of items
         double total = 0.0, wmax = 0.0;
         for (const TcItem& it : plan) {
             const double w = item_work(est, nb, it.tile, it.group, groups);
             total += w;
             wmax = std::max(wmax, w);
         }
-        K = sat_parts_for(wmax, 0.25 * total / std::max(slots, 1), std::max(1, std::min(8, gcap / groups)));
+        const int kwave = std::max(1, slots / std::max<int>(1, (int)plan.size()));
+        K = sat_parts_for(wmax, total / std::max(slots, 1), std::max(1, std::min(std::min(8, kwave), gcap / groups)));
         if (K > 1) {
             std::vector<std::pair<double, TcItem>> parts;
             for (const TcItem& it : plan)
@@ -573,14 +575,15 @@ void plan_batched(scwp_ctx* ctx, int slots, std::vector<TcItem>& items, std::vec
         // summed-area items: no more groups than the patch's own plan takes
         // (enough waves for the patch alone; more only adds blend traffic),
         // and each bucket's passes split over K parts where an item would
-        // still be heavier than the cap (dense patches)
+        // still outlast the balanced per-slot share of the frame (dense
+        // patches whose buckets take many passes)
         int K = 1;
         if (sat) {
             G = std::max(1, std::min(G, P.sat_groups));
             double wmax = 0.0;
             for (int t = 0; t < tiles[k]; ++t)
                 for (int g = 0; g < G; ++g) wmax = std::max(wmax, item_work(est[k], nb, t, g, G));
-            K = sat_parts_for(wmax, cap, std::max(1, std::min(8, P.partial_planes / G)));
+            K = sat_parts_for(wmax, 4.0 * cap, std::max(1, std::min(8, P.partial_planes / G)));
         }
         for (int t = 0; t < tiles[k]; ++t)
             for (int g = 0; g < G; ++g)
