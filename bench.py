@@ -470,8 +470,9 @@ def sat_roofline(sc, cfg, synth_ms, stage_info):
         cand += sc.stats(p).sat_candidates
     ops = tb * SAT_OPS_PER_TEXEL_BUCKET + cand * SAT_OPS_PER_CANDIDATE
     achieved = ops / (synth_ms / 1000.0) / 1e12
-    return {"bound": "alu", "kernel": "k_synth_sat", "achieved": achieved, "peak": ALU_PEAK_TOPS,
-            "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS, "traffic": profiled_traffic(cfg, "k_synth_sat"),
+    kernel = "k_synth_sat3" if sc.info(0).sat_variant == 1 else "k_synth_sat"
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": ALU_PEAK_TOPS,
+            "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS, "traffic": profiled_traffic(cfg, kernel),
             "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (thread instructions)",
             "ops_per_launch": ops, "texel_buckets_per_launch": tb, "candidates_per_launch": cand,
             "ops_note": f"{SAT_OPS_PER_TEXEL_BUCKET} per (texel, bucket): 9 components x (2 prefix adds + "
