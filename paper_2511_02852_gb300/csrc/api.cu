@@ -381,7 +381,7 @@ std::vector<double> tile_bucket_stages(const PatchHost& P, int& tiles) {
 constexpr double kSatBucketUs = 2.0;
 constexpr double kSatBumpUs = 0.0008;
 
-std::vector<double> tile_bucket_sat(const PatchHost& P, int& tiles) {
+std::vector<double> tile_bucket_sat(const PatchHost& P, int& tiles, double* max_passes = nullptr) {
     const PatchTablesHost& T = P.T;
     const int ts = synth_sat_tile();
     const int ntx = (T.W + ts - 1) / ts, nty = (T.H + ts - 1) / ts;
@@ -405,6 +405,7 @@ std::vector<double> tile_bucket_sat(const PatchHost& P, int& tiles) {
             // dense pairs go in several passes, each with the fixed part
             const double n = dens * ax * ay;
             const double passes = std::max(1.0, std::ceil(n * std::sqrt(n) / (double)P.bk[i].sat_c));
+            if (max_passes) *max_passes = std::max(*max_passes, passes);
             est[(size_t)t * T.nb + i] = (passes * kSatBucketUs + n * kSatBumpUs) / kStageUs;
         }
     }
@@ -971,11 +972,15 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
             gsat = std::max(gsat, P->sat_groups);
         }
         const int nbmax = std::min(T.nb, 16);
-        // planes: room for twice the groups, and on patches of up to 0.35M
-        // texels (at most 256 MiB of planes) for 64 planes, so that dense
-        // small patches can split their buckets' passes into parts
+        // planes: room for twice the groups, and on dense patches (buckets
+        // expected to take several passes) of up to 0.35M texels (at most
+        // 256 MiB of planes) for 64 planes, so that their buckets' passes
+        // can split into parts
         int gpart = std::min(nbmax, 2 * gsat);
-        if ((size_t)64 * 12 * T.W * T.H <= ((size_t)256 << 20)) gpart = 64;
+        double max_passes = 0.0;
+        int tiles_est = 0;
+        tile_bucket_sat(*P, tiles_est, &max_passes);
+        if (max_passes >= 2.0 && (size_t)64 * 12 * T.W * T.H <= ((size_t)256 << 20)) gpart = 64;
         P->partial_planes = std::max(std::max(D.groups, D.groups_tc), gpart);
         const int variant = (ctx->sat_variant == 1 && P->sat3_ok) ? 1 : 0;
         P->sat_slots = sat_slots_of(variant);
