@@ -132,31 +132,48 @@ __device__ __forceinline__ int pass_size(int ncand, float satc) {
 // Stage candidates s0 .. s0 + ns - 1 of segment s (thread t of nt): find the
 // candidate's bin row in the segment's part of the row table (the last row
 // whose exclusive candidate prefix is <= f), read its 32-byte record and
-// store its amplitude, phase pairs and support box clipped to the tile.
+// store its amplitude, phase pairs and support box clipped to the tile.  A
+// thread takes its candidates two at a time, both searches (a fixed number
+// of halvings over the segment's rows) and both record loads in flight
+// together, so that the L2 latency is paid once per pair.
 __device__ __forceinline__ void stage(SatSmem& S, const BumpRec* rec, int s, int s0, int ns, int32_t X0,
                                       int32_t Y0, int t, int nt) {
+    constexpr int U = 2;
     const int q0 = S.sgrb[s], q1 = S.sgrb[s + 1];
     const int R = S.mR[S.sgb[s]];
-    for (int k = t; k < ns; k += nt) {
-        const int f = s0 + k;
-        int lo = q0, hi = q1 - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (S.cum[mid] <= f) lo = mid; else hi = mid - 1;
+    const int top = 1 << (31 - __clz(q1 - q0));   // highest power of two <= the segment's rows
+    for (int k0 = t; k0 < ns; k0 += U * nt) {
+        int src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int f = s0 + min(k0 + u * nt, ns - 1);
+            int lo = q0;
+            for (int step = top; step > 0; step >>= 1)
+                if (lo + step < q1 && S.cum[lo + step] <= f) lo += step;
+            src[u] = S.rs[lo] + (f - S.cum[lo]);
         }
-        const float4* rp = reinterpret_cast<const float4*>(rec + S.rs[lo] + (f - S.cum[lo]));
-        const float4 rx = rp[0];   // x, cos, sin, id
-        const float4 ry = rp[1];   // y, cos, sin, A
-        const int32_t xb = __float_as_int(rx.x), yb = __float_as_int(ry.x);
-        // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
-        const int a = clamp_t(((xb - R - X0) >> 16) + 1);
-        const int b = clamp_t(-((X0 - xb - R) >> 16));
-        const int c = clamp_t(((yb - R - Y0) >> 16) + 1);
-        const int d = clamp_t(-((Y0 - yb - R) >> 16));
-        const uint32_t box =
-            (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) | ((uint32_t)d << 21) : 0u;
-        S.c4[k] = make_float4(ry.w, rx.y, rx.z, ry.y);
-        S.c2[k] = make_float2(ry.z, __uint_as_float(box));
+        float4 rx[U], ry[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float4* rp = reinterpret_cast<const float4*>(rec + src[u]);
+            rx[u] = rp[0];   // x, cos, sin, id
+            ry[u] = rp[1];   // y, cos, sin, A
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * nt;
+            if (k >= ns) break;
+            const int32_t xb = __float_as_int(rx[u].x), yb = __float_as_int(ry[u].x);
+            // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
+            const int a = clamp_t(((xb - R - X0) >> 16) + 1);
+            const int b = clamp_t(-((X0 - xb - R) >> 16));
+            const int c = clamp_t(((yb - R - Y0) >> 16) + 1);
+            const int d = clamp_t(-((Y0 - yb - R) >> 16));
+            const uint32_t box =
+                (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) | ((uint32_t)d << 21) : 0u;
+            S.c4[k] = make_float4(ry[u].w, rx[u].y, rx[u].z, ry[u].y);
+            S.c2[k] = make_float2(ry[u].z, __uint_as_float(box));
+        }
     }
 }
 
@@ -320,12 +337,23 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                             stage(S, p.rec, s, s0, ns, X0, Y0, tid, kSatThreads);
                             __syncthreads();
                         }
-                        // ---- corner events of the staged candidates
-                        for (int k = tid; k < ns; k += kSatThreads) {
-                            const float2 e = S.c2[k];
+                        // ---- corner events of the staged candidates (a thread's
+                        // two at most: both read before either is processed)
+                        static_assert(kStage <= 2 * kSatThreads, "two staged candidates per thread");
+                        float2 ev[2];
+                        float4 cv[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int k = tid + u * kSatThreads;
+                            ev[u] = k < ns ? S.c2[k] : make_float2(0.f, 0.f);
+                            cv[u] = k < ns ? S.c4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const float2 e = ev[u];
                             const uint32_t box = __float_as_uint(e.y);
-                            if (box == 0u) continue;   // no texel of the tile in the support
-                            const float4 cc = S.c4[k];
+                            if (box == 0u) continue;   // no texel of the tile in the support (or no candidate)
+                            const float4 cc = cv[u];
                             const int a = box & 127, bb = (box >> 7) & 127, c = (box >> 14) & 127,
                                       d = (box >> 21) & 127;
                             const float A = cc.x, qc = cc.w, qs = e.x;
