@@ -38,21 +38,25 @@
 // bucket group) items from a work queue (an atomic ticket over the plan's
 // heaviest-first order; the last CTA to finish resets the queue for the next
 // launch, so no CTA ever waits on another).  All nine S_ij planes of a
-// bucket live in shared memory at once (144 KB), so each candidate bump is
-// staged and turned into corner events exactly once per pass.  Per item, the
-// buckets' bin geometry and the bin rows that reach the tile are read once
-// into a row table (a bucket with more rows than the table spans several
-// segments, each a pass of its own).  Candidates are staged in chunks of
-// 1536: each thread finds its candidate's row by a binary search of the row
-// table and reads the 32-byte record from L2.  Each staged candidate adds its
-// nine weights at up to four corners; bumps whose box starts at the tile's
-// first texel in both axes (every bump covering the whole tile among them)
-// sum their (0, 0) corner in registers, which one warp reduction adds.  The
-// x prefix takes 18 of the 32 warps; meanwhile the other 14 fetch the
-// bucket's texel phases and stage the next segment's first chunk, so that
-// the L2 latency of the staging overlaps the prefix passes.  The last
-// column pass zeroes each difference-array element it reads, so no pass
-// needs a clearing phase.
+// bucket live in shared memory at once (144 KB), so each candidate bump
+// enters exactly once per pass.  Per item, the buckets' bin geometry and the
+// bin rows that reach the tile are read once into a row table (a bucket with
+// more rows than the table spans several segments, each a pass of its own).
+// Within a pass each thread takes the candidates c0 + tid, c0 + tid + 1024,
+// ... on its own, with no barrier until the pass ends: it finds a
+// candidate's bin row (a binary search of the row table) and copies the
+// record with asynchronous 16-byte copies (cp.async) into its own slot of
+// two, one candidate ahead, so the copy of its next candidate (of this pass,
+// or the first of the next pass) overlaps the current one's events, and the
+// next pass's first copies overlap the prefix passes.  As each thread reads
+// only the slots it filled, no barrier guards them.  Each thread clips its
+// candidate's support box to the tile and adds the nine weights at up to
+// four corners; bumps whose box starts at the tile's first texel in both axes
+// (every bump covering the whole tile among them) sum their (0, 0) corner in
+// registers, added by one warp reduction per pass.  Then the x prefix (one
+// row of one plane per thread), the y prefix (one column of one
+// plane per thread) and the contraction, which zeroes every difference-array
+// element it reads, so no pass needs a clearing phase.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -65,22 +69,19 @@ namespace {
 
 constexpr int kT = 64;                       // tile side in texels
 constexpr int kSatThreads = 1024;
-constexpr int kSegs = kSatThreads / kT;      // row segments of the column pass
+constexpr int kSegs = kSatThreads / kT;      // row segments of the contraction
 constexpr int kSegRows = kT / kSegs;         // rows per segment
 constexpr int kPlanes = 9;                   // S_ij, plane 3 i + j
 constexpr int kScanThreads = kPlanes * kT;   // one row (or column) scan per thread
 constexpr int kRowCap = 256;                 // bin rows held at once (all segments of a batch)
 constexpr int kMaxSeg = 64;                  // segments per batch
-constexpr int kStage = 1536;                 // candidates staged at once
 constexpr int32_t kQs = 65536, kHalfs = 32768;
-static_assert(kSegs * kSegRows == kT && kSegs == 16, "column-pass mapping");
+static_assert(kSegs * kSegRows == kT && kSegs == 16, "contraction mapping");
 static_assert(kScanThreads % 32 == 0 && kScanThreads + 128 <= kSatThreads, "scan warps and helper warps");
 
 struct SatSmem {
     uint32_t E[kPlanes][kT * kT];         // difference arrays, then prefix sums; zero between passes
-    uint32_t seg[kSegs][kPlanes][kT];     // column sums of each row segment
-    float4 c4[kStage];                    // staged candidates: A, cos, sin (x), cos (y)
-    float2 c2[kStage];                    //                    sin (y), support box (bits)
+    alignas(128) BumpRec raw[2][kSatThreads];   // two record slots per thread
     float2 ph[2][2 * kT];                 // texel phases (cos, sin) a of a segment's bucket: rows, then columns
     int32_t rs[kRowCap];                  // first record of each bin row of the batch
     int32_t cum[kRowCap];                 // candidates of the segment before the row
@@ -88,13 +89,15 @@ struct SatSmem {
     int32_t mR[kMaxBuckets], mC[kMaxBuckets], mnbx[kMaxBuckets], mbase[kMaxBuckets];
     int32_t mbx_lo[kMaxBuckets], mbx_hi[kMaxBuckets], mby_lo[kMaxBuckets], mnrows[kMaxBuckets];
     float mamax[kMaxBuckets], msatc[kMaxBuckets];
-    // the batch's segments: bucket (item-relative), first row, first table row, candidates
-    int32_t sgb[kMaxSeg], sgr0[kMaxSeg], sgrb[kMaxSeg + 1], sgnc[kMaxSeg];
-    int32_t item, patch, nseg, bt_next, bt_r0, staged;
+    // the batch's segments: bucket (item-relative), first row, first table
+    // row, candidates, candidates per pass
+    int32_t sgb[kMaxSeg], sgr0[kMaxSeg], sgrb[kMaxSeg + 1], sgnc[kMaxSeg], sgm[kMaxSeg];
+    int32_t item, patch, nseg, bt_next, bt_r0, pad;
     alignas(16) unsigned char pd[sizeof(PatchDev)];
     alignas(16) unsigned char spd[sizeof(SynthParams)];
 };
 static_assert(sizeof(SatSmem) <= 227 * 1024, "shared memory of one CTA");
+static_assert(sizeof(BumpRec) == 32, "32-byte records (two 16-byte copies)");
 
 // element (row y, column x) of a 64 x 64 plane: columns XOR-swizzled by the
 // row so that a warp walking a row (one row per lane) or a column (one
@@ -129,61 +132,67 @@ __device__ __forceinline__ int pass_size(int ncand, float satc) {
     return (ncand + kch - 1) / kch;
 }
 
-// Stage candidates s0 .. s0 + ns - 1 of segment s (thread t of nt): find the
-// candidate's bin row in the segment's part of the row table (the last row
-// whose exclusive candidate prefix is <= f), read its 32-byte record and
-// store its amplitude, phase pairs and support box clipped to the tile.  A
-// thread takes its candidates two at a time, both searches (a fixed number
-// of halvings over the segment's rows) and both record loads in flight
-// together, so that the L2 latency is paid once per pair.
-__device__ __forceinline__ void stage(SatSmem& S, const BumpRec* rec, int s, int s0, int ns, int32_t X0,
-                                      int32_t Y0, int t, int nt) {
-    constexpr int U = 2;
-    const int q0 = S.sgrb[s], q1 = S.sgrb[s + 1];
-    const int R = S.mR[S.sgb[s]];
-    const int top = 1 << (31 - __clz(q1 - q0));   // highest power of two <= the segment's rows
-    for (int k0 = t; k0 < ns; k0 += U * nt) {
-        int src[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int f = s0 + min(k0 + u * nt, ns - 1);
-            int lo = q0;
-            for (int step = top; step > 0; step >>= 1)
-                if (lo + step < q1 && S.cum[lo + step] <= f) lo += step;
-            src[u] = S.rs[lo] + (f - S.cum[lo]);
-        }
-        float4 rx[U], ry[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const float4* rp = reinterpret_cast<const float4*>(rec + src[u]);
-            rx[u] = rp[0];   // x, cos, sin, id
-            ry[u] = rp[1];   // y, cos, sin, A
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * nt;
-            if (k >= ns) break;
-            const int32_t xb = __float_as_int(rx[u].x), yb = __float_as_int(ry[u].x);
-            // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
-            const int a = clamp_t(((xb - R - X0) >> 16) + 1);
-            const int b = clamp_t(-((X0 - xb - R) >> 16));
-            const int c = clamp_t(((yb - R - Y0) >> 16) + 1);
-            const int d = clamp_t(-((Y0 - yb - R) >> 16));
-            const uint32_t box =
-                (a < b && c < d) ? (uint32_t)a | ((uint32_t)b << 7) | ((uint32_t)c << 14) | ((uint32_t)d << 21) : 0u;
-            S.c4[k] = make_float4(ry[u].w, rx[u].y, rx[u].z, ry[u].y);
-            S.c2[k] = make_float2(ry[u].z, __uint_as_float(box));
-        }
+// ---- asynchronous 16-byte copies global -> shared (L2 only)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most one group of this thread's copies is still in flight
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// A pass of this CTA's part: segment s, its candidates [c0, c1); s < 0: none.
+struct Pass {
+    int s, c0, c1;
+};
+
+__device__ __forceinline__ Pass make_pass(const SatSmem& S, int s, int c0) {
+    return Pass{s, c0, min(S.sgnc[s], c0 + S.sgm[s])};
+}
+
+// The part's first pass of segments s0, s0 + 1, ... with candidates.
+__device__ __forceinline__ Pass first_pass_from(const SatSmem& S, int s0, int nseg, int part) {
+    for (int s = s0; s < nseg; ++s)
+        if (part * S.sgm[s] < S.sgnc[s]) return make_pass(S, s, part * S.sgm[s]);
+    return Pass{-1, 0, 0};
+}
+
+// The pass after P in this part's order: the part's next pass of the same
+// segment (parts take every K-th pass), else the first of a later segment.
+__device__ __forceinline__ Pass next_pass(const SatSmem& S, Pass P, int nseg, int K, int part) {
+    const int c0 = P.c0 + K * S.sgm[P.s];
+    if (c0 < S.sgnc[P.s]) return make_pass(S, P.s, c0);
+    return first_pass_from(S, P.s + 1, nseg, part);
+}
+
+// This thread's copy of candidate j (of the segment whose table rows are
+// [lo, hi]) into its slot `slot`; returns the candidate's row.  The row is
+// the last one that starts at or before j (empty rows start where the next
+// one does).
+__device__ __forceinline__ int fetch_rows(SatSmem& S, const BumpRec* rec, int lo, int hi, int j, int slot, int tid) {
+    if (lo < hi && S.cum[lo + 1] > j) hi = lo;   // still the row of the hint
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.cum[mid] <= j)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
+    const BumpRec* src = rec + S.rs[lo] + (j - S.cum[lo]);
+    BumpRec* dst = &S.raw[slot][tid];
+    cp_async16(dst, src);
+    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16, reinterpret_cast<const unsigned char*>(src) + 16);
+    return lo;
 }
 
 __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* items, int n_items,
                                                             const PatchDev* pdevs, const SynthParams* sps,
                                                             unsigned int* queue) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SatSmem& S = *reinterpret_cast<SatSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // column pass: this thread owns texel column cx of rows sg*4 .. sg*4 + 3
+    // contraction: this thread owns texel column cx of rows sg*4 .. sg*4 + 3
     const int cx = tid & (kT - 1), sg = tid / kT;
     pdl_enter();
     // E starts zeroed, and every pass leaves it zeroed again
@@ -277,7 +286,6 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                 S.nseg = n;
                 S.bt_next = t;
                 S.bt_r0 = r0;
-                S.staged = -1;
             }
             __syncthreads();
             const int nseg = S.nseg;
@@ -308,191 +316,180 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                     if (q + lane < q1) S.cum[q + lane] = (int32_t)(carry + inc - l);
                     carry += __shfl_sync(0xffffffffu, inc, 31);
                 }
-                if (lane == 0) S.sgnc[s] = (int32_t)carry;
+                if (lane == 0) {
+                    S.sgnc[s] = (int32_t)carry;
+                    S.sgm[s] = carry ? pass_size((int)carry, S.msatc[S.sgb[s]]) : 0;
+                }
             }
             __syncthreads();
 
-            for (int s = 0; s < nseg; ++s) {
-                const int ncand = S.sgnc[s];
-                if (ncand == 0) continue;   // (uniform)
+            // ---- the batch's passes of this part.  Invariant at a pass's
+            // start: if this thread has a candidate in it (c0 + tid < c1),
+            // its record is on the way into slot k (the last commit group).
+            Pass P = first_pass_from(S, 0, nseg, part);
+            int k = 0;
+            if (P.s >= 0 && P.c0 + tid < P.c1) fetch_rows(S, p.rec, S.sgrb[P.s], S.sgrb[P.s + 1] - 1, P.c0 + tid, k, tid);
+            cp_async_commit();
+            while (P.s >= 0) {
+                const int s = P.s;
                 const int t = S.sgb[s];
                 const int b = b_begin + t;
-                const float amax = S.mamax[t];
-                const int mch = pass_size(ncand, S.msatc[t]);
+                const int R = S.mR[t];
                 float2* const ph = S.ph[s & 1];
-                for (int c0 = part * mch; c0 < ncand; c0 += K * mch) {   // this part's passes
-                    const int c1 = min(ncand, c0 + mch);
-                    if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)(c1 - c0));
-                    const float bound = 1.001f * (float)(c1 - c0) * amax;   // >= every |S_ij| of the pass
-                    const float scale = 1073741824.f / bound;              // 2^30 / bound
-                    const float inv = bound * (1.f / 1073741824.f);        // 1 / scale
-                    // the (0, 0) corner, shared by every bump whose box starts at
-                    // the tile's first texel in both axes: per-thread sums
-                    uint32_t z[kPlanes];
+                const float bound = 1.001f * (float)(P.c1 - P.c0) * S.mamax[t];   // >= every |S_ij| of the pass
+                const float scale = 1073741824.f / bound;                        // 2^30 / bound
+                const float inv = bound * (1.f / 1073741824.f);                  // 1 / scale
+                if (tid == 0) atomicAdd(p.stats + 5 + p.nb, (unsigned long long)(P.c1 - P.c0));
+                const Pass Pn = next_pass(S, P, nseg, K, part);
+                const bool pre = Pn.s >= 0 && Pn.c0 + tid < Pn.c1;   // a candidate in the next pass
+                // the (0, 0) corner, shared by every bump whose box starts at
+                // the tile's first texel in both axes: per-thread sums
+                uint32_t z[kPlanes];
 #pragma unroll
-                    for (int k = 0; k < kPlanes; ++k) z[k] = 0u;
-                    for (int s0 = c0; s0 < c1; s0 += kStage) {
-                        const int ns = min(kStage, c1 - s0);
-                        if (!(S.staged == s && s0 == 0)) {   // (uniform) else staged ahead
-                            stage(S, p.rec, s, s0, ns, X0, Y0, tid, kSatThreads);
-                            __syncthreads();
+                for (int q = 0; q < kPlanes; ++q) z[q] = 0u;
+                if (P.c0 + tid >= P.c1) {   // none here: the next pass's first copy
+                    if (pre) fetch_rows(S, p.rec, S.sgrb[Pn.s], S.sgrb[Pn.s + 1] - 1, Pn.c0 + tid, k, tid);
+                    cp_async_commit();
+                }
+                // the row of this thread's next candidate is at or after that of its current one
+                int q = S.sgrb[s];
+                const int qe = S.sgrb[s + 1] - 1;
+                for (int j = P.c0 + tid; j < P.c1; j += kSatThreads) {
+                    // the copy of this thread's next candidate starts now
+                    if (j + kSatThreads < P.c1)
+                        q = fetch_rows(S, p.rec, q, qe, j + kSatThreads, k ^ 1, tid);
+                    else if (pre)
+                        fetch_rows(S, p.rec, S.sgrb[Pn.s], S.sgrb[Pn.s + 1] - 1, Pn.c0 + tid, k ^ 1, tid);
+                    cp_async_commit();
+                    cp_async_wait_prev();   // this candidate's record has landed
+                    const BumpRec rc = S.raw[k][tid];
+                    k ^= 1;
+                    // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
+                    const int a = clamp_t(((rc.x - R - X0) >> 16) + 1);
+                    const int bb = clamp_t(-((X0 - rc.x - R) >> 16));
+                    const int c = clamp_t(((rc.y - R - Y0) >> 16) + 1);
+                    const int d = clamp_t(-((Y0 - rc.y - R) >> 16));
+                    if (a < bb && c < d) {
+                        const float A = rc.amp;
+                        const float m0 = A * scale, m1 = A * rc.cx * scale, m2 = A * rc.sx * scale;
+                        uint32_t w[kPlanes];
+                        w[0] = (uint32_t)__float2int_rn(m0);
+                        w[1] = (uint32_t)__float2int_rn(m0 * rc.cy);
+                        w[2] = (uint32_t)__float2int_rn(m0 * rc.sy);
+                        w[3] = (uint32_t)__float2int_rn(m1);
+                        w[4] = (uint32_t)__float2int_rn(m1 * rc.cy);
+                        w[5] = (uint32_t)__float2int_rn(m1 * rc.sy);
+                        w[6] = (uint32_t)__float2int_rn(m2);
+                        w[7] = (uint32_t)__float2int_rn(m2 * rc.cy);
+                        w[8] = (uint32_t)__float2int_rn(m2 * rc.sy);
+                        if (a == 0 && c == 0) {
+#pragma unroll
+                            for (int q = 0; q < kPlanes; ++q) z[q] += w[q];
+                        } else {
+                            event9(S, a, c, w, false);
                         }
-                        // ---- corner events of the staged candidates (a thread's
-                        // two at most: both read before either is processed)
-                        static_assert(kStage <= 2 * kSatThreads, "two staged candidates per thread");
-                        float2 ev[2];
-                        float4 cv[2];
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int k = tid + u * kSatThreads;
-                            ev[u] = k < ns ? S.c2[k] : make_float2(0.f, 0.f);
-                            cv[u] = k < ns ? S.c4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const float2 e = ev[u];
-                            const uint32_t box = __float_as_uint(e.y);
-                            if (box == 0u) continue;   // no texel of the tile in the support (or no candidate)
-                            const float4 cc = cv[u];
-                            const int a = box & 127, bb = (box >> 7) & 127, c = (box >> 14) & 127,
-                                      d = (box >> 21) & 127;
-                            const float A = cc.x, qc = cc.w, qs = e.x;
-                            const float m0 = A * scale, m1 = A * cc.y * scale, m2 = A * cc.z * scale;
-                            uint32_t w[kPlanes];
-                            w[0] = (uint32_t)__float2int_rn(m0);
-                            w[1] = (uint32_t)__float2int_rn(m0 * qc);
-                            w[2] = (uint32_t)__float2int_rn(m0 * qs);
-                            w[3] = (uint32_t)__float2int_rn(m1);
-                            w[4] = (uint32_t)__float2int_rn(m1 * qc);
-                            w[5] = (uint32_t)__float2int_rn(m1 * qs);
-                            w[6] = (uint32_t)__float2int_rn(m2);
-                            w[7] = (uint32_t)__float2int_rn(m2 * qc);
-                            w[8] = (uint32_t)__float2int_rn(m2 * qs);
-                            if (a == 0 && c == 0) {
-#pragma unroll
-                                for (int q = 0; q < kPlanes; ++q) z[q] += w[q];
-                            } else {
-                                event9(S, a, c, w, false);
-                            }
-                            if (bb < kT) event9(S, bb, c, w, true);
-                            if (d < kT) event9(S, a, d, w, true);
-                            if (bb < kT && d < kT) event9(S, bb, d, w, false);
-                        }
-                        if (s0 + kStage >= c1) {   // the pass's last chunk: the (0, 0) corner
-#pragma unroll
-                            for (int k = 0; k < kPlanes; ++k) z[k] = __reduce_add_sync(0xffffffffu, z[k]);
-                            if (lane == 0) {
-#pragma unroll
-                                for (int k = 0; k < kPlanes; ++k)
-                                    if (z[k]) atomicAdd(&S.E[k][0], z[k]);
-                            }
-                        }
-                        __syncthreads();
+                        if (bb < kT) event9(S, bb, c, w, true);
+                        if (d < kT) event9(S, a, d, w, true);
+                        if (bb < kT && d < kT) event9(S, bb, d, w, false);
                     }
-                    if (tid < kScanThreads) {
-                        // ---- prefix along x: one row of one plane per thread, in
-                        // chunks of 4 with the next chunk loaded before this one
-                        // is stored (the loads need not wait for the stores)
-                        uint32_t* E = S.E[tid / kT];
-                        const int y = tid % kT;
-                        uint32_t cur[4], nxt[4], run = 0u;
+                }
+                // (all threads converge here: one reduction per warp and pass)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) cur[k] = E[sw(y, k)];
+                for (int q = 0; q < kPlanes; ++q) z[q] = __reduce_add_sync(0xffffffffu, z[q]);
+                if (lane == 0) {
 #pragma unroll
-                        for (int x0 = 0; x0 < kT; x0 += 4) {
-                            if (x0 + 4 < kT) {
+                    for (int q = 0; q < kPlanes; ++q)
+                        if (z[q]) atomicAdd(&S.E[q][0], z[q]);
+                }
+                __syncthreads();   // E holds the pass's events
+                if (tid < kScanThreads) {
+                    // ---- prefix along x: one row of one plane per thread, in
+                    // chunks of 4 with the next chunk loaded before this one
+                    // is stored (the loads need not wait for the stores)
+                    uint32_t* E = S.E[tid / kT];
+                    const int y = tid % kT;
+                    uint32_t cr[4], nx[4], run = 0u;
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) nxt[k] = E[sw(y, x0 + 4 + k)];
-                            }
+                    for (int k = 0; k < 4; ++k) cr[k] = E[sw(y, k)];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                run += cur[k];
-                                E[sw(y, x0 + k)] = run;
-                            }
+                    for (int x0 = 0; x0 < kT; x0 += 4) {
+                        if (x0 + 4 < kT) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+                            for (int k = 0; k < 4; ++k) nx[k] = E[sw(y, x0 + 4 + k)];
                         }
-                    } else {
-                        // ---- meanwhile the other warps fetch this bucket's texel
-                        // phases and, after the segment's last pass, stage the first
-                        // chunk of the next segment that has candidates
-                        const int h = tid - kScanThreads, nh = kSatThreads - kScanThreads;
-                        if (h < 2 * kT)
-                            ph[h] = p.phase[(size_t)b * p.phase_len + (h < kT ? ty0 + h : tx0 + (h - kT))];
-                        if (K == 1 && c1 == ncand) {
-                            int sn = s + 1;
-                            while (sn < nseg && S.sgnc[sn] == 0) ++sn;
-                            if (sn < nseg) {
-                                const int mn = pass_size(S.sgnc[sn], S.msatc[S.sgb[sn]]);
-                                stage(S, p.rec, sn, 0, min(kStage, mn), X0, Y0, h, nh);
-                                if (h == 0) S.staged = sn;
-                            }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            run += cr[k];
+                            E[sw(y, x0 + k)] = run;
                         }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) cr[k] = nx[k];
                     }
-                    __syncthreads();
-                    // ---- prefix along y in three steps: the column sums of each
-                    // row segment ...
+                } else if (tid < kScanThreads + 2 * kT) {
+                    // ---- meanwhile spare warps fetch this bucket's texel phases
+                    const int h = tid - kScanThreads;
+                    ph[h] = p.phase[(size_t)b * p.phase_len + (h < kT ? ty0 + h : tx0 + (h - kT))];
+                }
+                __syncthreads();
+                if (tid < kScanThreads) {
+                    // ---- prefix along y: one column of one plane per thread
+                    uint32_t* E = S.E[tid / kT];
+                    const int x = tid % kT;
+                    uint32_t cr[4], nx[4], run = 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cr[k] = E[sw(k, x)];
+#pragma unroll
+                    for (int y0 = 0; y0 < kT; y0 += 4) {
+                        if (y0 + 4 < kT) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) nx[k] = E[sw(y0 + 4 + k, x)];
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            run += cr[k];
+                            E[sw(y0 + k, x)] = run;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) cr[k] = nx[k];
+                    }
+                }
+                __syncthreads();
+                // ---- this thread's texels contracted; each element of E is
+                // zeroed once read (the next pass starts from a cleared array)
+                const float2 ux = ph[kT + cx];   // (cos a_X, sin a_X) of this column
+                const float kh = 0.25f * inv, kd = lamq * inv;
+#pragma unroll
+                for (int r = 0; r < kSegRows; ++r) {
+                    const int y = sg * kSegRows + r;
+                    const int o = sw(y, cx);
+                    float f[kPlanes];
 #pragma unroll
                     for (int k = 0; k < kPlanes; ++k) {
-                        uint32_t v = 0u;
-#pragma unroll
-                        for (int r = 0; r < kSegRows; ++r) v += S.E[k][sw(sg * kSegRows + r, cx)];
-                        S.seg[sg][k][cx] = v;
+                        f[k] = (float)(int32_t)S.E[k][o];
+                        S.E[k][o] = 0u;
                     }
-                    __syncthreads();
-                    // ... their exclusive prefix over the segments ...
-                    if (tid < kScanThreads) {
-                        const int k = tid / kT, c = tid % kT;
-                        uint32_t run = 0u;
+                    const float2 vy = ph[y];   // (cos a_Y, sin a_Y)
+                    float tt[3], tp[3];
 #pragma unroll
-                        for (int q = 0; q < kSegs; ++q) {
-                            const uint32_t v = S.seg[q][k][c];
-                            S.seg[q][k][c] = run;
-                            run += v;
-                        }
+                    for (int i = 0; i < 3; ++i) {
+                        tt[i] = fmaf(-vy.y, f[3 * i + 2], fmaf(vy.x, f[3 * i + 1], f[3 * i]));   // v . S_i.
+                        tp[i] = fmaf(vy.y, f[3 * i + 1], vy.x * f[3 * i + 2]);                 // v' . S_i.
                     }
-                    __syncthreads();
-                    // ... then this segment's rows, contracted as they come; each
-                    // element of E is zeroed once read (the next pass starts from
-                    // a cleared difference array)
-                    uint32_t run[kPlanes];
-#pragma unroll
-                    for (int k = 0; k < kPlanes; ++k) run[k] = S.seg[sg][k][cx];
-                    const float2 ux = ph[kT + cx];   // (cos a_X, sin a_X) of this column
-                    const float kh = 0.25f * inv, kd = lamq * inv;
-#pragma unroll
-                    for (int r = 0; r < kSegRows; ++r) {
-                        const int y = sg * kSegRows + r;
-                        const int o = sw(y, cx);
-                        float f[kPlanes];
-#pragma unroll
-                        for (int k = 0; k < kPlanes; ++k) {
-                            run[k] += S.E[k][o];
-                            S.E[k][o] = 0u;
-                            f[k] = (float)(int32_t)run[k];
-                        }
-                        const float2 vy = ph[y];   // (cos a_Y, sin a_Y)
-                        float tt[3], tp[3];
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) {
-                            tt[i] = fmaf(-vy.y, f[3 * i + 2], fmaf(vy.x, f[3 * i + 1], f[3 * i]));   // v . S_i.
-                            tp[i] = fmaf(vy.y, f[3 * i + 1], vy.x * f[3 * i + 2]);                 // v' . S_i.
-                        }
-                        ah[r] = fmaf(kh, fmaf(-ux.y, tt[2], fmaf(ux.x, tt[1], tt[0])), ah[r]);
-                        adx[r] = fmaf(kd, fmaf(ux.y, tt[1], ux.x * tt[2]), adx[r]);
-                        ady[r] = fmaf(kd, fmaf(-ux.y, tp[2], fmaf(ux.x, tp[1], tp[0])), ady[r]);
-                    }
-                    __syncthreads();   // E cleared; the segment sums and the staging area are free
+                    ah[r] = fmaf(kh, fmaf(-ux.y, tt[2], fmaf(ux.x, tt[1], tt[0])), ah[r]);
+                    adx[r] = fmaf(kd, fmaf(ux.y, tt[1], ux.x * tt[2]), adx[r]);
+                    ady[r] = fmaf(kd, fmaf(-ux.y, tp[2], fmaf(ux.x, tp[1], tp[0])), ady[r]);
                 }
+                __syncthreads();   // E cleared; the phases may be rewritten
+                P = Pn;
             }
         }
 
-        // ---- store: the group's partial planes, or (one group) the blended maps
+        // ---- store: the item's partial plane, or (one plane) the blended maps
         const int x = tx0 + cx;
         if (x < sp.W) {
             const size_t plane = (size_t)sp.W * sp.H;
+            const int pl = g * K + part;
 #pragma unroll
-            const int pl = g * K + part;   // partial plane of this item
             for (int f = 0; f < 3; ++f) {
                 float* const dst =
                     (G * K > 1 ? p.partial + ((size_t)pl * 3 + f) * plane : p.out + (size_t)f * plane) + x;
