@@ -917,6 +917,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     const size_t cap = (size_t)D.cap;
     D.nblk_c = (int)((cap + 1023) / 1024);
     D.nblk_s = (int)((2 * cap + kSortTile - 1) / kSortTile);
+    D.nblk_o = (int)((2 * cap + kSortPassTile - 1) / kSortPassTile);
     bool ok = true;
     for (int k = 0; k < 2; ++k) {
         D.x[k] = (int32_t*)dalloc(ctx, cap * 4);
@@ -941,7 +942,12 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
         D.phase = (float2*)dalloc(ctx, (size_t)T.nb * D.phase_len * sizeof(float2));
         D.amax = (float*)dalloc(ctx, (size_t)T.nb * sizeof(float));
     }
-    D.hist = (uint32_t*)dalloc(ctx, ((size_t)256 * D.nblk_s + 256) * 4);
+    const size_t sort_words = (size_t)kMaxSortPasses * (256 + 2 + (size_t)256 * D.nblk_o);
+    D.hist = (uint32_t*)dalloc(ctx, sort_words * 4);
+    if (D.hist) {
+        D.sort_ticket = D.hist + (size_t)kMaxSortPasses * 256;
+        D.sort_status = D.sort_ticket + (size_t)kMaxSortPasses * 2;
+    }
     D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
     D.rec = (BumpRec*)dalloc(ctx, 2 * cap * sizeof(BumpRec));
     D.out = (float*)dalloc(ctx, (size_t)3 * T.W * T.H * sizeof(float));
@@ -1076,6 +1082,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     CU(cudaMemcpyAsync(D.phase, phase.data(), phase.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(D.amax, amax.data(), amax.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemsetAsync(D.flags, 0, cap, ctx->st));
+    CU(cudaMemsetAsync(D.hist, 0, sort_words * 4, ctx->st));
     CU(cudaMemsetAsync(D.stats, 0, (6 + (size_t)T.nb) * sizeof(unsigned long long), ctx->st));
     CU(cudaMemsetAsync(D.offsets, 0, ((size_t)D.total_bins + 1) * 4, ctx->st));
     CU(cudaMemsetAsync(D.out, 0, (size_t)3 * T.W * T.H * sizeof(float), ctx->st));

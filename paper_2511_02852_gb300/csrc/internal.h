@@ -8,7 +8,9 @@ namespace scwp {
 
 constexpr int kMaxBuckets = 64;
 constexpr int kRotN = 128;          // per-bucket phase-rotation table length
-constexpr int kSortTile = 1024;     // keys per block of the binning radix sort
+constexpr int kSortTile = 1024;     // keys per block of the bin-key kernel
+constexpr int kSortPassTile = 4096; // keys per block of a binning sort pass
+constexpr int kMaxSortPasses = 4;   // 8-bit digits of keys up to 32 bits
 constexpr int kMaxSegments = 2 * kMaxBuckets + 3;
 constexpr int kMaxRing = 64;        // ring-ripple particles emitted per frame at most
 constexpr int kMaxWakeRate = 64;    // wake particles per Kelvin arm per frame at most
@@ -64,8 +66,14 @@ struct PatchDev {
     float* amax = nullptr;                // [nb] bound on |A| of any bump of the bucket
     uint32_t* keys[2] = {nullptr, nullptr};  // [2 cap] bin keys (sort ping-pong)
     uint32_t* vals[2] = {nullptr, nullptr};  // [2 cap] bump ids
-    uint32_t* hist = nullptr;             // [256 * nblk_s] per-block digit counts, then [256] digit totals
-    int nblk_s = 0;
+    // binning sort scratch (all zero between sorts: each pass's last block
+    // clears its histogram and ticket, the key kernel clears the look-back
+    // words before every sort)
+    uint32_t* hist = nullptr;             // [kMaxSortPasses][256] digit totals of each pass
+    uint32_t* sort_ticket = nullptr;      // [kMaxSortPasses][2] block ticket, blocks done
+    uint32_t* sort_status = nullptr;      // [kMaxSortPasses][nblk_o][256] look-back words
+    int nblk_s = 0;                       // key-kernel blocks (kSortTile keys each)
+    int nblk_o = 0;                       // sort-pass blocks (kSortPassTile keys each)
     int key_bits = 16;
     uint32_t* offsets = nullptr;          // [total_bins + 1]
     BumpRec* rec = nullptr;               // [2 cap] bump records in bin order

@@ -3,11 +3,17 @@
 //                                            Sec. 4.1 WP updates),
 //   boundary injection and wake emission     (Sec. 3.3 Eqs. 15-17, Sec. 4.3),
 //   per-bucket integer binning               (Sec. 4.2: the particles of a
-//                                            bucket share radius and kernel).
+//                                            bucket share radius and kernel):
+//                                            a stable LSD radix sort of the bin
+//                                            keys, one launch per 8-bit digit
+//                                            (decoupled look-back for the
+//                                            blocks' digit offsets).
 // All particle state is integer (Q16.16 cell units); every decision is an
 // integer test, so the state is bit-exact against any other implementation of
 // the same rules.  No float atomics anywhere; integer atomics only for counts.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "internal.h"
@@ -19,8 +25,7 @@ namespace {
 constexpr int kTpb = 256;
 constexpr int kItems = 4;                 // per thread in the compaction tiles
 constexpr int kTileC = kTpb * kItems;     // 1024 particles per compaction block
-constexpr int kSortItems = kSortTile / kTpb;
-constexpr int kTileS = kSortTile;     // keys per sort block
+constexpr int kTileS = kSortTile;     // keys per bin-key block
 constexpr int32_t kQi = 65536, kHalfi = 32768;
 
 // Texel centres of [0, n) strictly inside (C - R, C + R) along one axis.
@@ -30,6 +35,34 @@ __device__ __forceinline__ int span_count(int32_t C, int32_t R, int n) {
     if (lo < 0) lo = 0;
     if (hi > n - 1) hi = n - 1;
     return hi >= lo ? (int)(hi - lo + 1) : 0;
+}
+
+// floor(x / d) and x - d floor(x / d) (in [0, d)) for d > 0: the quotient
+// estimated in FP32 (relative error below 2^-21, so off by at most one where
+// |x / d| < 2^19), then corrected in integers; exact integer division beyond
+// that range.
+__device__ __forceinline__ int32_t floor_divmod(int32_t x, int32_t d, int32_t& rem) {
+    const float qf = floorf(__fdividef((float)x, (float)d));
+    if (fabsf(qf) >= 524288.f) {   // 2^19: not in the estimate's range
+        int32_t q = x / d, r = x % d;
+        if (r < 0) {
+            --q;
+            r += d;
+        }
+        rem = r;
+        return q;
+    }
+    int32_t q = (int32_t)qf;
+    int64_t r = (int64_t)x - (int64_t)q * d;
+    if (r < 0) {
+        --q;
+        r += d;
+    } else if (r >= d) {
+        ++q;
+        r -= d;
+    }
+    rem = (int32_t)r;
+    return q;
 }
 
 __device__ __forceinline__ int4 lookup_vq(const PatchDev& p, uint32_t bd) {
@@ -216,18 +249,23 @@ __global__ void __launch_bounds__(kTpb) k_inject(PatchDev p, InjectParams ip) { 
 __global__ void __launch_bounds__(kTpb) k_inject_dev(PatchDev p, const InjectParams* ip) { pdl_enter(); inject_body(p, *ip); }
 
 // ---- a6: binning ---------------------------------------------------------------
-// Block b takes the particles of sort tile b (kTileS / 2 particles, two
-// bump keys each) and also produces the tile's histogram of the lowest key
-// digit: the first radix pass needs no separate histogram launch.
-__global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, uint32_t* vals) {
+// Block b takes the particles of key tile b (kTileS / 2 particles, two bump
+// keys each) and adds the tile's counts of every sort pass's digit to the
+// passes' digit totals, so the passes need no histogram launch; block b also
+// clears the look-back words of sort-pass block b.
+__global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, uint32_t* vals, int passes) {
     __shared__ unsigned long long s_ev[kTpb / 32];
     __shared__ unsigned int s_bin[kTpb / 32];
     __shared__ unsigned int s_live[kMaxBuckets];
-    __shared__ uint32_t s_h[256];
+    __shared__ uint32_t s_h[kMaxSortPasses][256];
     static_assert(kTpb == 256, "one digit counter per thread");
     pdl_enter();
     for (int i = threadIdx.x; i < p.nb; i += blockDim.x) s_live[i] = 0;
-    s_h[threadIdx.x] = 0;
+#pragma unroll
+    for (int ps = 0; ps < kMaxSortPasses; ++ps) s_h[ps][threadIdx.x] = 0;
+    if ((int)blockIdx.x < p.nblk_o)
+        for (int ps = 0; ps < passes; ++ps)
+            p.sort_status[((size_t)ps * p.nblk_o + blockIdx.x) * 256 + threadIdx.x] = 0u;
     __syncthreads();
     const int n = p.count[0];
     const int32_t* X = p.x[p.cur];
@@ -263,15 +301,17 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
             const int nx = span_count(cx, bk.R, p.W), ny = span_count(cy, bk.R, p.H);
             uint32_t key = (uint32_t)p.total_bins;
             if (nx > 0 && ny > 0) {
-                const int bx = (int)(((int64_t)cx + bk.R) / bk.C);
-                const int by = (int)(((int64_t)cy + bk.R) / bk.C);
+                // (cx + R, cy + R > 0 here: the support reaches the patch)
+                int32_t rx, ry;
+                const int bx = floor_divmod(cx + bk.R, bk.C, rx);
+                const int by = floor_divmod(cy + bk.R, bk.C, ry);
                 key = (uint32_t)(bk.base + by * bk.nbx + bx);
                 ev += (unsigned long long)nx * (unsigned long long)ny;
                 ++binned;
             }
             keys[2 * i + k] = key;
             vals[2 * i + k] = (uint32_t)(2 * i + k);
-            atomicAdd(&s_h[key & 255u], 1u);
+            for (int ps = 0; ps < passes; ++ps) atomicAdd(&s_h[ps][(key >> (8 * ps)) & 255u], 1u);
         }
     }
     // block reductions (integers: order-independent)
@@ -300,147 +340,218 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
     }
     for (int i = threadIdx.x; i < p.nb; i += blockDim.x)
         if (s_live[i]) atomicAdd(&p.stats[3 + i], (unsigned long long)s_live[i]);
-    p.hist[threadIdx.x * p.nblk_s + blockIdx.x] = s_h[threadIdx.x];   // (after the barrier above)
+    for (int ps = 0; ps < passes; ++ps)   // (after the barrier above)
+        if (s_h[ps][threadIdx.x]) atomicAdd(&p.hist[ps * 256 + threadIdx.x], s_h[ps][threadIdx.x]);
 }
 
-// LSD radix sort pass, 8-bit digit, stable.  Per-block digit histograms.
-__global__ void __launch_bounds__(kTpb) k_radix_hist(const uint32_t* keys, const int32_t* count,
-                                                     int shift, uint32_t* hist, int nblk) {
-    __shared__ uint32_t s_h[256];
-    pdl_enter();
-    s_h[threadIdx.x] = 0;
-    __syncthreads();
-    const int n = 2 * count[0];
-    const int base = blockIdx.x * kTileS;
-    uint32_t key[kSortItems];
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {   // all loads first: one round trip
-        const int i = base + k * kTpb + threadIdx.x;
-        key[k] = i < n ? keys[i] : 0xFFFFFFFFu;
-    }
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k)
-        if (base + k * kTpb + (int)threadIdx.x < n) atomicAdd(&s_h[(key[k] >> shift) & 255u], 1u);
-    __syncthreads();
-    hist[threadIdx.x * nblk + blockIdx.x] = s_h[threadIdx.x];
-}
-
-// exclusive scan of one digit's row of the digit-major histogram (block d
-// scans hist[d * nblk .. + nblk)) and that digit's total into dtot[d]; each
-// thread takes kScanItems consecutive entries per chunk, loaded together
-constexpr int kScanItems = 4;
-
-__global__ void __launch_bounds__(kTpb) k_scan_digits(uint32_t* hist, int nblk, uint32_t* dtot) {
-    __shared__ uint32_t s_warp[kTpb / 32];
-    pdl_enter();
-    uint32_t* row = hist + (size_t)blockIdx.x * nblk;
+// ---- one LSD radix-sort pass (8-bit digit, stable) -----------------------------
+// Block-wide exclusive scan of one value per thread (kTpb threads); one
+// barrier inside, s_warp free on entry.
+__device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t carry = 0;
-    for (int start = 0; start < nblk; start += kTpb * kScanItems) {
-        const int i0 = start + threadIdx.x * kScanItems;
-        uint32_t v[kScanItems];
-        uint32_t sum = 0;
+    uint32_t x = v;
 #pragma unroll
-        for (int q = 0; q < kScanItems; ++q) {
-            v[q] = i0 + q < nblk ? row[i0 + q] : 0u;
-            sum += v[q];
-        }
-        uint32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+    for (int w = 0; w < kTpb / 32; ++w)
+        if (w < warp) before += s_warp[w];
+    return before + x - v;
+}
+
+constexpr int kPassItems = kSortPassTile / kTpb;   // keys per thread
+static_assert(kSortPassTile <= 65536, "tile ranks kept in 16 bits");
+constexpr int kPassWarpKeys = 32 * kPassItems;     // keys per warp: a contiguous run of the tile
+// look-back word: flag in the top two bits, a count below
+constexpr uint32_t kLbAggregate = 1u << 30, kLbPrefix = 2u << 30, kLbCount = (1u << 30) - 1u;
+constexpr long long kLbWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+constexpr int kLbBatch = 8;                        // look-back words read per round trip
+// A look-back word carries its flag and count together, so plain relaxed
+// accesses (atomic per word, no ordering against other data) suffice, and
+// the loads of one batch overlap.
+__device__ __forceinline__ void st_relaxed(uint32_t* a, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* a) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a));
+    return v;
+}
+
+// One pass: a persistent grid whose blocks take tiles of kSortPassTile keys
+// in ticket order.  A block ranks a tile's keys by digit (warp w holds the
+// tile's keys [512 w, 512 w + 512) in order, so ranks follow the input
+// order), publishes the tile's digit counts, and finds for each digit the
+// keys of that digit in the earlier tiles by looking back over their
+// published words (an inclusive prefix ends the walk) — the single-pass scan
+// with decoupled look-back of Merrill and Garland.  Output position of a key:
+// keys of smaller digits (the pass's digit totals, counted by the key kernel)
+// + keys of its digit in earlier tiles + its rank in the tile.  The tile is
+// reordered in shared memory first, so each digit's run leaves as
+// consecutive stores.  A block only ever waits on tiles with earlier
+// tickets, which running blocks hold or finished; every wait is bounded (the
+// error flag records a timeout).  The last block to finish clears the pass's
+// digit totals and ticket for the next sort.
+__global__ void __launch_bounds__(kTpb, 3) k_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                                                    uint32_t* vout, const int32_t* count, int shift,
+                                                    uint32_t* dtot, uint32_t* status, uint32_t* ticket,
+                                                    unsigned long long* err) {
+    __shared__ uint32_t s_k[kSortPassTile];
+    __shared__ uint32_t s_v[kSortPassTile];
+    __shared__ uint32_t s_wh[kTpb / 32][256];   // per-warp digit counts, then the warp's offset in the digit
+    __shared__ uint32_t s_ls[256];              // the digit's first position in the reordered tile
+    __shared__ uint32_t s_gb[256];              // output position of reordered tile position 0 of the digit
+    __shared__ uint32_t s_warp[kTpb / 32];
+    __shared__ int s_bid;
+    __shared__ bool s_last;
+    pdl_enter();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = 2 * count[0];
+    const uint32_t gd = block_exscan256(dtot[tid], s_warp);   // keys of smaller digits, all tiles
+    const uint32_t lt = (1u << lane) - 1u;
+    for (;;) {
+        if (tid == 0) s_bid = (int)atomicAdd(ticket, 1u);
+#pragma unroll
+        for (int w = 0; w < kTpb / 32; ++w) s_wh[w][tid] = 0u;
+        __syncthreads();   // (also: the previous tile's shared data is no longer read)
+        const int bid = s_bid;
+        const int base = bid * kSortPassTile;
+        if (base >= n) break;   // (uniform)
+        const int i0 = base + warp * kPassWarpKeys + lane;
+        uint32_t kk[kPassItems], vv[kPassItems], rk[kPassItems / 2];   // ranks (< 4096): two per word
+#pragma unroll
+        for (int k = 0; k < kPassItems / 2; ++k) rk[k] = 0u;
+#pragma unroll
+        for (int k = 0; k < kPassItems; ++k) {   // every load first
+            const int i = i0 + 32 * k;
+            kk[k] = i < n ? kin[i] : 0u;
+            vv[k] = i < n ? vin[i] : 0u;
         }
-        if (lane == 31) s_warp[warp] = x;
+#pragma unroll
+        for (int k = 0; k < kPassItems; ++k) {
+            const bool act = i0 + 32 * k < n;
+            const uint32_t d = act ? (kk[k] >> shift) & 255u : 256u + (uint32_t)lane;   // inactive: alone
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t r = __popc(peers & lt);
+            const uint32_t before = act ? s_wh[warp][d] : 0u;
+            rk[k / 2] |= (before + r) << (16 * (k & 1));
+            __syncwarp();
+            if (act && r == 0) s_wh[warp][d] = before + __popc(peers);
+            __syncwarp();
+        }
         __syncthreads();
-        uint32_t before = 0, all = 0;
+        // digit tid: each warp's offset within the tile's keys of the digit
+        uint32_t c = 0;
 #pragma unroll
         for (int w = 0; w < kTpb / 32; ++w) {
-            const uint32_t t = s_warp[w];
-            if (w < warp) before += t;
-            all += t;
+            const uint32_t x = s_wh[w][tid];
+            s_wh[w][tid] = c;
+            c += x;
         }
-        uint32_t run = carry + before + x - sum;
+        // keys of digit tid in the earlier tiles: walk back over their words,
+        // kLbBatch at a time, summing aggregates up to the nearest inclusive
+        // prefix; an unpublished word ends the batch and is read again
+        uint32_t excl = 0;
+        uint32_t* mine = status + (size_t)bid * 256 + tid;
+        if (bid == 0) {
+            st_relaxed(mine, kLbPrefix | c);
+        } else {
+            st_relaxed(mine, kLbAggregate | c);
+            const long long t0 = clock64();
+            int j = bid - 1;   // the nearest word not yet summed
+            for (;;) {
+                uint32_t w[kLbBatch];
 #pragma unroll
-        for (int q = 0; q < kScanItems; ++q) {
-            if (i0 + q < nblk) row[i0 + q] = run;
-            run += v[q];
+                for (int q = 0; q < kLbBatch; ++q)
+                    w[q] = j - q >= 0 ? ld_relaxed(status + (size_t)(j - q) * 256 + tid) : kLbPrefix;
+                bool done = false, stalled = false;
+#pragma unroll
+                for (int q = 0; q < kLbBatch; ++q) {
+                    if (done || stalled) continue;
+                    const uint32_t f = w[q] & ~kLbCount;
+                    if (f == 0u) {
+                        stalled = true;   // not yet published: read again from here
+                    } else {
+                        excl += w[q] & kLbCount;
+                        --j;
+                        done = f == kLbPrefix;
+                    }
+                }
+                if (done) break;
+                if (stalled && clock64() - t0 > kLbWaitCycles) {
+                    atomicOr(err, (unsigned long long)kErrTimeout);
+                    break;
+                }
+            }
+            st_relaxed(mine, kLbPrefix | (excl + c));
         }
-        carry += all;
+        const uint32_t ls = block_exscan256(c, s_warp);   // (its barrier orders s_wh above)
+        s_ls[tid] = ls;
+        s_gb[tid] = gd + excl - ls;
         __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPassItems; ++k) {
+            if (i0 + 32 * k < n) {
+                const uint32_t d = (kk[k] >> shift) & 255u;
+                const uint32_t pos = s_ls[d] + s_wh[warp][d] + ((rk[k / 2] >> (16 * (k & 1))) & 0xFFFFu);
+                s_k[pos] = kk[k];
+                s_v[pos] = vv[k];
+            }
+        }
+        __syncthreads();
+        const int m = min(kSortPassTile, n - base);
+        for (int i = tid; i < m; i += kTpb) {
+            const uint32_t key = s_k[i];
+            const uint32_t o = s_gb[(key >> shift) & 255u] + (uint32_t)i;
+            kout[o] = key;
+            vout[o] = s_v[i];
+        }
     }
-    if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
+    // the last block out (every block has read the digit totals by then)
+    // clears them and the ticket
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        dtot[tid] = 0u;
+        if (tid == 0) {
+            ticket[0] = 0u;
+            ticket[1] = 0u;
+        }
+        __threadfence();
+    }
 }
 
-// stable scatter of one sort block's keys by digit: base of digit d = keys
-// of smaller digits (exclusive scan of the 256 digit totals) + keys of
-// digit d in earlier blocks (the scanned row)
-__global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, const uint32_t* vin,
-                                                        uint32_t* kout, uint32_t* vout,
-                                                        const int32_t* count, int shift,
-                                                        const uint32_t* hist, const uint32_t* dtot,
-                                                        int nblk) {
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_wc[kTpb / 32][256];
-    __shared__ uint32_t s_dw[kTpb / 32];
-    pdl_enter();
-    const int n = 2 * count[0];
-    const int base = blockIdx.x * kTileS;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // every load of the block first (one round trip): the tile's keys and
-    // ids, this digit's total and its count in the earlier tiles
-    uint32_t kk[kSortItems], vv[kSortItems];
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const int i = base + k * kTpb + threadIdx.x;
-        kk[k] = i < n ? kin[i] : 0u;
-        vv[k] = i < n ? vin[i] : 0u;
-    }
-    const uint32_t h_before = hist[threadIdx.x * nblk + blockIdx.x];
-    {
-        // exclusive scan of the digit totals (one digit per thread)
-        const uint32_t v = dtot[threadIdx.x];
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+int sort_pass_blocks_per_sm() {
+    static int cache[kMaxCachedDevices];
+    return cached_per_device(cache, [] {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sort_pass, kTpb, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
         }
-        if (lane == 31) s_dw[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-#pragma unroll
-        for (int w = 0; w < kTpb / 32; ++w)
-            if (w < warp) before += s_dw[w];
-        s_base[threadIdx.x] = before + x - v + h_before;
-    }
-    const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const int i = base + k * kTpb + threadIdx.x;
-        const bool act = i < n;
-        const uint32_t key = kk[k], val = vv[k];
-        const uint32_t d = act ? (key >> shift) & 255u : 0x100u + (uint32_t)warp;  // inactive sentinel
-#pragma unroll
-        for (int w = 0; w < kTpb / 32; ++w) s_wc[w][threadIdx.x] = 0;
-        __syncthreads();
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (act && rank == 0) s_wc[warp][d] = __popc(peers);
-        __syncthreads();
-        if (act) {
-            uint32_t off = s_base[d] + rank;
-            for (int w = 0; w < warp; ++w) off += s_wc[w][d];
-            kout[off] = key;
-            vout[off] = val;
+        return nb > 0 ? nb : -1;
+    });
+}
+
+int sm_count() {
+    static int cache[kMaxCachedDevices];
+    return cached_per_device(cache, [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
         }
-        __syncthreads();
-        // (the next chunk reads s_base only after its first barrier)
-        uint32_t add = 0;
-#pragma unroll
-        for (int w = 0; w < kTpb / 32; ++w) add += s_wc[w][threadIdx.x];
-        s_base[threadIdx.x] += add;
-    }
+        return n > 0 ? n : -1;
+    });
 }
 
 // One pass over the sorted (key, bump id) pairs:
@@ -450,45 +561,70 @@ __global__ void __launch_bounds__(kTpb) k_radix_scatter(const uint32_t* kin, con
 //  * the bump records in bin order (X, Y, signed amplitude, id and the
 //    kernel phase pairs) of the entries with a bin (key < total_bins; the
 //    others sort last).
-__global__ void k_offsets_records(PatchDev p, const uint32_t* keys, const uint32_t* vals) {
+constexpr int kRecItems = 4;   // sorted entries per thread and round, loads issued together
+
+__global__ void __launch_bounds__(kTpb) k_offsets_records(PatchDev p, const uint32_t* keys, const uint32_t* vals) {
     pdl_enter();
     const int n = 2 * p.count[0];
     const int32_t* X = p.x[p.cur];
     const int32_t* Y = p.y[p.cur];
     const uint32_t* BD = p.bd[p.cur];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n; e += gridDim.x * blockDim.x) {
-        const uint32_t key = e < n ? keys[e] : (uint32_t)p.total_bins;
-        const int lo = e == 0 ? 0 : (int)keys[e - 1] + 1;
-        const int hi = e == n ? p.total_bins : min((int)key, p.total_bins);
-        for (int k = lo; k <= hi; ++k) p.offsets[k] = (uint32_t)e;
-        if (e == n || key >= (uint32_t)p.total_bins) continue;
-        const uint32_t id = vals[e];
-        const int i = (int)(id >> 1);
-        const bool trough = id & 1u;
-        const uint32_t bd = BD[i];
-        const int4 vq = lookup_vq(p, bd);
-        const float A = lookup_amp(p, bd);
-        const int32_t R = p.bk[bd >> 16].R;
-        BumpRec r;
-        r.x = trough ? X[i] - vq.z : X[i];
-        r.y = trough ? Y[i] - vq.w : Y[i];
-        r.amp = trough ? -A : A;
-        r.id = id;
-        // e^{-i pi (x mod 2R)/R}: exact integer reduction (2R < 2^31), then
-        // sincospi of the FP32 quotient (within a few ulp of the exact one)
-        const int32_t R2 = 2 * R;
-        int32_t xm = r.x % R2, ym = r.y % R2;
-        if (xm < 0) xm += R2;
-        if (ym < 0) ym += R2;
-        const float invR = p.bk[bd >> 16].invR;
-        float sn, cs;
-        sincospif((float)xm * invR, &sn, &cs);
-        r.cx = cs;
-        r.sx = -sn;
-        sincospif((float)ym * invR, &sn, &cs);
-        r.cy = cs;
-        r.sy = -sn;
-        p.rec[e] = r;
+    const uint32_t tb = (uint32_t)p.total_bins;
+    const int stride = gridDim.x * kTpb * kRecItems;
+    for (int e0 = blockIdx.x * kTpb * kRecItems + threadIdx.x; e0 <= n; e0 += stride) {
+        uint32_t key[kRecItems], prev[kRecItems], id[kRecItems];
+#pragma unroll
+        for (int q = 0; q < kRecItems; ++q) {
+            const int e = e0 + q * kTpb;
+            key[q] = e < n ? keys[e] : tb;
+            prev[q] = (e > 0 && e <= n) ? keys[e - 1] : 0u;
+            id[q] = e < n ? vals[e] : 0u;
+        }
+        int32_t xs[kRecItems], ys[kRecItems];
+        uint32_t bds[kRecItems];
+#pragma unroll
+        for (int q = 0; q < kRecItems; ++q) {   // the particles' state: every gather first
+            const int e = e0 + q * kTpb;
+            const int i = (int)(id[q] >> 1);
+            const bool ok = e < n && key[q] < tb;
+            xs[q] = ok ? X[i] : 0;
+            ys[q] = ok ? Y[i] : 0;
+            bds[q] = ok ? BD[i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kRecItems; ++q) {
+            const int e = e0 + q * kTpb;
+            if (e > n) continue;
+            const int lo = e == 0 ? 0 : (int)prev[q] + 1;
+            const int hi = e == n ? p.total_bins : min((int)key[q], p.total_bins);
+            for (int k = lo; k <= hi; ++k) p.offsets[k] = (uint32_t)e;
+            if (e == n || key[q] >= tb) continue;
+            const uint32_t bd = bds[q];
+            const bool trough = id[q] & 1u;
+            const int4 vq = lookup_vq(p, bd);
+            const float A = lookup_amp(p, bd);
+            const BucketDev& bk = p.bk[bd >> 16];
+            BumpRec r;
+            r.x = trough ? xs[q] - vq.z : xs[q];
+            r.y = trough ? ys[q] - vq.w : ys[q];
+            r.amp = trough ? -A : A;
+            r.id = id[q];
+            // e^{-i pi (x mod 2R)/R}: exact integer reduction (2R < 2^31), then
+            // sincospi of the FP32 quotient (within a few ulp of the exact one)
+            const int32_t R2 = 2 * bk.R;
+            int32_t xm, ym;
+            floor_divmod(r.x, R2, xm);
+            floor_divmod(r.y, R2, ym);
+            const float invR = bk.invR;
+            float sn, cs;
+            sincospif((float)xm * invR, &sn, &cs);
+            r.cx = cs;
+            r.sx = -sn;
+            sincospif((float)ym * invR, &sn, &cs);
+            r.cy = cs;
+            r.sy = -sn;
+            p.rec[e] = r;
+        }
     }
 }
 
@@ -523,30 +659,26 @@ cudaError_t launch_inject_dev(const PatchDev& p, const InjectParams* ip, cudaStr
 }
 
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
-    // one block per sort tile: keys, vals and the first digit's histograms
-    cudaError_t e = launch_pdl(k_bin_keys, p.nblk_s, kTpb, 0, st, p, p.keys[0], p.vals[0]);
+    // one block per key tile: keys, ids and every pass's digit totals
     const int passes = (p.key_bits + 7) / 8;
+    // the sort passes: a persistent grid of the blocks that fit at once
+    const int per_sm = sort_pass_blocks_per_sm(), sms = sm_count();
+    const int grid = std::max(1, std::min(p.nblk_o, std::max(1, per_sm) * std::max(1, sms)));
+    cudaError_t e = launch_pdl(k_bin_keys, p.nblk_s, kTpb, 0, st, p, p.keys[0], p.vals[0], passes);
     int src = 0;
-    uint32_t* dtot = p.hist + (size_t)256 * p.nblk_s;
     for (int ps = 0; ps < passes && e == cudaSuccess; ++ps) {
-        const int shift = 8 * ps;
-        if (ps > 0)
-            e = launch_pdl(k_radix_hist, p.nblk_s, kTpb, 0, st, (const uint32_t*)p.keys[src],
-                           (const int32_t*)p.count, shift, p.hist, p.nblk_s);
-        if (e == cudaSuccess) e = launch_pdl(k_scan_digits, 256, kTpb, 0, st, p.hist, p.nblk_s, dtot);
-        if (e == cudaSuccess)
-            e = launch_pdl(k_radix_scatter, p.nblk_s, kTpb, 0, st, (const uint32_t*)p.keys[src],
-                           (const uint32_t*)p.vals[src], p.keys[1 - src], p.vals[1 - src],
-                           (const int32_t*)p.count, shift, (const uint32_t*)p.hist, (const uint32_t*)dtot,
-                           p.nblk_s);
+        e = launch_pdl(k_sort_pass, grid, kTpb, 0, st, (const uint32_t*)p.keys[src],
+                       (const uint32_t*)p.vals[src], p.keys[1 - src], p.vals[1 - src], (const int32_t*)p.count,
+                       8 * ps, p.hist + 256 * ps, p.sort_status + (size_t)ps * p.nblk_o * 256,
+                       p.sort_ticket + 2 * ps, p.stats + 2);
         src = 1 - src;
     }
-    int rb = (2 * p.cap + 1 + kTpb - 1) / kTpb;
-    if (rb > 152 * 16) rb = 152 * 16;
+    int rb = (2 * p.cap + 1 + kTpb * kRecItems - 1) / (kTpb * kRecItems);
+    rb = std::max(1, std::min(rb, std::max(1, sm_count()) * 8));
     if (e == cudaSuccess)
         e = launch_pdl(k_offsets_records, rb, kTpb, 0, st, p, (const uint32_t*)p.keys[src],
                        (const uint32_t*)p.vals[src]);
-    count_launches(1 + 3 * passes);
+    count_launches(2 + passes);
     return e;
 }
 
