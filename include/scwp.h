@@ -285,6 +285,19 @@ scwp_status scwp_set_particles(scwp_ctx* ctx, int32_t patch_id, const int32_t* x
 scwp_status scwp_get_bins(scwp_ctx* ctx, int32_t patch_id, uint32_t* counts, uint32_t* offsets,
                           uint32_t* entries, int64_t entries_cap, int64_t* n_entries);
 
+/* Failure-detection self-test of the bounded device waits (the paper has no
+ * counterpart: its binning is not described at this level).  Recomputes the
+ * bin keys of the patch's live particles and runs the first pass of the
+ * binning sort with the look-back word of its first key tile never
+ * published, so that every wait on that word runs out after wait_seconds
+ * (0 < wait_seconds <= 2) of SM clock; no kernel faults, traps or hangs.
+ * Needs at least 2049 live particles in the patch (two sort tiles of 4096
+ * bump keys), else SCWP_E_INVALID.  Returns SCWP_E_TIMEOUT when the kernel
+ * reported the timeout, as a frame would; the context is then sticky
+ * (every later call returns SCWP_E_TIMEOUT) and must be destroyed, while the
+ * CUDA context and every other scwp context stay usable.  Synchronises. */
+scwp_status scwp_debug_sort_timeout(scwp_ctx* ctx, int32_t patch_id, double wait_seconds);
+
 /* Recompute the synthesis and blend of every patch from the current
  * particles and background without advancing the frame (the bins are
  * rebuilt).  mode: any SCWP_SYNTH_* (SCWP_SYNTH_SAT, the default path of

@@ -1964,6 +1964,30 @@ scwp_status scwp_get_bins(scwp_ctx* ctx, int32_t patch_id, uint32_t* counts, uin
     return SCWP_OK;
 }
 
+scwp_status scwp_debug_sort_timeout(scwp_ctx* ctx, int32_t patch_id, double wait_seconds) {
+    scwp_status s = ready(ctx);
+    if (s != SCWP_OK) return s;
+    if (patch_id < 0 || patch_id >= (int)ctx->patches.size() || !(wait_seconds > 0.0) || wait_seconds > 2.0)
+        return fail(ctx, SCWP_E_INVALID, "args");
+    PatchHost* P = ctx->patches[patch_id];
+    int32_t cnt = 0;
+    CU(cudaMemcpyAsync(&cnt, P->dev.count, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    // at least two sort tiles of bump keys: tile 1 then looks back to tile 0
+    if (2 * (int64_t)cnt <= kSortPassTile) return fail(ctx, SCWP_E_INVALID, "too few particles for two sort tiles");
+    int dev = 0, khz = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const long long cycles = (long long)(wait_seconds * 1e3 * (double)(khz > 0 ? khz : 2070000));
+    graph_reset(ctx);
+    CU(launch_sort_stall(P->dev, cycles, ctx->st));
+    unsigned long long flags = 0;
+    CU(cudaMemcpyAsync(&flags, P->dev.stats + 2, sizeof(flags), cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    if (flags & kErrTimeout) return fail(ctx, SCWP_E_TIMEOUT, "a device wait timed out (sort look-back self-test)");
+    return fail(ctx, SCWP_E_STATE, "the sort look-back self-test did not time out");
+}
+
 scwp_status scwp_set_timing(scwp_ctx* ctx, int32_t enable) {
     scwp_status s = ready(ctx);
     if (s != SCWP_OK) return s;

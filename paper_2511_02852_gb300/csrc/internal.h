@@ -207,6 +207,10 @@ cudaError_t launch_inject(const PatchDev& p, const InjectParams& ip, cudaStream_
 // grid, so that the launch can be replayed from a CUDA graph)
 cudaError_t launch_inject_dev(const PatchDev& p, const InjectParams* ip, cudaStream_t st);
 cudaError_t launch_bin(const PatchDev& p, cudaStream_t st);
+// failure-detection self-test: the bin keys, then the first sort pass with
+// its first tile never taken, so the look-back waits on it give up after
+// wait_cycles SM clocks and set the timeout flag (outputs meaningless)
+cudaError_t launch_sort_stall(const PatchDev& p, long long wait_cycles, cudaStream_t st);
 cudaError_t launch_synth_gather(const PatchDev& p, const SynthParams& sp, cudaStream_t st);
 // Tensor-core synthesis of `n_items` items (any patches) in one launch, then
 // the group-sum blend of `n_spans` spans in one launch.  `pdevs` and `sps`

@@ -369,7 +369,7 @@ static_assert(kSortPassTile <= 65536, "tile ranks kept in 16 bits");
 constexpr int kPassWarpKeys = 32 * kPassItems;     // keys per warp: a contiguous run of the tile
 // look-back word: flag in the top two bits, a count below
 constexpr uint32_t kLbAggregate = 1u << 30, kLbPrefix = 2u << 30, kLbCount = (1u << 30) - 1u;
-constexpr long long kLbWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+constexpr long long kLbWaitCycles = 2000000000ll;  // the frame's limit: ~1 s at 2 GHz
 
 constexpr int kLbBatch = 8;                        // look-back words read per round trip
 // A look-back word carries its flag and count together, so plain relaxed
@@ -396,12 +396,18 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* a) {
 // reordered in shared memory first, so each digit's run leaves as
 // consecutive stores.  A block only ever waits on tiles with earlier
 // tickets, which running blocks hold or finished; every wait is bounded (the
-// error flag records a timeout).  The last block to finish clears the pass's
-// digit totals and ticket for the next sort.
+// error flag records a timeout, after wait_cycles SM clocks).  The last block
+// to finish clears the pass's digit totals and ticket for the next sort.
+// Tickets start at tile first_tile: 0 in every frame; the failure-detection
+// self-test starts at 1, so that tile 0's word is never published and the
+// waits on it run out.  A block that gave up has summed a subset of the
+// earlier tiles' counts, so its output positions stay below the true ones
+// (in bounds, though the order is then wrong).
 __global__ void __launch_bounds__(kTpb, 3) k_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
                                                     uint32_t* vout, const int32_t* count, int shift,
                                                     uint32_t* dtot, uint32_t* status, uint32_t* ticket,
-                                                    unsigned long long* err) {
+                                                    unsigned long long* err, long long wait_cycles,
+                                                    int first_tile) {
     __shared__ uint32_t s_k[kSortPassTile];
     __shared__ uint32_t s_v[kSortPassTile];
     __shared__ uint32_t s_wh[kTpb / 32][256];   // per-warp digit counts, then the warp's offset in the digit
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(kTpb, 3) k_sort_pass(const uint32_t* kin, cons
     const uint32_t gd = block_exscan256(dtot[tid], s_warp);   // keys of smaller digits, all tiles
     const uint32_t lt = (1u << lane) - 1u;
     for (;;) {
-        if (tid == 0) s_bid = (int)atomicAdd(ticket, 1u);
+        if (tid == 0) s_bid = (int)atomicAdd(ticket, 1u) + first_tile;
 #pragma unroll
         for (int w = 0; w < kTpb / 32; ++w) s_wh[w][tid] = 0u;
         __syncthreads();   // (also: the previous tile's shared data is no longer read)
@@ -484,7 +490,7 @@ __global__ void __launch_bounds__(kTpb, 3) k_sort_pass(const uint32_t* kin, cons
                     }
                 }
                 if (done) break;
-                if (stalled && clock64() - t0 > kLbWaitCycles) {
+                if (stalled && clock64() - t0 > wait_cycles) {
                     atomicOr(err, (unsigned long long)kErrTimeout);
                     break;
                 }
@@ -670,7 +676,7 @@ cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
         e = launch_pdl(k_sort_pass, grid, kTpb, 0, st, (const uint32_t*)p.keys[src],
                        (const uint32_t*)p.vals[src], p.keys[1 - src], p.vals[1 - src], (const int32_t*)p.count,
                        8 * ps, p.hist + 256 * ps, p.sort_status + (size_t)ps * p.nblk_o * 256,
-                       p.sort_ticket + 2 * ps, p.stats + 2);
+                       p.sort_ticket + 2 * ps, p.stats + 2, kLbWaitCycles, 0);
         src = 1 - src;
     }
     int rb = (2 * p.cap + 1 + kTpb * kRecItems - 1) / (kTpb * kRecItems);
@@ -683,5 +689,20 @@ cudaError_t launch_bin(const PatchDev& p, cudaStream_t st) {
 }
 
 int sorted_buffer_index(const PatchDev& p) { return ((p.key_bits + 7) / 8) & 1; }
+
+cudaError_t launch_sort_stall(const PatchDev& p, long long wait_cycles, cudaStream_t st) {
+    // the frame's keys and digit totals, then the first pass with tile 0
+    // never taken: every block that looks back to it waits wait_cycles
+    const int passes = (p.key_bits + 7) / 8;
+    const int per_sm = sort_pass_blocks_per_sm(), sms = sm_count();
+    const int grid = std::max(1, std::min(p.nblk_o, std::max(1, per_sm) * std::max(1, sms)));
+    cudaError_t e = launch_pdl(k_bin_keys, p.nblk_s, kTpb, 0, st, p, p.keys[0], p.vals[0], passes);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_sort_pass, grid, kTpb, 0, st, (const uint32_t*)p.keys[0], (const uint32_t*)p.vals[0],
+                       p.keys[1], p.vals[1], (const int32_t*)p.count, 0, p.hist, p.sort_status, p.sort_ticket,
+                       p.stats + 2, wait_cycles, 1);
+    count_launches(2);
+    return e;
+}
 
 }  // namespace scwp

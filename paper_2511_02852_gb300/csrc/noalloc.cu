@@ -72,8 +72,8 @@ extern "C" scwp_status scwp_background_noalloc(const float* h0, const float* ome
                                                void* stream) {
     if (!h0 || !omega || !out || !(fft_L > 0)) return SCWP_E_INVALID;
     if (n < 8 || n > kNoAllocMaxN || (n & (n - 1)) != 0) return SCWP_E_INVALID;
-    // h0 is read as 8-byte complex pairs and omega as doubles: an address off
-    // that alignment would fault the kernel, so it is refused here
+    // h0 and omega are read as 8-byte float pairs: an address off that
+    // alignment would fault the kernel, so it is refused here
     if ((((uintptr_t)h0 | (uintptr_t)omega) & 7u) != 0 || ((uintptr_t)out & 3u) != 0) return SCWP_E_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

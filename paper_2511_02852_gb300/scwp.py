@@ -117,6 +117,7 @@ EXPORTS = {
                                      C.c_int64]),
     "scwp_get_bins": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_int64, C.POINTER(C.c_int64)]),
+    "scwp_debug_sort_timeout": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
     "scwp_resynthesize": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_synth_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "scwp_set_batched": (C.c_int, [C.c_void_p, C.c_int32]),
