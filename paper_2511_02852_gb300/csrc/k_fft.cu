@@ -61,9 +61,6 @@ __host__ __device__ constexpr int tstride() { return padded<N>() + ((18 - padded
 // columns per column-pass CTA for h + i Dx (twice as many for Dy, in pairs)
 template <int N>
 __host__ __device__ constexpr int col_group() { return N >= 2048 ? 4 : N >= 1024 ? 8 : N >= 32 ? 16 : N / 2; }
-// the radix of the last stage: N = 16^a r, r in {1, 2, 4, 8}
-template <int N>
-__host__ __device__ constexpr int last_radix() { return N < 16 ? N : last_radix<N / 16>(); }
 
 
 // e^{+2 pi i k / 16}, k = 0 .. 7 (the roots the 16-point transform uses)
@@ -112,13 +109,50 @@ __device__ __forceinline__ void dft_inv(float2 (&v)[R]) {
     for (int i = 0; i < R; ++i) v[i] = u[i];
 }
 
+// Multiply v[r] by the twiddle e^{2 pi i r m / N}, r = 1 .. R - 1, of one
+// butterfly (m = k step): e^{2 pi i m / N} to the powers 1, 2, 4, 8 come
+// from the table (one load each), the others are products of two or three
+// of them (at most three roundings, within 3e-7 of the table values), so a
+// radix-16 butterfly loads 4 twiddles instead of 15.
+template <int R>
+__device__ __forceinline__ void apply_twiddles(float2 (&v)[R], int m, const float2* __restrict__ tw) {
+    const float2 w1 = __ldg(&tw[m]);
+    v[1] = cmul(v[1], w1);
+    if constexpr (R >= 4) {
+        const float2 w2 = __ldg(&tw[2 * m]);
+        const float2 w3 = cmul(w1, w2);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        if constexpr (R >= 8) {
+            const float2 w4 = __ldg(&tw[4 * m]);
+            const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+            v[4] = cmul(v[4], w4);
+            v[5] = cmul(v[5], w5);
+            v[6] = cmul(v[6], w6);
+            v[7] = cmul(v[7], w7);
+            if constexpr (R >= 16) {
+                const float2 w8 = __ldg(&tw[8 * m]);
+                v[8] = cmul(v[8], w8);
+                v[9] = cmul(v[9], cmul(w1, w8));
+                v[10] = cmul(v[10], cmul(w2, w8));
+                v[11] = cmul(v[11], cmul(w3, w8));
+                v[12] = cmul(v[12], cmul(w4, w8));
+                v[13] = cmul(v[13], cmul(w5, w8));
+                v[14] = cmul(v[14], cmul(w6, w8));
+                v[15] = cmul(v[15], cmul(w7, w8));
+            }
+        }
+    }
+}
+
 // One Stockham stage of radix R over the transforms of a block: thread jt
 // (0 <= jt < P = N / 16) of transform `buf` does the 16 / R butterflies
 // j = jt + q P.  Butterfly j (span Ns): k = j mod Ns; inputs x[j + r N/R]
 // times e^{2 pi i r k / (Ns R)}, an R-point transform, outputs at
 // (j - k) R + k + s Ns.  All loads come before the barrier, all stores after.
-template <int N, int R>
-__device__ __forceinline__ void stage(float2* buf, int jt, int Ns, const float2* __restrict__ tw) {
+// The first stage (Ns = 1) has no twiddles.
+template <int N, int R, int Ns>
+__device__ __forceinline__ void stage(float2* buf, int jt, const float2* __restrict__ tw) {
     constexpr int P = threads_per_transform<N>();
     constexpr int B = (N >= 16 ? 16 : N) / R;   // butterflies per thread
     float2 v[B][R];
@@ -131,9 +165,7 @@ __device__ __forceinline__ void stage(float2* buf, int jt, int Ns, const float2*
     for (int q = 0; q < B; ++q) {
         const int j = jt + q * P;
         const int k = j & (Ns - 1);
-        const int step = N / (Ns * R);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], __ldg(&tw[r * k * step]));
+        if constexpr (Ns > 1) apply_twiddles<R>(v[q], k * (N / (Ns * R)), tw);
         dft_inv<R>(v[q]);
         const int d = (j - k) * R + k;
 #pragma unroll
@@ -142,25 +174,24 @@ __device__ __forceinline__ void stage(float2* buf, int jt, int Ns, const float2*
     __syncthreads();
 }
 
+// the stages of a length-N inverse transform: radix 16 while 16 divides the
+// rest, then one stage of radix 8, 4 or 2
+template <int N, int Ns>
+__device__ __forceinline__ void stages_from(float2* buf, int jt, const float2* __restrict__ tw) {
+    if constexpr (N / Ns >= 16) {
+        stage<N, 16, Ns>(buf, jt, tw);
+        stages_from<N, Ns * 16>(buf, jt, tw);
+    } else if constexpr (N / Ns > 1) {
+        stage<N, N / Ns, Ns>(buf, jt, tw);
+    }
+}
+
 // Inverse FFT of length N of the transform in `buf` (padded layout) by the
 // P = N / 16 threads jt of it (every thread of the block takes part in the
 // barriers).
 template <int N>
 __device__ __forceinline__ void fft_inv(float2* buf, int jt, const float2* __restrict__ tw) {
-    if constexpr (N <= 16) {
-        stage<N, N>(buf, jt, 1, tw);
-    } else {
-        int Ns = 1;
-#pragma unroll
-        for (int rem = N; rem >= 16; rem /= 16) {
-            stage<N, 16>(buf, jt, Ns, tw);
-            Ns *= 16;
-        }
-        constexpr int last = last_radix<N>();
-        if constexpr (last == 8) stage<N, 8>(buf, jt, Ns, tw);
-        if constexpr (last == 4) stage<N, 4>(buf, jt, Ns, tw);
-        if constexpr (last == 2) stage<N, 2>(buf, jt, Ns, tw);
-    }
+    stages_from<N, 1>(buf, jt, tw);
 }
 
 
@@ -180,7 +211,7 @@ __device__ __forceinline__ float phase(float2 w, float th, float tl) {
 // f = tid / P.  h0 is [N][N] (FFT-natural order), omega [N][N] float pairs
 // (hi, lo); I is [3][N/2 + 1][N].
 template <int N>
-__global__ void __launch_bounds__(3 * threads_per_transform<N>(), N >= 1024 ? 3 : 1)
+__global__ void __launch_bounds__(3 * threads_per_transform<N>(), N >= 4096 ? 1 : N >= 1024 ? 3 : 1)
     k_spectrum_rows(BgDev bg, float th, float tl, const float2* t_dev) {
     constexpr int P = threads_per_transform<N>(), Np = tstride<N>();
     constexpr int NT = 3 * P, E = (N + NT - 1) / NT;   // grid points per thread
