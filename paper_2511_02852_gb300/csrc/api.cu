@@ -950,6 +950,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     }
     D.offsets = (uint32_t*)dalloc(ctx, ((size_t)D.total_bins + 1) * 4);
     D.rec = (BumpRec*)dalloc(ctx, 2 * cap * sizeof(BumpRec));
+    D.pk = (int4*)dalloc(ctx, cap * sizeof(int4));
     D.out = (float*)dalloc(ctx, (size_t)3 * T.W * T.H * sizeof(float));
     {
         // split the synthesis into bucket groups so that a frame has enough
@@ -1008,7 +1009,7 @@ scwp_status scwp_add_patch(scwp_ctx* ctx, const scwp_patch_desc* desc, int32_t* 
     }
     D.stats = (unsigned long long*)dalloc(ctx, (6 + (size_t)T.nb) * sizeof(unsigned long long));
     ok = ok && D.count && D.flags && D.blk && D.vq && D.dirlist && D.amp && D.bk && D.rot && D.phase && D.amax && D.hist &&
-         D.offsets && D.rec && D.out && D.stats;
+         D.offsets && D.rec && D.pk && D.out && D.stats;
     if (!ok) {
         delete P;
         return fail(ctx, SCWP_E_NOMEM, "device allocation failed");

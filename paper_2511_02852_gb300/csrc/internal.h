@@ -76,6 +76,8 @@ struct PatchDev {
     int nblk_o = 0;                       // sort-pass blocks (kSortPassTile keys each)
     int key_bits = 16;
     uint32_t* offsets = nullptr;          // [total_bins + 1]
+    int4* pk = nullptr;                   // [cap] (x, y, bd, 0) of the live particles, written by the key
+                                          // kernel for the record pass's gathers
     BumpRec* rec = nullptr;               // [2 cap] bump records in bin order
     float* out = nullptr;                 // [3][H][W] blended maps
     float* partial = nullptr;             // [groups][3][H][W] per-bucket-group sums (groups > 1)

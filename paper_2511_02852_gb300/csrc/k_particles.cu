@@ -286,6 +286,13 @@ __global__ void __launch_bounds__(kTpb) k_bin_keys(PatchDev p, uint32_t* keys, u
         px[m] = i < n ? X[i] : 0;
         py[m] = i < n ? Y[i] : 0;
     }
+    // the state packed per particle for the record pass (one 16-byte gather
+    // per bump instead of three 4-byte ones)
+#pragma unroll
+    for (int m = 0; m < kBinItems; ++m) {
+        const int i = i0 + m * kTpb;
+        if (i < n) p.pk[i] = make_int4(px[m], py[m], (int)bd[m], 0);
+    }
 #pragma unroll
     for (int m = 0; m < kBinItems; ++m) {
         const int i = i0 + m * kTpb;
@@ -570,14 +577,18 @@ int sm_count() {
 constexpr int kRecItems = 4;   // sorted entries per thread and round, loads issued together
 
 __global__ void __launch_bounds__(kTpb) k_offsets_records(PatchDev p, const uint32_t* keys, const uint32_t* vals) {
+    // per warp: the 32 records of its 32 consecutive entries (1 KB), stored
+    // out as 16-byte chunks of consecutive addresses (whole sectors)
+    __shared__ uint4 s_rec[kTpb / 32][64];
     pdl_enter();
     const int n = 2 * p.count[0];
-    const int32_t* X = p.x[p.cur];
-    const int32_t* Y = p.y[p.cur];
-    const uint32_t* BD = p.bd[p.cur];
+    const int4* PK = p.pk;
     const uint32_t tb = (uint32_t)p.total_bins;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int stride = gridDim.x * kTpb * kRecItems;
-    for (int e0 = blockIdx.x * kTpb * kRecItems + threadIdx.x; e0 <= n; e0 += stride) {
+    // (the loop is uniform over a warp: its lanes take entries eb + lane)
+    for (int eb = blockIdx.x * kTpb * kRecItems + (threadIdx.x & ~31); eb <= n; eb += stride) {
+        const int e0 = eb + lane;
         uint32_t key[kRecItems], prev[kRecItems], id[kRecItems];
 #pragma unroll
         for (int q = 0; q < kRecItems; ++q) {
@@ -586,50 +597,59 @@ __global__ void __launch_bounds__(kTpb) k_offsets_records(PatchDev p, const uint
             prev[q] = (e > 0 && e <= n) ? keys[e - 1] : 0u;
             id[q] = e < n ? vals[e] : 0u;
         }
-        int32_t xs[kRecItems], ys[kRecItems];
-        uint32_t bds[kRecItems];
+        int4 st[kRecItems];
 #pragma unroll
         for (int q = 0; q < kRecItems; ++q) {   // the particles' state: every gather first
             const int e = e0 + q * kTpb;
-            const int i = (int)(id[q] >> 1);
             const bool ok = e < n && key[q] < tb;
-            xs[q] = ok ? X[i] : 0;
-            ys[q] = ok ? Y[i] : 0;
-            bds[q] = ok ? BD[i] : 0u;
+            st[q] = ok ? PK[id[q] >> 1] : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int q = 0; q < kRecItems; ++q) {
             const int e = e0 + q * kTpb;
-            if (e > n) continue;
-            const int lo = e == 0 ? 0 : (int)prev[q] + 1;
-            const int hi = e == n ? p.total_bins : min((int)key[q], p.total_bins);
-            for (int k = lo; k <= hi; ++k) p.offsets[k] = (uint32_t)e;
-            if (e == n || key[q] >= tb) continue;
-            const uint32_t bd = bds[q];
-            const bool trough = id[q] & 1u;
-            const int4 vq = lookup_vq(p, bd);
-            const float A = lookup_amp(p, bd);
-            const BucketDev& bk = p.bk[bd >> 16];
-            BumpRec r;
-            r.x = trough ? xs[q] - vq.z : xs[q];
-            r.y = trough ? ys[q] - vq.w : ys[q];
-            r.amp = trough ? -A : A;
-            r.id = id[q];
-            // e^{-i pi (x mod 2R)/R}: exact integer reduction (2R < 2^31), then
-            // sincospi of the FP32 quotient (within a few ulp of the exact one)
-            const int32_t R2 = 2 * bk.R;
-            int32_t xm, ym;
-            floor_divmod(r.x, R2, xm);
-            floor_divmod(r.y, R2, ym);
-            const float invR = bk.invR;
-            float sn, cs;
-            sincospif((float)xm * invR, &sn, &cs);
-            r.cx = cs;
-            r.sx = -sn;
-            sincospif((float)ym * invR, &sn, &cs);
-            r.cy = cs;
-            r.sy = -sn;
-            p.rec[e] = r;
+            if (e <= n) {
+                const int lo = e == 0 ? 0 : (int)prev[q] + 1;
+                const int hi = e == n ? p.total_bins : min((int)key[q], p.total_bins);
+                for (int k = lo; k <= hi; ++k) p.offsets[k] = (uint32_t)e;
+            }
+            const bool valid = e < n && key[q] < tb;
+            uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = r0;
+            if (valid) {
+                const uint32_t bd = (uint32_t)st[q].z;
+                const bool trough = id[q] & 1u;
+                const int4 vq = lookup_vq(p, bd);
+                const float A = lookup_amp(p, bd);
+                const BucketDev& bk = p.bk[bd >> 16];
+                const int32_t x = trough ? st[q].x - vq.z : st[q].x;
+                const int32_t y = trough ? st[q].y - vq.w : st[q].y;
+                // e^{-i pi (x mod 2R)/R}: exact integer reduction (2R < 2^31),
+                // then sincospi of the FP32 quotient (within a few ulp of the
+                // exact one)
+                const int32_t R2 = 2 * bk.R;
+                int32_t xm, ym;
+                floor_divmod(x, R2, xm);
+                floor_divmod(y, R2, ym);
+                const float invR = bk.invR;
+                float sx, cx, sy, cy;
+                sincospif((float)xm * invR, &sx, &cx);
+                sincospif((float)ym * invR, &sy, &cy);
+                // BumpRec {x, cx, -sx, id, y, cy, -sy, amp}
+                r0 = make_uint4((uint32_t)x, __float_as_uint(cx), __float_as_uint(-sx), id[q]);
+                r1 = make_uint4((uint32_t)y, __float_as_uint(cy), __float_as_uint(-sy), __float_as_uint(trough ? -A : A));
+            }
+            s_rec[warp][2 * lane] = r0;
+            s_rec[warp][2 * lane + 1] = r1;
+            __syncwarp();
+            // entries eb + q kTpb + r, r = 0 .. 31; chunk c (16 bytes) belongs
+            // to entry r = c / 2 and leaves only if that entry has a record
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            uint4* const dst = reinterpret_cast<uint4*>(p.rec + (eb + q * kTpb));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                if ((vm >> (c >> 1)) & 1u) dst[c] = s_rec[warp][c];
+            }
+            __syncwarp();
         }
     }
 }
