@@ -121,21 +121,53 @@ __global__ void __launch_bounds__(kTpb) k_advect_flag(PatchDev p) {
     int32_t* Y = p.y[p.cur];
     const uint32_t* BD = p.bd[p.cur];
     uint32_t alive_cnt = 0;
+    // the thread's kItems consecutive particles: one 16-byte access per array
+    // where all four are live (i0 is a multiple of 4)
+    static_assert(kItems == 4, "16-byte accesses of four particles");
+    const int i0 = base + threadIdx.x * kItems;
+    const bool full = i0 + kItems <= n;
+    int32_t xs[kItems], ys[kItems];
+    uint32_t bs[kItems];
+    if (full) {
+        const int4 a = *reinterpret_cast<const int4*>(X + i0);
+        const int4 b = *reinterpret_cast<const int4*>(Y + i0);
+        const uint4 c = *reinterpret_cast<const uint4*>(BD + i0);
+        xs[0] = a.x, xs[1] = a.y, xs[2] = a.z, xs[3] = a.w;
+        ys[0] = b.x, ys[1] = b.y, ys[2] = b.z, ys[3] = b.w;
+        bs[0] = c.x, bs[1] = c.y, bs[2] = c.z, bs[3] = c.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            xs[k] = i0 + k < n ? X[i0 + k] : 0;
+            ys[k] = i0 + k < n ? Y[i0 + k] : 0;
+            bs[k] = i0 + k < n ? BD[i0 + k] : 0u;
+        }
+    }
+    uint32_t fl = 0u;   // the four alive flags, one byte each
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
-        const int i = base + threadIdx.x * kItems + k;
-        if (i < n) {
-            const uint32_t bd = BD[i];
+        if (i0 + k < n) {
+            const uint32_t bd = bs[k];
             const int4 vq = lookup_vq(p, bd);
-            const int32_t x = X[i] + vq.x, y = Y[i] + vq.y;
-            X[i] = x;
-            Y[i] = y;
+            const int32_t x = xs[k] + vq.x, y = ys[k] + vq.y;
+            xs[k] = x;
+            ys[k] = y;
             const int32_t R = p.bk[bd >> 16].R;
             const bool a = (span_count(x, R, p.W) > 0 && span_count(y, R, p.H) > 0) ||
                            (span_count(x - vq.z, R, p.W) > 0 && span_count(y - vq.w, R, p.H) > 0);
-            p.flags[i] = a ? 1 : 0;
+            fl |= (a ? 1u : 0u) << (8 * k);
             alive_cnt += a ? 1u : 0u;
+            if (!full) {
+                X[i0 + k] = x;
+                Y[i0 + k] = y;
+                p.flags[i0 + k] = a ? 1 : 0;
+            }
         }
+    }
+    if (full) {
+        *reinterpret_cast<int4*>(X + i0) = make_int4(xs[0], xs[1], xs[2], xs[3]);
+        *reinterpret_cast<int4*>(Y + i0) = make_int4(ys[0], ys[1], ys[2], ys[3]);
+        *reinterpret_cast<uint32_t*>(p.flags + i0) = fl;
     }
     uint32_t total;
     block_exscan(alive_cnt, s_warp, total);
@@ -163,15 +195,29 @@ __global__ void __launch_bounds__(kTpb) k_compact_scatter(PatchDev p) {
     uint32_t before = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += kTpb) before += p.blk[b];
     const uint32_t blk_cnt = p.blk[blockIdx.x];
+    const int i0 = base + threadIdx.x * kItems;   // (a multiple of 4: 16-byte loads)
+    if (i0 + kItems <= n) {
+        const uint32_t fl = *reinterpret_cast<const uint32_t*>(p.flags + i0);
+        const int4 a = *reinterpret_cast<const int4*>(Xs + i0);
+        const int4 b = *reinterpret_cast<const int4*>(Ys + i0);
+        const uint4 c = *reinterpret_cast<const uint4*>(Bs + i0);
+        xs[0] = a.x, xs[1] = a.y, xs[2] = a.z, xs[3] = a.w;
+        ys[0] = b.x, ys[1] = b.y, ys[2] = b.z, ys[3] = b.w;
+        bs[0] = c.x, bs[1] = c.y, bs[2] = c.z, bs[3] = c.w;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const int i = base + threadIdx.x * kItems + k;
-        f[k] = (i < n) ? p.flags[i] : 0;
-        xs[k] = (i < n) ? Xs[i] : 0;
-        ys[k] = (i < n) ? Ys[i] : 0;
-        bs[k] = (i < n) ? Bs[i] : 0u;
-        mine += f[k];
+        for (int k = 0; k < kItems; ++k) f[k] = (uint8_t)((fl >> (8 * k)) & 0xFFu);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int i = i0 + k;
+            f[k] = (i < n) ? p.flags[i] : 0;
+            xs[k] = (i < n) ? Xs[i] : 0;
+            ys[k] = (i < n) ? Ys[i] : 0;
+            bs[k] = (i < n) ? Bs[i] : 0u;
+        }
     }
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) mine += f[k];
     // survivors of the earlier blocks, summed by this block (integers: any
     // order); the last block also publishes the total as the new live count
     uint32_t blk_off;
