@@ -825,11 +825,8 @@ scwp_status scwp_create(const scwp_spectrum_desc* desc, scwp_ctx** out) {
     std::vector<float> h0;
     std::vector<double> om;
     build_background(ctx->sm, N, desc->fft_L, desc->seed, h0, om);
-    std::vector<float2> tw(N);
-    for (int m = 0; m < N; ++m) {
-        const double a = 2.0 * M_PI * m / N;
-        tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
+    std::vector<float2> tw(N, make_float2(0.f, 0.f));   // the tables take at most N / 3 entries
+    build_background_twiddles(N, tw.data());
     const size_t NN = (size_t)N * N;
     ctx->h0 = (float2*)dalloc(ctx, NN * sizeof(float2));
     ctx->omega = (float2*)dalloc(ctx, NN * sizeof(float2));

@@ -260,7 +260,7 @@ struct BgDev {
     int N = 0;
     const float2* h0 = nullptr;   // [N][N] FFT-natural order
     const float2* omega = nullptr;// [N][N] w(k) as a float pair (hi, lo), w = hi + lo
-    const float2* tw = nullptr;   // [N] e^{2 pi i m / N}
+    const float2* tw = nullptr;   // twiddle tables of the stages (build_background_twiddles)
     float2* I = nullptr;          // [3][N/2 + 1][N] row-pass output (H1, Dx1, Dy1 of rows k_y <= N/2)
     float* out = nullptr;         // [3][N][N] h, Dx, Dy
     float lam = 1.f, dk = 0.f;
@@ -270,5 +270,11 @@ struct BgDev {
 cudaError_t launch_background(const BgDev& b, double t, cudaStream_t st, const float2* t_dev = nullptr);
 // complex elements of the row-pass intermediate of an N x N background
 size_t background_scratch_elems(int N);
+// entries of the twiddle tables of a length-N transform (at most N / 3)
+size_t background_twiddle_elems(int N);
+// the twiddle tables of a length-N transform, built in float64 on the host:
+// per stage after the first (span Ns = 16, 256, ..., radix R = min(16, N / Ns)),
+// e^{2 pi i p k / (Ns R)} for p = 1, 2, 4, 8 (p < R) and k = 0 .. Ns - 1, as [p][k]
+void build_background_twiddles(int N, float2* out);
 
 }  // namespace scwp

@@ -30,11 +30,20 @@
 // registers, 16 values per thread, each stage one shared-memory round trip
 // (load, barrier, twiddle, 16-point transform, store, barrier) on one buffer
 // per transform, padded by one element every 16 so that the strided stores
-// of the first stage fall on distinct banks.  Twiddles e^{2 pi i m / N} come
-// from a float table built in float64 on the host.  The inverse transform is
+// of the first stage fall on distinct banks.  The inverse transform is
 // unnormalised: f[j] = sum_m F[m] e^{+2 pi i m j / N}.
+//
+// Twiddles come from a float table built in float64 on the host, laid out by
+// stage: for each stage after the first (span Ns = 16, 256, ..., radix
+// R = min(16, N / Ns)) the powers e^{2 pi i p k / (Ns R)}, p = 1, 2, 4, 8
+// (p < R), k = 0 .. Ns - 1, stored [p][k].  The threads of a warp take
+// consecutive butterflies k, so each of their twiddle loads reads one run of
+// consecutive entries (a table indexed by m = p k N / (Ns R) would scatter
+// the loads of a warp over up to 32 sectors).
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cmath>
 
 #include "internal.h"
 
@@ -53,85 +62,130 @@ template <int N>
 __host__ __device__ constexpr int threads_per_transform() { return N >= 16 ? N / 16 : 1; }
 template <int N>
 __host__ __device__ constexpr int padded() { return N + N / 16; }
-// stride of one transform in shared memory: the padded length, rounded to
-// 2 mod 16 complex values so that consecutive transforms start 4 banks apart
-// (the column pass's loads and stores walk across transforms)
-template <int N>
-__host__ __device__ constexpr int tstride() { return padded<N>() + ((18 - padded<N>() % 16) % 16); }
 // columns per column-pass CTA for h + i Dx (twice as many for Dy, in pairs)
 template <int N>
 __host__ __device__ constexpr int col_group() { return N >= 2048 ? 4 : N >= 1024 ? 8 : N >= 32 ? 16 : N / 2; }
-
-
-// e^{+2 pi i k / 16}, k = 0 .. 7 (the roots the 16-point transform uses)
-__device__ __forceinline__ float2 root16(int k) {
-    constexpr float c1 = 0.9238795325f, c2 = 0.7071067812f, c3 = 0.3826834324f;
-    switch (k & 7) {
-        case 0: return make_float2(1.f, 0.f);
-        case 1: return make_float2(c1, c3);
-        case 2: return make_float2(c2, c2);
-        case 3: return make_float2(c3, c1);
-        case 4: return make_float2(0.f, 1.f);
-        case 5: return make_float2(-c3, c1);
-        case 6: return make_float2(-c2, c2);
-        default: return make_float2(-c1, c3);
-    }
+// stride of one transform in shared memory: the padded length, rounded to
+// 32 / CZ mod 16 complex values (CZ = col_group).  The column pass's
+// transposes put lane l of a warp at transform l mod CZ, row l / CZ; with
+// that stride the 32 lanes fill the 16 two-word bank slots exactly twice, the
+// least a warp's 8-byte accesses can take.
+template <int N>
+__host__ __device__ constexpr int tstride() {
+    return padded<N>() + (((32 / col_group<N>()) % 16 - padded<N>() % 16 + 16) % 16);
 }
 
-// In-register inverse DFT of R points (R = 2, 4, 8, 16): radix-2
-// decimation in time on bit-reversed input, result in natural order.
+// the stages' twiddle tables (see the header): radix of the stage of span
+// Ns, and the offset of that stage's table
+__host__ __device__ constexpr int log2c(int x) { return x <= 1 ? 0 : 1 + log2c(x / 2); }
+__host__ __device__ constexpr int radix_at(int N, int Ns) { return N / Ns >= 16 ? 16 : N / Ns; }
+__host__ __device__ constexpr int tw_base(int N, int Ns) {
+    return Ns <= 16 ? 0 : tw_base(N, Ns / 16) + log2c(radix_at(N, Ns / 16)) * (Ns / 16);
+}
+
+
+// a e^{+2 pi i e / 16} for the exponents of the 16-point transform
+constexpr float kC1 = 0.92387953251128674f;   // cos(pi / 8)
+constexpr float kS1 = 0.38268343236508977f;   // sin(pi / 8)
+constexpr float kH = 0.70710678118654752f;    // cos(pi / 4)
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }   // e = 4
+__device__ __forceinline__ float2 mul_e2(float2 a) { return make_float2(kH * (a.x - a.y), kH * (a.x + a.y)); }
+__device__ __forceinline__ float2 mul_e6(float2 a) { return make_float2(-kH * (a.x + a.y), kH * (a.x - a.y)); }
+__device__ __forceinline__ float2 mul_cs(float2 a, float c, float s) {
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// In-register inverse DFT of R points (R = 2, 4, 8, 16), natural order in
+// and out: X[k] = sum_n v[n] e^{+2 pi i n k / R}.  R = 16 is a 4 x 4
+// decomposition (n = 4 n1 + n2, k = k1 + 4 k2: four 4-point transforms over
+// n1, the factors e^{2 pi i n2 k1 / 16}, four 4-point transforms over n2),
+// R = 8 a 2 x 4 one; multiplications by 1 and i are moves, those by
+// e^{i pi/4} and e^{3 i pi/4} two products each.
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = make_float2(d02.x - d13.y, d02.y + d13.x);   // d02 + i d13
+    a3 = make_float2(d02.x + d13.y, d02.y - d13.x);   // d02 - i d13
+}
+
 template <int R>
 __device__ __forceinline__ void dft_inv(float2 (&v)[R]) {
-    constexpr int L = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
-    float2 u[R];
+    if constexpr (R == 2) {
+        const float2 a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    } else if constexpr (R == 4) {
+        dft4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        // even and odd halves, then X[k] = E[k] + e^{i pi k/4} O[k], X[k + 4] = E[k] - ...
+        dft4(v[0], v[2], v[4], v[6]);
+        dft4(v[1], v[3], v[5], v[7]);
+        const float2 o1 = mul_e2(v[3]), o2 = mul_i(v[5]), o3 = mul_e6(v[7]);
+        const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+        v[0] = cadd(e0, v[1]);
+        v[4] = csub(e0, v[1]);
+        v[1] = cadd(e1, o1);
+        v[5] = csub(e1, o1);
+        v[2] = cadd(e2, o2);
+        v[6] = csub(e2, o2);
+        v[3] = cadd(e3, o3);
+        v[7] = csub(e3, o3);
+    } else {
+        static_assert(R == 16, "radix 2, 4, 8 or 16");
+        // y[n2][k1] in v[4 k1 + n2]... computed in place: the 4-point
+        // transform over n1 of column n2 leaves k1 at v[n2 + 4 k1]
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        int r = 0;
+        for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+        // factors e^{2 pi i n2 k1 / 16} (n2, k1 >= 1)
+        v[5] = mul_cs(v[5], kC1, kS1);     // 1
+        v[6] = mul_e2(v[6]);               // 2
+        v[7] = mul_cs(v[7], kS1, kC1);     // 3
+        v[9] = mul_e2(v[9]);               // 2
+        v[10] = mul_i(v[10]);              // 4
+        v[11] = mul_e6(v[11]);             // 6
+        v[13] = mul_cs(v[13], kS1, kC1);   // 3
+        v[14] = mul_e6(v[14]);             // 6
+        v[15] = mul_cs(v[15], -kC1, -kS1); // 9
+        // 4-point transforms over n2 of row k1: X[k1 + 4 k2]
 #pragma unroll
-        for (int b = 0; b < L; ++b) r |= ((i >> b) & 1) << (L - 1 - b);
-        u[r] = v[i];
-    }
+        for (int k1 = 0; k1 < 4; ++k1) dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+        // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 block
+        float2 t;
 #pragma unroll
-    for (int len = 2; len <= R; len <<= 1) {
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int i = 0; i < R; i += len) {
-#pragma unroll
-            for (int j = 0; j < len / 2; ++j) {
-                const float2 w = root16(j * (16 / len));   // e^{2 pi i j / len}
-                const float2 a = u[i + j];
-                const float2 b = j == 0 ? u[i + j + len / 2] : cmul(w, u[i + j + len / 2]);
-                u[i + j] = cadd(a, b);
-                u[i + j + len / 2] = csub(a, b);
+            for (int b = a + 1; b < 4; ++b) {
+                t = v[4 * a + b];
+                v[4 * a + b] = v[4 * b + a];
+                v[4 * b + a] = t;
             }
-        }
     }
-#pragma unroll
-    for (int i = 0; i < R; ++i) v[i] = u[i];
 }
 
-// Multiply v[r] by the twiddle e^{2 pi i r m / N}, r = 1 .. R - 1, of one
-// butterfly (m = k step): e^{2 pi i m / N} to the powers 1, 2, 4, 8 come
-// from the table (one load each), the others are products of two or three
-// of them (at most three roundings, within 3e-7 of the table values), so a
-// radix-16 butterfly loads 4 twiddles instead of 15.
-template <int R>
-__device__ __forceinline__ void apply_twiddles(float2 (&v)[R], int m, const float2* __restrict__ tw) {
-    const float2 w1 = __ldg(&tw[m]);
+// Multiply v[r] by the twiddle e^{2 pi i r k / (Ns R)}, r = 1 .. R - 1, of
+// butterfly k of a stage of span Ns: the powers r = 1, 2, 4, 8 come from
+// the stage's table tws ([p][k], one load each), the others are products of
+// two or three of them (at most three roundings, within 3e-7 of the exact
+// values), so a radix-16 butterfly loads 4 twiddles instead of 15.
+template <int R, int Ns>
+__device__ __forceinline__ void apply_twiddles(float2 (&v)[R], int k, const float2* __restrict__ tws) {
+    const float2 w1 = __ldg(&tws[k]);
     v[1] = cmul(v[1], w1);
     if constexpr (R >= 4) {
-        const float2 w2 = __ldg(&tw[2 * m]);
+        const float2 w2 = __ldg(&tws[Ns + k]);
         const float2 w3 = cmul(w1, w2);
         v[2] = cmul(v[2], w2);
         v[3] = cmul(v[3], w3);
         if constexpr (R >= 8) {
-            const float2 w4 = __ldg(&tw[4 * m]);
+            const float2 w4 = __ldg(&tws[2 * Ns + k]);
             const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
             v[4] = cmul(v[4], w4);
             v[5] = cmul(v[5], w5);
             v[6] = cmul(v[6], w6);
             v[7] = cmul(v[7], w7);
             if constexpr (R >= 16) {
-                const float2 w8 = __ldg(&tw[8 * m]);
+                const float2 w8 = __ldg(&tws[3 * Ns + k]);
                 v[8] = cmul(v[8], w8);
                 v[9] = cmul(v[9], cmul(w1, w8));
                 v[10] = cmul(v[10], cmul(w2, w8));
@@ -165,7 +219,7 @@ __device__ __forceinline__ void stage(float2* buf, int jt, const float2* __restr
     for (int q = 0; q < B; ++q) {
         const int j = jt + q * P;
         const int k = j & (Ns - 1);
-        if constexpr (Ns > 1) apply_twiddles<R>(v[q], k * (N / (Ns * R)), tw);
+        if constexpr (Ns > 1) apply_twiddles<R, Ns>(v[q], k, tw + tw_base(N, Ns));
         dft_inv<R>(v[q]);
         const int d = (j - k) * R + k;
 #pragma unroll
@@ -250,11 +304,12 @@ __global__ void __launch_bounds__(3 * threads_per_transform<N>(), N >= 4096 ? 1 
         const float2 q = make_float2(b.x * c - b.y * s, b.x * s + b.y * c);
         const float2 ht = make_float2(a.x * c - a.y * s + q.x, a.x * s + a.y * c - q.y);
         const float kx = bg.dk * (float)nx;
-        const float kk = sqrtf(kx * kx + ky * ky);
+        const float k2 = kx * kx + ky * ky;
         float ux = 0.f, uy = 0.f;
-        if (kk > 0.f) {
-            ux = kx / kk;
-            uy = ky / kk;
+        if (k2 > 0.f) {   // k / |k|
+            const float rk = rsqrtf(k2);
+            ux = kx * rk;
+            uy = ky * rk;
         }
         // D~ = -i lam u h~ = lam u (h~.y, -h~.x)
         buf[0][pad(mx)] = ht;
@@ -384,5 +439,25 @@ cudaError_t launch_background(const BgDev& bg, double t, cudaStream_t st, const 
 }
 
 size_t background_scratch_elems(int N) { return (size_t)3 * (N / 2 + 1) * N; }
+
+size_t background_twiddle_elems(int N) {
+    size_t n = 0;
+    for (int Ns = 16; Ns < N; Ns *= 16) n += (size_t)log2c(radix_at(N, Ns)) * Ns;
+    return n;
+}
+
+void build_background_twiddles(int N, float2* out) {
+    size_t o = 0;
+    for (int Ns = 16; Ns < N; Ns *= 16) {
+        const int R = radix_at(N, Ns);
+        for (int p = 1; p < R; p *= 2)
+            for (int k = 0; k < Ns; ++k) {
+                // e^{2 pi i p k / (Ns R)} = e^{2 pi i m / N}
+                const long long m = (long long)p * k * (N / (Ns * R));
+                const double a = 2.0 * M_PI * (double)m / (double)N;
+                out[o++] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+    }
+}
 
 }  // namespace scwp

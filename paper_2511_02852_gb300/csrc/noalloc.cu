@@ -7,7 +7,7 @@
 // buffers, or plug-ins whose host application owns every allocation.  This
 // entry point lets them evolve and transform a background spectrum they
 // already hold in device memory.  Its scratch (the row-pass intermediate and
-// the twiddle table) lives in one file-scope __device__ array below, sized
+// the twiddle tables) lives in one file-scope __device__ array below, sized
 // for grids up to kNoAllocMaxN x kNoAllocMaxN; every GPU that loads this
 // library holds that array (3 x 257 x 512 + 512 complex floats, about
 // 3.0 MiB) until the process exits.
@@ -27,17 +27,26 @@ constexpr size_t kInterElems = 3 * (size_t)(kNoAllocMaxN / 2 + 1) * kNoAllocMaxN
 constexpr size_t kScratchElems = kInterElems + kNoAllocMaxN;
 
 // [0, kInterElems): row-pass output (H1, Dx1, Dy1 of the rows k_y <= N/2);
-// [kInterElems, kInterElems + N): e^{2 pi i m / N} for N = kNoAllocMaxN.
+// [kInterElems, kScratchElems): the twiddle tables of every grid N = 8 ..
+// kNoAllocMaxN, one after another (tw_offset(N)); together they take 480 of
+// the kNoAllocMaxN entries.
 static __device__ __align__(256) float2 g_noalloc_scratch[kScratchElems];
+
+// offset of grid N's twiddle table in the twiddle area
+size_t tw_offset(int n) {
+    size_t o = 0;
+    for (int m = 8; m < n; m *= 2) o += scwp::background_twiddle_elems(m);
+    return o;
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 float2* g_scratch_ptr[kMaxDevices] = {};
 
 // One-time set-up per device (the caller's current device): look up the
-// array's device address and fill the twiddle table.  Runs on the first call
-// on that device; the copy below is a synchronous cudaMemcpy, so that first
-// call must not happen inside a stream capture.
+// array's device address and fill the twiddle tables.  Runs on the first
+// call on that device; the copy below is a synchronous cudaMemcpy, so that
+// first call must not happen inside a stream capture.
 cudaError_t setup_device(int dev, float2** out) {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (g_scratch_ptr[dev]) {
@@ -47,22 +56,14 @@ cudaError_t setup_device(int dev, float2** out) {
     float2* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    if (tw_offset(2 * kNoAllocMaxN) > (size_t)kNoAllocMaxN) return cudaErrorInvalidValue;   // the tables fit
     static float2 tw[kNoAllocMaxN];   // host staging, no heap allocation
-    for (int m = 0; m < kNoAllocMaxN; ++m) {
-        const double a = 2.0 * M_PI * m / kNoAllocMaxN;
-        tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
+    for (int n = 8; n <= kNoAllocMaxN; n *= 2) scwp::build_background_twiddles(n, tw + tw_offset(n));
     e = cudaMemcpy(ptr + kInterElems, tw, kNoAllocMaxN * sizeof(float2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = ptr;
     *out = ptr;
     return cudaSuccess;
-}
-
-// twiddles of a smaller power-of-two grid: every (N_max / N)-th entry
-__global__ void k_gather_twiddles(const float2* full, float2* dst, int n, int stride) {
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
-        dst[m] = full[m * stride];
 }
 
 }  // namespace
@@ -86,16 +87,7 @@ extern "C" scwp_status scwp_background_noalloc(const float* h0, const float* ome
         return SCWP_E_CUDA;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const float2* full_tw = scratch + kInterElems;
-    // the row-pass buffer holds 3 (n/2 + 1) n values; for n < N_max its tail
-    // keeps this grid's twiddles (written before, read by, the FFT of this call)
-    const float2* tw = full_tw;
-    if (n < kNoAllocMaxN) {
-        float2* small = scratch + scwp::background_scratch_elems(n);
-        k_gather_twiddles<<<1, 256, 0, st>>>(full_tw, small, n, kNoAllocMaxN / n);
-        scwp::count_launches(1);
-        tw = small;
-    }
+    const float2* tw = scratch + kInterElems + tw_offset(n);
     scwp::BgDev bg;
     bg.N = n;
     bg.h0 = reinterpret_cast<const float2*>(h0);
