@@ -54,9 +54,12 @@
 // four corners; bumps whose box starts at the tile's first texel in both axes
 // (every bump covering the whole tile among them) sum their (0, 0) corner in
 // registers, added by one warp reduction per pass.  Then the x prefix (one
-// row of one plane per thread), the y prefix (one column of one
-// plane per thread) and the contraction, which zeroes every difference-array
-// element it reads, so no pass needs a clearing phase.
+// row of one plane per thread), the y prefix (one column of one plane per
+// thread, stored only at the first row of each 4-row segment of the
+// contraction) and the contraction (one column of a segment per thread),
+// which finishes the y prefix of the segment's other rows in registers and
+// zeroes every difference-array element it reads, so no pass needs a
+// clearing phase.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -432,7 +435,11 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                 }
                 __syncthreads();
                 if (tid < kScanThreads) {
-                    // ---- prefix along y: one column of one plane per thread
+                    // ---- prefix along y: one column of one plane per thread.
+                    // Only the first row of each contraction segment gets its
+                    // prefix sum; the contraction adds the segment's other
+                    // rows to it in registers
+                    static_assert(kSegRows == 4, "one stored row per 4-row segment");
                     uint32_t* E = S.E[tid / kT];
                     const int x = tid % kT;
                     uint32_t cr[4], nx[4], run = 0u;
@@ -444,20 +451,21 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
 #pragma unroll
                             for (int k = 0; k < 4; ++k) nx[k] = E[sw(y0 + 4 + k, x)];
                         }
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            run += cr[k];
-                            E[sw(y0 + k, x)] = run;
-                        }
+                        run += cr[0];
+                        E[sw(y0, x)] = run;
+                        run += cr[1] + cr[2] + cr[3];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) cr[k] = nx[k];
                     }
                 }
                 __syncthreads();
                 // ---- this thread's texels contracted; each element of E is
-                // zeroed once read (the next pass starts from a cleared array)
+                // zeroed once read (the next pass starts from a cleared array).
+                // Row r > 0 of the segment: the prefix sum of row r - 1 plus
+                // the x prefix of row r (exact modulo 2^32)
                 const float2 ux = ph[kT + cx];   // (cos a_X, sin a_X) of this column
                 const float kh = 0.25f * inv, kd = lamq * inv;
+                uint32_t sy[kPlanes];
 #pragma unroll
                 for (int r = 0; r < kSegRows; ++r) {
                     const int y = sg * kSegRows + r;
@@ -465,7 +473,9 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                     float f[kPlanes];
 #pragma unroll
                     for (int k = 0; k < kPlanes; ++k) {
-                        f[k] = (float)(int32_t)S.E[k][o];
+                        const uint32_t e = S.E[k][o];
+                        sy[k] = r == 0 ? e : sy[k] + e;
+                        f[k] = (float)(int32_t)sy[k];
                         S.E[k][o] = 0u;
                     }
                     const float2 vy = ph[y];   // (cos a_Y, sin a_Y)
