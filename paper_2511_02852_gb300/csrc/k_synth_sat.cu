@@ -145,6 +145,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most one group of this thread's copies is still in flight
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Record slots are 32 bytes per thread.  Threads with bit 2 of their index
+// set keep the two 16-byte halves of their record in swapped order, so that
+// the eight threads of a quarter warp (whose 16-byte accesses one shared
+// memory wavefront serves) touch eight different 16-byte bank groups: the
+// copies into the slots and the reads from them are free of bank conflicts
+// (with the halves in order, threads t and t + 4 met in the same banks).
+__device__ __forceinline__ int half_swap(int tid) { return (tid >> 2) & 1; }
+
 // A pass of this CTA's part: segment s, its candidates [c0, c1); s < 0: none.
 struct Pass {
     int s, c0, c1;
@@ -182,11 +190,30 @@ __device__ __forceinline__ int fetch_rows(SatSmem& S, const BumpRec* rec, int lo
         else
             hi = mid - 1;
     }
-    const BumpRec* src = rec + S.rs[lo] + (j - S.cum[lo]);
-    BumpRec* dst = &S.raw[slot][tid];
-    cp_async16(dst, src);
-    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16, reinterpret_cast<const unsigned char*>(src) + 16);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(rec + S.rs[lo] + (j - S.cum[lo]));
+    unsigned char* dst = reinterpret_cast<unsigned char*>(&S.raw[slot][tid]);
+    const int hs = half_swap(tid);
+    cp_async16(dst + 16 * hs, src);
+    cp_async16(dst + 16 * (hs ^ 1), src + 16);
     return lo;
+}
+
+// The record of this thread's slot (its two 16-byte halves in the order
+// half_swap gives).
+__device__ __forceinline__ BumpRec read_slot(const SatSmem& S, int slot, int tid) {
+    const uint4* q = reinterpret_cast<const uint4*>(&S.raw[slot][tid]);
+    const int hs = half_swap(tid);
+    const uint4 a = q[hs], b = q[hs ^ 1];
+    BumpRec r;
+    r.x = (int32_t)a.x;
+    r.cx = __uint_as_float(a.y);
+    r.sx = __uint_as_float(a.z);
+    r.id = a.w;
+    r.y = (int32_t)b.x;
+    r.cy = __uint_as_float(b.y);
+    r.sy = __uint_as_float(b.z);
+    r.amp = __uint_as_float(b.w);
+    return r;
 }
 
 __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* items, int n_items,
@@ -365,7 +392,7 @@ __global__ void __launch_bounds__(kSatThreads, 1) k_synth_sat(const TcItem* item
                         fetch_rows(S, p.rec, S.sgrb[Pn.s], S.sgrb[Pn.s + 1] - 1, Pn.c0 + tid, k ^ 1, tid);
                     cp_async_commit();
                     cp_async_wait_prev();   // this candidate's record has landed
-                    const BumpRec rc = S.raw[k][tid];
+                    const BumpRec rc = read_slot(S, k, tid);
                     k ^= 1;
                     // texel t of the tile is inside iff x_b - R < X0 + t Q < x_b + R
                     const int a = clamp_t(((rc.x - R - X0) >> 16) + 1);
