@@ -782,8 +782,10 @@ def run_ours(args):
             "roofline": roofline, "roofline_fft": roof_fft, "cpu_baseline": cpu, "e2e": e2e,
             "plain": plain, "batched_vs_plain": bvp, "gather_tc": other,
             "gpu_launches": launches, "clocks": clocks, "autotune": tuned,
-            "synth_groups": [sc.info(p).sat_groups if args.synth == "sat" else sc.info(p).synth_groups
-                             for p in range(npatch)],
+            # bucket groups of each patch's own (one patch per launch) plan;
+            # a batched frame plans its groups over all patches at once
+            "synth_groups_per_patch_plan": [sc.info(p).sat_groups if args.synth == "sat" else sc.info(p).synth_groups
+                                            for p in range(npatch)],
         }
         print(json.dumps(line))
     sc.close()
