@@ -6,6 +6,8 @@ summed-area synthesis (SCWP_SYNTH_SAT), through the C ABI.
   over every patch, frames replayed as captured graphs);
 * mixed_large: 2048^2 FFT over 4 km, 8 patches of 1024^2 texels with 2M
   particles and 32 buckets each;
+* realistic: one 1024^2 patch with 16 buckets, ~200k particles and a wake,
+  over its whole 600-frame run (checked at frames 100, 300 and 600);
 * the background FFT at 1024^2 and 2048^2, at t = 0.05 s and t = 60 s (the
   phase w t reduced without float64 on the GPU).
 
@@ -151,6 +153,27 @@ def test_mixed_large_full_size():
     sc, orc = run_scene(cfg, 2, batched=True)
     worst, n_max = check_patches(sc, orc, cfg, 150, "mixed_large")
     assert n_max > 5000          # the regime the quantum bound is about
+    sc.close()
+
+
+def test_realistic_600_frames_full_size():
+    """The realistic workload over its whole 600-frame run (1024^2 patch,
+    16 buckets, ~200k particles, wake; 10 s of simulated time): state, bins
+    and eval counts bit-exact and the sampled maps within the contract at
+    frames 100, 300 and 600, so neither the integer particle state nor the
+    background's phase drifts from the oracle over the run."""
+    from paper_2511_02852_gb300 import scwp
+    cfg = wl.realistic()
+    sc = scwp.Scene(cfg, device=0)
+    sc.set_synth_mode(scwp.SYNTH_SAT)
+    orc = OracleScene(cfg)
+    for f in range(1, 601):
+        sc.step(cfg["dt"])
+        orc.step(cfg["dt"])
+        if f in (100, 300, 600):
+            torch.cuda.synchronize()
+            assert sc.stats(0).live_particles > 150000
+            check_patches(sc, orc, cfg, 150, f"realistic frame {f}")
     sc.close()
 
 
