@@ -66,13 +66,14 @@ __host__ __device__ constexpr int padded() { return N + N / 16; }
 template <int N>
 __host__ __device__ constexpr int col_group() { return N >= 2048 ? 4 : N >= 1024 ? 8 : N >= 32 ? 16 : N / 2; }
 // stride of one transform in shared memory: the padded length, rounded to
-// 32 / CZ mod 16 complex values (CZ = col_group).  The column pass's
+// 16 / CZ mod 16 complex values (CZ = col_group).  The column pass's
 // transposes put lane l of a warp at transform l mod CZ, row l / CZ; with
-// that stride the 32 lanes fill the 16 two-word bank slots exactly twice, the
-// least a warp's 8-byte accesses can take.
+// that stride the 16 lanes of each half warp (the lanes one shared-memory
+// wavefront of 8-byte accesses serves) meet 16 different two-word bank
+// slots, so a warp's access takes two wavefronts, the least it can.
 template <int N>
 __host__ __device__ constexpr int tstride() {
-    return padded<N>() + (((32 / col_group<N>()) % 16 - padded<N>() % 16 + 16) % 16);
+    return padded<N>() + (((16 / col_group<N>()) % 16 - padded<N>() % 16 + 16) % 16);
 }
 
 // the stages' twiddle tables (see the header): radix of the stage of span
